@@ -1,0 +1,410 @@
+"""FP64 CPU oracle of the QED particle step (test infrastructure only).
+
+This package is the plain, slow reference the CUDA library is checked against.
+It is written from the paper (Lobet et al., arXiv:1311.1107, sections 2-3:
+Eq. 1-8 and the Monte-Carlo pair scheme) and shares no code with the library.
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the product path never does.
+
+The arithmetic lives in ``qed_oracle.c`` (plain C, FP64, compiled with
+``-ffp-contract=off`` so that results do not depend on the host's FMA
+contraction).  This module compiles it with gcc on first use and exposes it
+through ctypes with numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qed_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# grid sizes of the table definition (see qed_oracle.c)
+NRATE, NCDF, NS = 769, 97, 256
+
+ELECTRON, POSITRON, PHOTON = 0, 1, 2
+RNG_INIT, RNG_EMIT, RNG_PHOTON_TAU, RNG_PAIR, RNG_PAIR_POS = 0, 1, 2, 3, 4
+FIELD_NONE, FIELD_PLANE, FIELD_GAUSSIAN, FIELD_YEE2D, FIELD_UNIFORM_B = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, FP64, no FMA contraction)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+class Units(C.Structure):
+    _fields_ = [("lambda_m", C.c_double), ("omega", C.c_double), ("tau_c", C.c_double),
+                ("a_S", C.c_double), ("C_rate", C.c_double), ("tau0w", C.c_double),
+                ("alpha", C.c_double)]
+
+
+class Field(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a0", C.c_double), ("w0", C.c_double),
+                ("tau_fwhm", C.c_double), ("x_focus", C.c_double), ("t_focus", C.c_double),
+                ("b0", C.c_double), ("yee", C.c_void_p * 6), ("nx", C.c_int64),
+                ("ny", C.c_int64), ("dx", C.c_double), ("dy", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double)]
+
+
+class _Species(C.Structure):
+    _fields_ = [("n", C.c_int64), ("cap", C.c_int64)] + [
+        (name, C.c_void_p) for name in ("x", "y", "z", "ux", "uy", "uz", "tau", "w", "chi",
+                                        "margin", "nemit")]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("step", C.c_int64), ("seed", C.c_uint64),
+                ("chi_th", C.c_double), ("photon_min_gamma", C.c_double),
+                ("pairs", C.c_int32), ("max_emit", C.c_int32), ("recoil", C.c_int32),
+                ("dims", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_emit", "n_photon", "n_photon_drop",
+                                         "n_subthreshold", "n_pair", "n_pair_drop",
+                                         "n_saturated", "n_clamped", "n_continuous")] + [
+        ("e_subthreshold", C.c_double), ("e_dropped", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        d, i64, u32p = C.c_double, C.c_int64, C.POINTER(C.c_uint32)
+        vp = C.c_void_p
+        sig = {
+            "or_units_init": (None, [d, C.POINTER(Units)]),
+            "or_bessel_K": (d, [d, d]),
+            "or_int_K13": (d, [d]),
+            "or_F_gamma": (d, [d, d, d]),
+            "or_F_pair": (d, [d, d, d]),
+            "or_H_exact": (d, [d]),
+            "or_G_exact": (d, [d]),
+            "or_T_exact": (d, [d]),
+            "or_cdf_gamma_exact": (d, [d, d]),
+            "or_cdf_pair_exact": (d, [d, d]),
+            "or_tables_size": (C.c_size_t, []),
+            "or_tables_build": (None, [vp]),
+            "or_lookup_rate": (d, [vp, C.c_int, d, C.POINTER(C.c_int)]),
+            "or_sample_gamma": (d, [vp, d, d, C.POINTER(C.c_int)]),
+            "or_sample_pair": (d, [vp, d, d, C.POINTER(C.c_int)]),
+            "or_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "or_u53": (d, [C.c_uint32, C.c_uint32]),
+            "or_draw": (None, [C.c_uint64, C.c_int, C.c_int, i64, i64, C.c_int, u32p]),
+            "or_field_eval": (None, [C.POINTER(Field), d, d, d, d, vp, vp]),
+            "or_chi_e": (d, [vp, vp, vp, d, d]),
+            "or_chi_gamma": (d, [vp, vp, vp, d]),
+            "or_boris": (None, [d, d, vp, vp, vp]),
+            "or_step": (C.c_int, [C.POINTER(Units), vp, C.POINTER(Field), C.POINTER(Params),
+                                  C.POINTER(_Species), C.POINTER(_Species),
+                                  C.POINTER(_Species), C.POINTER(Stats)]),
+            "or_run": (C.c_int, [C.POINTER(Units), vp, C.POINTER(Field), C.POINTER(Params),
+                                 i64, C.POINTER(_Species), C.POINTER(_Species),
+                                 C.POINTER(_Species), C.POINTER(Stats)]),
+            "or_init_tau": (None, [C.c_uint64, C.c_int, vp, i64, i64]),
+            "or_count_events_frozen": (i64, [C.POINTER(Units), vp, d, d, d, i64, C.c_uint64,
+                                             C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _vec(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(3))
+
+
+# ---------------------------------------------------------------- units, functions
+
+def units(lambda_m: float = 0.8e-6) -> Units:
+    u = Units()
+    lib().or_units_init(lambda_m, C.byref(u))
+    return u
+
+
+def bessel_K(nu, x):
+    f = lib().or_bessel_K
+    return np.vectorize(lambda xx: f(float(nu), float(xx)), otypes=[float])(x)
+
+
+def int_K13(x):
+    f = lib().or_int_K13
+    return np.vectorize(lambda xx: f(float(xx)), otypes=[float])(x)
+
+
+def F_gamma(u, chi, omu=None):
+    """Eq. 2 bracket (positive reading) at photon fraction u."""
+    f = lib().or_F_gamma
+    u = np.asarray(u, dtype=float)
+    omu = 1.0 - u if omu is None else np.asarray(omu, dtype=float)
+    return np.vectorize(lambda a, b: f(float(a), float(b), float(chi)), otypes=[float])(u, omu)
+
+
+def F_pair(v, chi, omv=None):
+    f = lib().or_F_pair
+    v = np.asarray(v, dtype=float)
+    omv = 1.0 - v if omv is None else np.asarray(omv, dtype=float)
+    return np.vectorize(lambda a, b: f(float(a), float(b), float(chi)), otypes=[float])(v, omv)
+
+
+def H_exact(chi):
+    return np.vectorize(lambda c: lib().or_H_exact(float(c)), otypes=[float])(chi)
+
+
+def G_exact(chi):
+    return np.vectorize(lambda c: lib().or_G_exact(float(c)), otypes=[float])(chi)
+
+
+def T_exact(chi):
+    return np.vectorize(lambda c: lib().or_T_exact(float(c)), otypes=[float])(chi)
+
+
+def cdf_gamma_exact(s, chi):
+    """Eq. 7 CDF at the photon fraction with logit s."""
+    return np.vectorize(lambda a: lib().or_cdf_gamma_exact(float(a), float(chi)),
+                        otypes=[float])(s)
+
+
+def cdf_pair_exact(s, chi):
+    return np.vectorize(lambda a: lib().or_cdf_pair_exact(float(a), float(chi)),
+                        otypes=[float])(s)
+
+
+# ---------------------------------------------------------------- tables
+
+class Tables:
+    """The oracle's own rate and CDF tables (built from its own quadrature)."""
+
+    def __init__(self):
+        n = lib().or_tables_size()
+        self._buf = np.zeros(n // 8, dtype=np.float64)
+        lib().or_tables_build(self.ptr)
+        b = self._buf
+        off = 0
+
+        def take(k):
+            nonlocal off
+            a = b[off:off + k]
+            off += k
+            return a
+        self.chi, self.H, self.Gs, self.Ts = take(NRATE), take(NRATE), take(NRATE), take(NRATE)
+        self.chic = take(NCDF)
+        self.sg, self.ug, self.sp, self.vp = take(NS), take(NS), take(NS), take(NS)
+        self.Cg = take(NCDF * NS).reshape(NCDF, NS)
+        self.Cp = take(NCDF * NS).reshape(NCDF, NS)
+        assert off * 8 == n
+
+    @property
+    def ptr(self):
+        return self._buf.ctypes.data_as(C.c_void_p)
+
+    def lookup(self, which: int, chi: float):
+        cl = C.c_int(0)
+        v = lib().or_lookup_rate(self.ptr, which, float(chi), C.byref(cl))
+        return v, bool(cl.value)
+
+    def sample_gamma(self, chi: float, xi: float) -> float:
+        cl = C.c_int(0)
+        return lib().or_sample_gamma(self.ptr, float(chi), float(xi), C.byref(cl))
+
+    def sample_pair(self, chi: float, xi: float) -> float:
+        cl = C.c_int(0)
+        return lib().or_sample_pair(self.ptr, float(chi), float(xi), C.byref(cl))
+
+
+_tables_cache = None
+
+
+def tables() -> Tables:
+    """Process-wide oracle tables (built once, a few seconds)."""
+    global _tables_cache
+    if _tables_cache is None:
+        _tables_cache = Tables()
+    return _tables_cache
+
+
+# ---------------------------------------------------------------- RNG
+
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def u53(a: int, b: int) -> float:
+    return lib().or_u53(a & 0xFFFFFFFF, b & 0xFFFFFFFF)
+
+
+def draw(seed, species, purpose, slot, step, k=0):
+    o = (C.c_uint32 * 4)()
+    lib().or_draw(int(seed), int(species), int(purpose), int(slot), int(step), int(k), o)
+    return [int(v) for v in o]
+
+
+# ---------------------------------------------------------------- fields, push, chi
+
+def plane_field(a0: float) -> Field:
+    f = Field()
+    f.kind, f.a0 = FIELD_PLANE, a0
+    return f
+
+
+def gaussian_field(a0, w0, tau_fwhm, x_focus, t_focus) -> Field:
+    f = Field()
+    f.kind, f.a0, f.w0, f.tau_fwhm = FIELD_GAUSSIAN, a0, w0, tau_fwhm
+    f.x_focus, f.t_focus = x_focus, t_focus
+    return f
+
+
+def uniform_b_field(b0: float) -> Field:
+    f = Field()
+    f.kind, f.b0 = FIELD_UNIFORM_B, b0
+    return f
+
+
+def yee2d_field(comps, dx, dy, x0=0.0, y0=0.0) -> Field:
+    """comps: 6 float32 arrays (Ex Ey Ez Bx By Bz) of shape (ny, nx)."""
+    f = Field()
+    f.kind = FIELD_YEE2D
+    keep = [np.ascontiguousarray(c, dtype=np.float32) for c in comps]
+    ny, nx = keep[0].shape
+    for k, c in enumerate(keep):
+        f.yee[k] = c.ctypes.data
+    f.nx, f.ny, f.dx, f.dy, f.x0, f.y0 = nx, ny, dx, dy, x0, y0
+    f._keep = keep  # keep the arrays alive
+    return f
+
+
+def field_eval(field: Field, x, y, z, t):
+    E = np.zeros(3)
+    B = np.zeros(3)
+    lib().or_field_eval(C.byref(field), float(x), float(y), float(z), float(t), _ptr(E), _ptr(B))
+    return E, B
+
+
+def chi_e(E, B, u, gamma, a_S):
+    return lib().or_chi_e(_ptr(_vec(E)), _ptr(_vec(B)), _ptr(_vec(u)), float(gamma), float(a_S))
+
+
+def chi_gamma(E, B, u, a_S):
+    return lib().or_chi_gamma(_ptr(_vec(E)), _ptr(_vec(B)), _ptr(_vec(u)), float(a_S))
+
+
+def boris(q, dt, E, B, u):
+    uu = _vec(u).copy()
+    lib().or_boris(float(q), float(dt), _ptr(_vec(E)), _ptr(_vec(B)), _ptr(uu))
+    return uu
+
+
+# ---------------------------------------------------------------- species and runs
+
+class Species:
+    """SoA state of one species in FP64 numpy arrays with a slot capacity."""
+
+    NAMES = ("x", "y", "z", "ux", "uy", "uz", "tau", "w")
+
+    def __init__(self, cap: int, dims: int = 3, track: bool = True):
+        self.cap, self.dims, self.n = int(cap), dims, 0
+        for nm in self.NAMES:
+            if nm == "z" and dims == 2:
+                setattr(self, nm, None)
+            else:
+                setattr(self, nm, np.zeros(self.cap))
+        self.chi = np.zeros(self.cap) if track else None
+        self.margin = np.full(self.cap, np.inf) if track else None
+        self.nemit = np.zeros(self.cap, dtype=np.int32) if track else None
+
+    @classmethod
+    def from_arrays(cls, arrays: dict, cap: int, dims: int = 3, track: bool = True):
+        n = len(arrays["x"])
+        s = cls(max(cap, n), dims, track)
+        for nm in cls.NAMES:
+            if nm in arrays and getattr(s, nm) is not None:
+                getattr(s, nm)[:n] = np.asarray(arrays[nm], dtype=np.float64)
+        s.n = n
+        return s
+
+    def _struct(self):
+        st = _Species()
+        st.n, st.cap = self.n, self.cap
+        for nm in self.NAMES + ("chi", "margin", "nemit"):
+            a = getattr(self, nm)
+            setattr(st, nm, None if a is None else a.ctypes.data)
+        return st
+
+    def live(self, nm):
+        a = getattr(self, nm)
+        return None if a is None else a[:self.n]
+
+
+def init_tau(seed: int, species: int, sp: Species, first: int = 0, last: int | None = None):
+    last = sp.n if last is None else last
+    lib().or_init_tau(int(seed), int(species), sp.tau.ctypes.data_as(C.c_void_p), first, last)
+
+
+class Sim:
+    """A run of the oracle: units, tables, field, parameters and three species."""
+
+    def __init__(self, field: Field, params: dict, electrons: Species | None = None,
+                 positrons: Species | None = None, photons: Species | None = None,
+                 lambda_m: float = 0.8e-6, table: Tables | None = None):
+        self.U = units(lambda_m)
+        self.T = table if table is not None else tables()
+        self.field = field
+        self.P = Params()
+        self.P.dt = params["dt"]
+        self.P.step = int(params.get("step", 0))
+        self.P.seed = int(params.get("seed", 0))
+        self.P.chi_th = float(params.get("chi_th", 0.0))
+        self.P.photon_min_gamma = float(params.get("photon_min_gamma", 2.0))
+        self.P.pairs = int(bool(params.get("pairs", False)))
+        self.P.max_emit = int(params.get("max_emit", 8))
+        self.P.recoil = int(params.get("recoil", 1))
+        self.P.dims = int(params.get("dims", 3))
+        self.sp = [electrons, positrons, photons]
+        self.stats = Stats()
+
+    def run(self, n_steps: int):
+        structs = [s._struct() if s is not None else None for s in self.sp]
+        ptrs = [C.byref(s) if s is not None else None for s in structs]
+        lib().or_run(C.byref(self.U), self.T.ptr, C.byref(self.field), C.byref(self.P),
+                     int(n_steps), ptrs[0], ptrs[1], ptrs[2], C.byref(self.stats))
+        for s, st in zip(self.sp, structs):
+            if s is not None:
+                s.n = st.n
+        self.P.step += int(n_steps)
+
+    def count_events_frozen(self, chi, gam, dt, n_steps, seed, max_emit=8):
+        return lib().or_count_events_frozen(C.byref(self.U), self.T.ptr, float(chi), float(gam),
+                                            float(dt), int(n_steps), int(seed), int(max_emit))
