@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the QED particle step on GB300.
+
+Default workload: the 2D laser-on-foil case (2048x512 Yee grid, 131072 e-,
+fixed Gaussian-pulse fields, Sokolov below chi 1e-3, Monte-Carlo above,
+photons and pairs tracked), run on the mixed-precision path (the headline
+`value`) and on the FP64 path (`fp64`) on the same GPU.  A step is one
+qp_step (step-begin, lepton and photon kernels) over every live particle;
+K steps are timed from the initial state (K = 500 is the whole job).
+L2 is flushed (256 MB write) between timed steps; each step is timed with
+CUDA events on its stream; clocks are sampled with nvidia-smi meanwhile.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload foil|collision|plane]
+
+Under torchrun each rank runs an independent replica (seed = rank) on its
+own GPU: weak scaling with no collective in the data path; the barrier and
+the max over ranks of the timed region come from torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "QED particle-steps/s, mixed vs FP64 on same GPU; p50/p99 request latency"
+UNIT = "particle-steps/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=500)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--workload", choices=("foil", "collision", "plane"), default="foil")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=100)
+    return p.parse_args()
+
+
+def workload(name: str, seed: int):
+    from paper_1311_1107_gb300 import workloads as W
+    if name == "foil":
+        return W.laser_on_foil(seed=seed)
+    if name == "collision":
+        return W.beam_collision(seed=seed)
+    return W.plane_wave_collision(seed=seed)
+
+
+# ----------------------------------------------------------------------------- bytes model
+
+def species_bytes(dims: int, pairs: bool):
+    """Algorithmic HBM bytes: per lepton slot-step (x, u, tau read and
+    written), per photon slot-step (x, u, tau read; x and, with pairs, tau
+    written), per appended particle (its 7-8 arrays) and per emitting parent
+    (its weight)."""
+    pos = 8 * dims
+    lep = 2 * (pos + 24 + 8)
+    pho = pos + 24 + 8 + pos + (8 if pairs else 0)
+    new = pos + 24 + 8 + 8
+    return lep, pho, new
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU path
+
+def run_path(w, precision, steps, warmup, dev, dist, flush):
+    import torch
+
+    from paper_1311_1107_gb300 import qedpic as Q
+    from paper_1311_1107_gb300.sim import Simulation
+    from paper_1311_1107_gb300.workloads import LAMBDA_M
+
+    ctx = Q.qp_init_tables(LAMBDA_M, dev)
+    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False)
+    stream = torch.cuda.current_stream()
+    # warm-up steps on the initial state, then back to the initial state
+    for _ in range(warmup):
+        flush.zero_()
+        sim.run(1)
+    torch.cuda.synchronize()
+    sim.load_initial()
+    torch.cuda.synchronize()
+    names = ("electron", "positron", "photon")
+    counts = torch.zeros((steps, 3), dtype=torch.int64, device=f"cuda:{dev}")
+    live = [sim.species[n].n_live for n in names]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    Q.qp_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        torch.cat(live, out=counts[k])       # live slots at the start of the step
+        ev[k][0].record(stream)
+        sim.run(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms, launches = Q.qp_profile_read(ctx)
+    Q.qp_profile_enable(ctx, False)
+    c = counts.cpu().numpy()
+    diag = {n: sim.diagnostics(n) for n in names}
+    lep_slots = int(c[:, 0].sum() + c[:, 1].sum())
+    pho_slots = int(c[:, 2].sum())
+    res = {
+        "ctx": ctx, "sim": sim, "step_ms": step_ms, "kernel_ms": ms, "launches": launches,
+        "lep_slots": lep_slots, "pho_slots": pho_slots, "wall_s": wall,
+        "photons_added": int(sum(diag[n].n_photon for n in ("electron", "positron"))),
+        "pairs_added": int(diag["photon"].n_pair - diag["photon"].n_pair_drop),
+        "emitters": int(sum(diag[n].n_emit for n in ("electron", "positron"))),
+        "final_live": {n: int(sim.species[n].count()) for n in names},
+        "status": min(d.status for d in diag.values()),
+    }
+    return res
+
+
+def roofline(res, dims, pairs, hbm_peak, peak_kind):
+    lep_b, pho_b, new_b = species_bytes(dims, pairs)
+    lep_bytes = res["lep_slots"] * lep_b + res["photons_added"] * new_b
+    pho_bytes = res["pho_slots"] * pho_b + 2 * res["pairs_added"] * new_b
+    ms = res["kernel_ms"]
+    cand = []
+    if ms[1] > 0:
+        cand.append(("k_lepton", lep_bytes, ms[1], res["launches"][1]))
+    if ms[2] > 0:
+        cand.append(("k_photon", pho_bytes, ms[2], res["launches"][2]))
+    name, b, t, n = max(cand, key=lambda x: x[2])
+    achieved = b / (t * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+            "bytes_per_launch": round(b / max(n, 1)), "avg_launch_us": round(t * 1e3 / max(n, 1), 3),
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s", "kernel_share": {
+                "k_step_begin": round(ms[0] / sum(ms), 4), "k_lepton": round(ms[1] / sum(ms), 4),
+                "k_photon": round(ms[2] / sum(ms), 4)}}
+
+
+def e2e(w, precision, steps, dev):
+    """End to end through the public API with host buffers: every step copies
+    the live particles from pinned host memory to the device, runs qp_step,
+    and reads the new state and live counts back."""
+    import torch
+
+    from paper_1311_1107_gb300 import qedpic as Q
+    from paper_1311_1107_gb300.sim import Simulation
+    from paper_1311_1107_gb300.workloads import LAMBDA_M
+
+    ctx = Q.qp_init_tables(LAMBDA_M, dev)
+    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False)
+    names = ("electron", "positron", "photon")
+    host = {}
+    for n in names:
+        sp = sim.species[n]
+        host[n] = {k: torch.empty(max(sp.cap, 1), dtype=torch.float64, pin_memory=True)
+                   for k in sp.t}
+    counts_h = torch.empty(3, dtype=torch.int64, pin_memory=True)
+    live = {n: sim.species[n].count() for n in names}
+    for n in names:
+        for k, t in sim.species[n].t.items():
+            host[n][k][:live[n]].copy_(t[:live[n]])
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    total_slots = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for n in names:
+            sp = sim.species[n]
+            m = live[n]
+            for k, t in sp.t.items():
+                if m:
+                    t[:m].copy_(host[n][k][:m], non_blocking=True)
+                    h2d += m * 8
+            sp.n_live.fill_(m)
+        total_slots += sum(live.values())
+        sim.run(1)
+        counts_h.copy_(torch.cat([sim.species[n].n_live for n in names]))
+        d2h += 24
+        live = dict(zip(names, (int(v) for v in counts_h.tolist())))
+        for n in names:
+            sp = sim.species[n]
+            m = live[n]
+            for k, t in sp.t.items():
+                if m:
+                    host[n][k][:m].copy_(t[:m], non_blocking=True)
+                    d2h += m * 8
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    Q.qp_destroy(ctx)
+    return {"value": round(total_slots / wall, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
+            "steps": steps, "precision": precision}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, n_sample: int, n_steps: int):
+    """Time the CPU oracle (single thread) on a bounded sample of the
+    workload: n_sample electrons (evenly spaced slots, each with its own
+    random stream) for n_steps steps."""
+    import oracle as O
+    from tests.parity import oracle_field
+
+    n_all = len(w["electrons"]["x"])
+    idx = np.linspace(0, n_all - 1, min(n_sample, n_all)).astype(np.int64)
+    sub = {k: np.asarray(v)[idx] for k, v in w["electrons"].items()}
+    dims = w["dims"]
+    el = O.Species.from_arrays(sub, len(idx) * 4 + 64, dims, track=False, ids=idx)
+    tau = np.zeros(n_all)
+    O.lib().or_init_tau(int(w["params"]["seed"]), O.ELECTRON, tau.ctypes.data_as(O.C.c_void_p), 0,
+                        n_all)
+    el.tau[:len(idx)] = tau[idx]
+    po = O.Species(len(idx) * 4 + 64, dims, track=False)
+    ph = O.Species(len(idx) * 256 + 64, dims, track=False)
+    O.tables()
+    sim = O.Sim(oracle_field(w["field"]), w["params"], electrons=el, positrons=po, photons=ph)
+    slots = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        slots += el.n + po.n + ph.n
+        sim.run(1)
+    dt = time.perf_counter() - t0
+    return slots, dt, len(idx)
+
+
+def cpu_baseline(w, args):
+    slots, dt, n = oracle_sample(w, 16384 if args.workload != "collision" else 4096,
+                                 min(args.steps, 200))
+    return {"value": round(slots / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} electrons (evenly spaced slots) for {min(args.steps, 200)} steps "
+                      f"of the same workload, FP64 oracle, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as D
+        torch.cuda.set_device(local)
+        D.init_process_group("nccl")
+        dist = D
+    return world, rank, local, dist
+
+
+def reference_arm(args):
+    world, rank, _, dist = dist_setup(args)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    w = workload(args.workload, 0)
+    n_sample = 16384 if args.workload != "collision" else 4096
+    slots_w, dt_w, _ = oracle_sample(w, n_sample, args.warmup)
+    slots, dt, n = oracle_sample(w, n_sample, args.steps)
+    v = slots / dt
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "sample": f"{n} electrons"},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} evenly spaced electrons of the workload, "
+                                       f"{args.steps} steps, single thread"},
+            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def ours_arm(args):
+    import torch
+
+    world, rank, local, dist = dist_setup(args)
+    dev = local
+    torch.cuda.set_device(dev)
+    w = workload(args.workload, rank)
+    dims = w["dims"]
+    pairs = bool(w["params"].get("pairs", False))
+    hbm_peak, peak_kind = peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    mixed = run_path(w, "mixed", args.steps, args.warmup, dev, dist, flush)
+    fp64 = run_path(w, "fp64", args.steps, args.warmup, dev, dist, flush)
+    clk = clocks.stop()
+
+    def agg(res):
+        t_ms = sum(res["step_ms"])
+        slots = res["lep_slots"] + res["pho_slots"]
+        if dist:
+            tt = torch.tensor([t_ms], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ss = torch.tensor([slots], dtype=torch.float64, device=f"cuda:{dev}")
+            dist.all_reduce(ss, op=dist.ReduceOp.SUM)
+            t_ms, slots = float(tt.item()), float(ss.item())
+        return slots / (t_ms * 1e-3), t_ms
+
+    v_mixed, t_mixed = agg(mixed)
+    v_fp64, t_fp64 = agg(fp64)
+    line = None
+    if rank == 0:
+        e2e_res = None
+        if not args.no_e2e:
+            e2e_res = e2e(w, "mixed", min(args.e2e_steps, args.steps), dev)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(w, args)
+        launches = int(sum(mixed["launches"]))
+        line = {
+            "metric": METRIC, "value": round(v_mixed, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_mixed / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed path)",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "precision": "mixed",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "particle_steps": "live slots of e-, e+ and photons at each step start",
+                       "steps_timed": "steps 0..K-1 of the job from the initial state",
+                       "final_live": mixed["final_live"], "parallelism": f"replicas x{world}"},
+            "fp64": {"value": round(v_fp64, 1), "unit": UNIT,
+                     "ms_per_step": round(t_fp64 / args.steps, 4), "dtype": "f64",
+                     "roofline": roofline(fp64, dims, pairs, hbm_peak, peak_kind),
+                     "mixed_over_fp64": round(v_mixed / v_fp64, 3),
+                     "final_live": fp64["final_live"]},
+            "roofline": roofline(mixed, dims, pairs, hbm_peak, peak_kind),
+            "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
+            "clocks": clk, "status": {"mixed": mixed["status"], "fp64": fp64["status"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,285 @@
+/*
+ * qedpic.h -- C ABI of the GB300 QED particle-step library (libqedpic.so).
+ *
+ * The library advances super-particles (electrons, positrons, photons) of a
+ * particle-in-cell simulation through one or more steps of the radiative and
+ * QED model of Lobet et al., "Modeling of radiative and quantum
+ * electrodynamics effects in PIC simulations of ultra-relativistic
+ * laser-plasma interaction" (arXiv:1311.1107):
+ *   - field gather (analytic laser, constant B, or a fixed 2D Yee grid);
+ *   - Boris push of the Lorentz force, with Sokolov radiation damping below a
+ *     quantum-parameter threshold (section 3, Eq. 4 and Eq. 5);
+ *   - Lorentz-invariant quantum parameters chi_e, chi_gamma (section 2, Eq. 1);
+ *   - optical-depth decrement against tabulated nonlinear-Compton and
+ *     Breit-Wheeler rates (Eq. 2, Eq. 3, Eq. 6);
+ *   - inverse-CDF sampling of photon and pair energies (Eq. 7), collinear
+ *     recoil (Eq. 8), pair creation at the photon position (section 3);
+ *   - deterministic, slot-ordered append of new photons, electrons and
+ *     positrons to caller-owned device buffers.
+ *
+ * Conventions
+ *   - Every function returns an int status: QP_OK (0), a warning (> 0) or an
+ *     error (< 0).  qp_status_string() names it.
+ *   - All particle arrays and counters are DEVICE pointers owned by the
+ *     caller; the library never frees caller memory.  Tables, scan scratch
+ *     and status flags are owned by the context.
+ *   - Streams are passed as `void *` holding a cudaStream_t (NULL = legacy
+ *     default stream).  qp_step and qp_init_optical_depth are asynchronous on
+ *     that stream; qp_diagnostics synchronises it.
+ *   - Units are normalised at the context's reference wavelength lambda:
+ *     time in 1/omega (omega = 2 pi c / lambda), length in c/omega, momentum
+ *     u = p/(m c), E in m c omega / e, B in m omega / e.  One laser period is
+ *     2 pi.
+ *   - Storage is FP64 structure-of-arrays, one array per component, each at
+ *     least `capacity` elements, 8-byte aligned (256-byte alignment gives the
+ *     best coalescing).  Slot i of every array belongs to particle i; slots
+ *     [0, *n_live) are live.  A photon with tau < 0 has decayed into a pair
+ *     and is skipped; leptons are never removed.
+ *   - Random numbers come from Philox4x32-10 keyed by (seed) with counter
+ *     (slot, step, species/purpose/emission index), so results do not depend
+ *     on the launch configuration and a run can be resumed at any step.
+ */
+#ifndef QEDPIC_H
+#define QEDPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QP_OK 0
+#define QP_WARN_BUFFER_FULL 1      /* particles dropped: an append buffer is full   */
+#define QP_WARN_TABLE_CLAMPED 2    /* chi above the table range (2^10) was clamped  */
+#define QP_ERR_INVALID_ARG (-1)    /* rejected before anything was enqueued         */
+#define QP_ERR_CUDA (-2)           /* a CUDA runtime call failed                    */
+#define QP_ERR_OOM (-3)            /* device allocation failed                      */
+#define QP_ERR_NOT_INITIALIZED (-4)/* NULL or destroyed context, unknown handle     */
+#define QP_ERR_TIMEOUT (-5)        /* a bounded device-side wait gave up            */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { QP_ELECTRON = 0, QP_POSITRON = 1, QP_PHOTON = 2 };
+enum { QP_FP64 = 0, QP_MIXED = 1 };
+enum {
+    QP_FIELD_NONE = 0,      /* E = B = 0                                         */
+    QP_FIELD_PLANE = 1,     /* E_y = B_z = a0 cos(t - x)                         */
+    QP_FIELD_GAUSSIAN = 2,  /* paraxial Gaussian pulse along +x, polarised y     */
+    QP_FIELD_YEE2D = 3,     /* fixed FP32 Yee grid, linear interpolation         */
+    QP_FIELD_UNIFORM_B = 4  /* B = b0 z^ (the paper's section 4 test)            */
+};
+#define QP_MAX_EMISSIONS 8  /* upper bound of qp_step_params.max_emissions     */
+#define QP_HIST_BINS 64     /* diagnostic spectrum bins in log10(gamma)        */
+#define QP_HIST_LOG10_MIN (-1.0)
+#define QP_HIST_LOG10_MAX (5.0)
+
+typedef struct qp_ctx qp_ctx;
+
+/* ---- qp_init_tables ---------------------------------------------------- */
+typedef struct {
+    double lambda_m;   /* reference wavelength [m] that fixes the units (> 0) */
+    int32_t device;    /* CUDA device ordinal the context lives on            */
+    int32_t reserved;  /* must be 0                                           */
+} qp_table_params;
+
+/*
+ * Create a context on `p->device`: build, in FP64 on the host, the tables of
+ * the rates and CDFs that Eq. 2 and Eq. 3 define, and upload FP64 and FP32
+ * copies.  Grids (a specification shared with the test oracle):
+ *   rate tables  H(chi)=int_0^1 F_gamma du, G(chi)/chi with
+ *                G=int_0^1 u F_gamma du (Eq. 5), T(chi) exp(8/(3 chi)) with
+ *                T=int_0^1 F_pm dv, at chi_j = 2^(-14+j/32)(1+(j mod 32)/32),
+ *                j = 0..768, linear interpolation in chi;
+ *   CDF tables   Eq. 7 rows at chi_j = 2^(-14+j/4)(1+(j mod 4)/4), j = 0..96,
+ *                on 256 logit nodes of u (-30..20) and of v (-20..20).
+ * Also allocates the context's scan scratch and status flags.
+ * Returns QP_ERR_INVALID_ARG for bad arguments, QP_ERR_CUDA / QP_ERR_OOM on
+ * device failure (nothing is leaked; *out_ctx is left NULL).
+ */
+int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx);
+
+/* Release everything the context owns (not the caller's buffers).  Safe on
+ * NULL.  The caller must make sure no step is still running on its streams. */
+int qp_destroy(qp_ctx *ctx);
+
+/* ---- qp_create_species ------------------------------------------------- */
+typedef struct {
+    int32_t kind;       /* QP_ELECTRON, QP_POSITRON or QP_PHOTON                 */
+    int32_t dims;       /* 3 (x, y, z) or 2 (x, y; z must be NULL)               */
+    int64_t capacity;   /* slots in every array below (>= 0)                     */
+    double *x, *y, *z;  /* positions                                             */
+    double *ux, *uy, *uz; /* momenta p/(m c); photons: |u| = gamma_gamma         */
+    double *tau;        /* remaining optical depth (tau_f - tau of Eq. 6)        */
+    double *w;          /* super-particle weight                                 */
+    double *chi;        /* optional (may be NULL): chi of the particle's last
+                           step (chi_e, or chi_gamma for photons above 2 m c^2)  */
+    int64_t *n_live;    /* device counter of live slots; the library updates it
+                           when it appends; the caller sets its initial value    */
+} qp_species_desc;
+
+/*
+ * Register a species' caller-owned device buffers with the context
+ * (super-particles of section 3: weight, position, momentum) and return a
+ * handle (>= 0).  Nothing is copied or enqueued.  QP_ERR_INVALID_ARG if a
+ * required pointer is NULL, dims is not 2 or 3, or z is given for dims 2.
+ */
+int qp_create_species(qp_ctx *ctx, const qp_species_desc *d, int32_t *out_handle);
+
+/*
+ * Draw the final optical depth tau_f = -log(xi), xi in ]0,1] (section 3,
+ * after Eq. 6), for slots [first, first + count) of a species, from the
+ * Philox stream (seed, slot, purpose "initial").  Asynchronous on `stream`.
+ */
+int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t first,
+                          int64_t count, void *stream);
+
+/* ---- qp_step ----------------------------------------------------------- */
+typedef struct {
+    int32_t kind;         /* QP_FIELD_*                                         */
+    int32_t reserved;
+    double a0;            /* PLANE, GAUSSIAN: peak normalised amplitude           */
+    double w0;            /* GAUSSIAN: waist (1/e field radius at focus)          */
+    double tau_fwhm;      /* GAUSSIAN: FWHM duration of the intensity             */
+    double x_focus;       /* GAUSSIAN: focal plane                                */
+    double t_focus;       /* GAUSSIAN: time the envelope peak crosses x_focus     */
+    double b0;            /* UNIFORM_B: B_z                                       */
+    const float *yee[6];  /* YEE2D: device Ex Ey Ez Bx By Bz, ny rows of nx values;
+                             staggering Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j)
+                             Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2)              */
+    int64_t nx, ny;       /* YEE2D: nodes per row, rows                           */
+    double dx, dy;        /* YEE2D: cell size                                     */
+    double x0, y0;        /* YEE2D: position of node (0,0)                        */
+} qp_field;
+
+typedef struct {
+    qp_field field;
+    double dt;               /* time step (> 0)                                   */
+    int64_t step;            /* index n of the first step; fields at t = n dt     */
+    int32_t n_steps;         /* steps to run (>= 0)                               */
+    int32_t precision;       /* QP_FP64 or QP_MIXED                               */
+    uint64_t seed;           /* Philox key                                        */
+    double chi_threshold;    /* Sokolov (continuous) regime below, MC above      */
+    double photon_min_gamma; /* super-photons stored only above this energy (2)  */
+    int32_t pairs;           /* 1 = photons above 2 m c^2 may create pairs        */
+    int32_t max_emissions;   /* 1..QP_MAX_EMISSIONS emissions per particle-step   */
+    int32_t electron;        /* species handles, -1 = absent                      */
+    int32_t positron;
+    int32_t photon;
+    int32_t reserved;
+} qp_step_params;
+
+/*
+ * Advance the species named in `s` by s->n_steps steps, asynchronously on
+ * `stream`.  Per step n, in this order:
+ *   electrons then positrons, slots [0, n_live at the start of the step):
+ *     gather E, B at x^n, t^n; Boris u^(n-1/2) -> u^(n+1/2); chi_e (Eq. 1);
+ *     chi_e < chi_threshold: Sokolov damping (Eq. 4, P_rad of Eq. 5);
+ *     otherwise tau -= W dt (Eq. 6) with a residual-time sub-loop: on
+ *     tau <= W dt an emission at chi_gamma = u chi_e with u from Eq. 7,
+ *     collinear recoil (Eq. 8), a super-photon appended if gamma_gamma >
+ *     photon_min_gamma, tau = -log(xi), and the rest of the step continues;
+ *     x^(n+1) = x^n + (v + delta_v) dt.
+ *   photons existing at the start of the step (tau >= 0): chi_gamma (Eq. 1);
+ *     above 2 m c^2 with pairs on, tau -= W_pm dt; on decay the photon gets
+ *     tau = -1 and an electron and a positron are appended at its position
+ *     with v = chi_-/chi_gamma from the pair CDF; otherwise x += c k^ dt.
+ * Appended particles fill slots [n_live, ...) in the order of their parent's
+ * slot (then emission index); photons emitted by electrons precede those of
+ * positrons.  Particles that do not fit are counted as dropped and their
+ * energy recorded; the step still completes.  No allocation, no host
+ * synchronisation, no host reads: the call can be captured in a CUDA graph.
+ * Returns QP_ERR_INVALID_ARG (nothing enqueued) for bad parameters, a
+ * missing photon species while species emit, or a YEE2D grid with a NULL
+ * component; QP_ERR_CUDA if a launch fails.  Overflow, table clamping and
+ * wait time-outs are reported by the next qp_diagnostics.
+ */
+int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream);
+
+/* ---- qp_diagnostics ---------------------------------------------------- */
+typedef struct {
+    int64_t n_live;          /* live slots                                         */
+    int64_t n_alive;         /* slots with tau >= 0                                */
+    double weight;           /* sum w over alive slots                             */
+    double energy;           /* sum w gamma (leptons) or w |u| (photons), m c^2    */
+    double px, py, pz;       /* sum w u                                            */
+    double chi_mean;         /* w-weighted mean chi (0 if no chi array)            */
+    double hist[QP_HIST_BINS]; /* w-weighted histogram of log10(gamma) over
+                                  [QP_HIST_LOG10_MIN, QP_HIST_LOG10_MAX); out-of-
+                                  range values go to the first / last bin          */
+    /* counters accumulated by qp_step since the species was created, for the
+       events this species caused (emissions for leptons, pairs for photons) */
+    int64_t n_emit;          /* emission events                                    */
+    int64_t n_photon;        /* super-photons appended                             */
+    int64_t n_photon_drop;   /* super-photons that did not fit                     */
+    int64_t n_subthreshold;  /* emissions below photon_min_gamma                   */
+    int64_t n_pair;          /* pair events                                        */
+    int64_t n_pair_drop;     /* pairs that did not fit                             */
+    int64_t n_saturated;     /* particle-steps that reached max_emissions          */
+    int64_t n_clamped;       /* particle-steps with chi above the table range      */
+    int64_t n_continuous;    /* particle-steps in the Sokolov regime               */
+    double e_subthreshold;   /* sum w gamma_gamma of photons below the cut         */
+    double e_dropped;        /* sum w gamma of particles that did not fit          */
+    int32_t status;          /* sticky context status (QP_OK or the first error
+                                or warning raised on the device)                   */
+    int32_t reserved;
+} qp_diag;
+
+/*
+ * Reduce a species' state in a fixed order (the result does not depend on
+ * the launch or on timing) into `out`, on `stream`, and synchronise it.
+ * These are the quantities of the paper's Fig. 1 and Fig. 2 captions: total
+ * energy, number (weight), mean quantum parameter and energy spectrum.  The
+ * returned status is out->status when the call itself succeeded.
+ */
+int qp_diagnostics(qp_ctx *ctx, int32_t handle, qp_diag *out, void *stream);
+
+/* ---- qp_export_tables -------------------------------------------------- */
+#define QP_NRATE 769
+#define QP_NCDF 97
+#define QP_NNODE 256
+typedef struct {
+    double H[QP_NRATE];             /* H(chi_j)                                  */
+    double Gs[QP_NRATE];            /* G(chi_j) / chi_j                          */
+    double Ts[QP_NRATE];            /* T(chi_j) exp(8/(3 chi_j)), 0 below 2^-8    */
+    double Cg[QP_NCDF * QP_NNODE];  /* emission CDF rows (Eq. 7)                  */
+    double Cp[QP_NCDF * QP_NNODE];  /* pair CDF rows                              */
+    double a_S;                     /* Schwinger field in normalised units        */
+    double C_rate;                  /* alpha / (sqrt(3) pi tau_c omega)           */
+    double tau0w;                   /* Sokolov tau_0 in units of 1/omega          */
+} qp_tables_export;
+
+/* Copy the context's FP64 tables and unit constants to host memory `out`
+ * (caller-owned).  Synchronous. */
+int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
+
+/* Reset the species' event counters and the context's sticky status. */
+int qp_reset_counters(qp_ctx *ctx, int32_t handle);
+
+/*
+ * Kernel timing for benchmarks.  While enabled, qp_step brackets each of its
+ * kernel launches with CUDA events recorded on the step's stream (events are
+ * owned by the context; enabling clears earlier records).
+ * qp_profile_read synchronises on the recorded events and returns, per
+ * kernel (0 step-begin, 1 lepton, 2 photon), the summed device time in ms
+ * and the number of launches.  No counterpart in the paper.
+ */
+int qp_profile_enable(qp_ctx *ctx, int enable);
+int qp_profile_read(qp_ctx *ctx, double ms[3], int64_t launches[3]);
+
+/*
+ * Self-test of the device-side failure detection: one look-back wait on a
+ * predecessor tile that never publishes, bounded by `spin_limit` sleeps of
+ * about 64 ns.  Returns the status the device raised (QP_ERR_TIMEOUT when the
+ * bound works) and clears the context's sticky status.  Synchronous; the
+ * context stays usable.  No counterpart in the paper (it tests the library).
+ */
+int qp_selftest_wait_timeout(qp_ctx *ctx, uint32_t spin_limit);
+
+/* Static, NUL-terminated name of a status code. */
+const char *qp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEDPIC_H */

@@ -67,7 +67,7 @@ class Field(C.Structure):
 class _Species(C.Structure):
     _fields_ = [("n", C.c_int64), ("cap", C.c_int64)] + [
         (name, C.c_void_p) for name in ("x", "y", "z", "ux", "uy", "uz", "tau", "w", "chi",
-                                        "margin", "nemit")]
+                                        "margin", "nemit", "ids")]
 
 
 class Params(C.Structure):
@@ -344,21 +344,27 @@ class Species:
         self.chi = np.zeros(self.cap) if track else None
         self.margin = np.full(self.cap, np.inf) if track else None
         self.nemit = np.zeros(self.cap, dtype=np.int32) if track else None
+        self.ids = None  # optional int64 slot numbers for the random streams
 
     @classmethod
-    def from_arrays(cls, arrays: dict, cap: int, dims: int = 3, track: bool = True):
+    def from_arrays(cls, arrays: dict, cap: int, dims: int = 3, track: bool = True,
+                    ids=None):
+        """ids: optional slot numbers (for sampled subsets of a population)."""
         n = len(arrays["x"])
         s = cls(max(cap, n), dims, track)
         for nm in cls.NAMES:
             if nm in arrays and getattr(s, nm) is not None:
                 getattr(s, nm)[:n] = np.asarray(arrays[nm], dtype=np.float64)
         s.n = n
+        if ids is not None:
+            s.ids = np.zeros(s.cap, dtype=np.int64)
+            s.ids[:n] = np.asarray(ids, dtype=np.int64)
         return s
 
     def _struct(self):
         st = _Species()
         st.n, st.cap = self.n, self.cap
-        for nm in self.NAMES + ("chi", "margin", "nemit"):
+        for nm in self.NAMES + ("chi", "margin", "nemit", "ids"):
             a = getattr(self, nm)
             setattr(st, nm, None if a is None else a.ctypes.data)
         return st

@@ -611,7 +611,8 @@ static double or_yee_component(const or_field *F, int c, double x, double y)
     for (int b = 0; b < 2; b++) {
         for (int a = 0; a < 2; a++) {
             double ii = fi + a, jj = fj + b;
-            if (ii < 0.0 || jj < 0.0 || ii >= (double)F->nx || jj >= (double)F->ny) continue;
+            /* written so that NaN positions fail the test too */
+            if (!(ii >= 0.0 && jj >= 0.0 && ii < (double)F->nx && jj < (double)F->ny)) continue;
             double wgt = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
             sum += wgt * (double)F->yee[c][(int64_t)jj * F->nx + (int64_t)ii];
         }
@@ -720,7 +721,12 @@ typedef struct {
     double *chi;      /* optional: chi of the last step per slot     */
     double *margin;   /* optional: smallest |tau - dtau| / dtau seen */
     int32_t *nemit;   /* optional: emissions per slot (cumulative)   */
+    int64_t *ids;     /* optional: the slot number each entry stands for
+                         in the random streams (default: its index);
+                         lets a test run a sample of a larger population */
 } or_species;
+
+static int64_t or_id(const or_species *S, int64_t i) { return S->ids ? S->ids[i] : i; }
 
 typedef struct {
     double dt;
@@ -778,6 +784,7 @@ static void or_append_photon(or_species *P, int64_t base, int64_t *ord, const do
     if (P->chi) P->chi[slot] = 0.0;
     if (P->margin) P->margin[slot] = INFINITY;
     if (P->nemit) P->nemit[slot] = 0;
+    if (P->ids) P->ids[slot] = slot;
     st->n_photon++;
 }
 
@@ -843,27 +850,38 @@ static void or_lepton_step(const or_units *U, const or_tables *T, const or_field
             }
             r = r - tau / wdt;
             uint32_t rr[4];
-            or_draw(P->seed, species, OR_RNG_EMIT, i, P->step, k, rr);
+            or_draw(P->seed, species, OR_RNG_EMIT, or_id(S, i), P->step, k, rr);
             double xi_p = or_u53(rr[0], rr[1]);   /* xi'  (Eq. 7) */
             double xi = or_u53(rr[2], rr[3]);     /* xi   (tau^f) */
             double ufrac = or_sample_gamma(T, chi, xi_p, &clamped);
             double pmag = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
             double gg = ufrac * gam;
             if (gg > pmag) gg = pmag; /* READING: photon cannot exceed |p| */
-            double khat[3] = {u[0] / pmag, u[1] / pmag, u[2] / pmag};
+            /* a particle at rest (|p| = 0) emits nothing: gg = 0, no recoil */
+            double khat[3] = {0.0, 0.0, 0.0};
+            if (pmag > 0.0) {
+                khat[0] = u[0] / pmag;
+                khat[1] = u[1] / pmag;
+                khat[2] = u[2] / pmag;
+            }
             st->n_emit++;
             if (S->nemit) S->nemit[i]++;
             if (gg > P->photon_min_gamma) {
                 uint32_t rp[4];
-                or_draw(P->seed, species, OR_RNG_PHOTON_TAU, i, P->step, k, rp);
+                or_draw(P->seed, species, OR_RNG_PHOTON_TAU, or_id(S, i), P->step, k, rp);
                 double tau_g = -log(or_u53(rp[0], rp[1]));
                 double ku[3] = {gg * khat[0], gg * khat[1], gg * khat[2]};
-                if (Ph) or_append_photon(Ph, ph_base, ph_ord, x, ku, S->w[i], tau_g, st, gg);
+                if (Ph) {
+                    or_append_photon(Ph, ph_base, ph_ord, x, ku, S->w[i], tau_g, st, gg);
+                } else {
+                    st->n_photon_drop++; /* no photon species: nowhere to store it */
+                    st->e_dropped += S->w[i] * gg;
+                }
             } else {
                 st->n_subthreshold++;
                 st->e_subthreshold += S->w[i] * gg;
             }
-            if (P->recoil) {
+            if (P->recoil && pmag > 0.0) {
                 /* Eq. 8: p_f = (|p| - eps_gamma/c) p/|p| */
                 double scale = (pmag - gg) / pmag;
                 u[0] *= scale;
@@ -902,6 +920,7 @@ static void or_append_lepton(or_species *S, int64_t slot, const double x[3], con
     if (S->chi) S->chi[slot] = 0.0;
     if (S->margin) S->margin[slot] = INFINITY;
     if (S->nemit) S->nemit[slot] = 0;
+    if (S->ids) S->ids[slot] = slot;
 }
 
 /* One step of one super-photon: ballistic motion at c along k, optical depth
@@ -932,8 +951,8 @@ static void or_photon_step(const or_units *U, const or_tables *T, const or_field
         if (dtau > 0.0 && !(tau > dtau)) {
             /* pair event: photon deleted, e- e+ created at its position */
             uint32_t r1[4], r2[4];
-            or_draw(P->seed, OR_SP_PHOTON, OR_RNG_PAIR, i, P->step, 0, r1);
-            or_draw(P->seed, OR_SP_PHOTON, OR_RNG_PAIR_POS, i, P->step, 0, r2);
+            or_draw(P->seed, OR_SP_PHOTON, OR_RNG_PAIR, or_id(Ph, i), P->step, 0, r1);
+            or_draw(P->seed, OR_SP_PHOTON, OR_RNG_PAIR_POS, or_id(Ph, i), P->step, 0, r2);
             double v = or_sample_pair(T, chi, or_u53(r1[0], r1[1]), &clamped);
             double tau_m = -log(or_u53(r1[2], r1[3]));
             double tau_p = -log(or_u53(r2[0], r2[1]));
@@ -956,7 +975,8 @@ static void or_photon_step(const or_units *U, const or_tables *T, const or_field
         }
         tau = tau - dtau;
     }
-    for (int c = 0; c < 3; c++) x[c] = x[c] + dt * (u[c] / g);
+    if (g > 0.0)
+        for (int c = 0; c < 3; c++) x[c] = x[c] + dt * (u[c] / g);
     Ph->x[i] = x[0];
     Ph->y[i] = x[1];
     if (Ph->z) Ph->z[i] = x[2];

@@ -1,0 +1,559 @@
+// C ABI of libqedpic: context, species registry, argument checks, launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "qedpic.h"
+#include "qp_internal.h"
+#include "qp_kernels.h"
+
+namespace {
+
+constexpr int kMaxSpecies = 4096;
+// Bound of every look-back wait (iterations of a ~64 ns sleep): about a
+// second, far above the time any predecessor tile needs.
+constexpr unsigned kSpinLimit = 1u << 24;
+
+struct SpeciesRec {
+    qp_species_desc d;
+};
+
+// FP64 tables are built once per process and shared by every context.
+std::mutex g_tab_mu;
+qp::HostTables *g_host_tables = nullptr;
+
+const qp::HostTables *host_tables()
+{
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (!g_host_tables) {
+        qp::HostTables *t = new (std::nothrow) qp::HostTables;
+        if (!t) return nullptr;
+        qp::build_tables_host(t);
+        g_host_tables = t;
+    }
+    return g_host_tables;
+}
+
+}  // namespace
+
+struct qp_ctx {
+    int device = 0;
+    int num_sms = 1;
+    double lambda_m = 0.0;
+    qp::Units U{};
+    // tables: FP64 H Gs Ts Cg Cp, then FP32 copies in the same order
+    double *d_tab64 = nullptr;
+    float *d_tab32 = nullptr;
+    qp::DevStats *d_stats = nullptr;  // [kMaxSpecies]
+    int64_t *d_n_start = nullptr;     // [3]
+    unsigned *d_tickets = nullptr;    // [2]
+    int *d_status = nullptr;
+    unsigned long long *d_chain = nullptr;  // lepton chain then photon chain
+    size_t chain_words = 0;           // words per chain
+    double *d_diag = nullptr;         // partials + final
+    std::vector<SpeciesRec> species;
+    int grid_cache[2][2][5];          // [precision][photon][field] blocks per SM, 0 = unknown
+    // kernel timing (qp_profile_*): event pool and (kernel, start event) records
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    std::vector<int> records;         // kernel id per recorded pair
+};
+
+namespace {
+
+constexpr size_t kTabRate = 3 * (size_t)qp::kNRate;
+constexpr size_t kTabCdf = 2 * (size_t)qp::kNCdf * qp::kNNode;
+constexpr size_t kTabWords = kTabRate + kTabCdf;
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return QP_OK;
+    if (e == cudaErrorMemoryAllocation) return QP_ERR_OOM;
+    return QP_ERR_CUDA;
+}
+
+void release(qp_ctx *c)
+{
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    cudaFree(c->d_tab64);
+    cudaFree(c->d_tab32);
+    cudaFree(c->d_stats);
+    cudaFree(c->d_n_start);
+    cudaFree(c->d_tickets);
+    cudaFree(c->d_status);
+    cudaFree(c->d_chain);
+    cudaFree(c->d_diag);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+// RAII switch to the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool valid_handle(const qp_ctx *c, int32_t h)
+{
+    return c && h >= 0 && (size_t)h < c->species.size();
+}
+
+// Make the look-back scratch large enough for `words` tiles per chain.
+int ensure_chain(qp_ctx *c, size_t words)
+{
+    if (words <= c->chain_words) return QP_OK;
+    unsigned long long *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, 2 * words * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemset(p, 0, 2 * words * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_status(e);
+    }
+    cudaFree(c->d_chain);
+    c->d_chain = p;
+    c->chain_words = words;
+    return QP_OK;
+}
+
+size_t tiles_of(int64_t cap) { return (size_t)((cap + qp::kTile - 1) / qp::kTile); }
+
+// Next free event of the profiling pool (grown on demand).
+cudaError_t next_event(qp_ctx *c, cudaEvent_t *ev)
+{
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        c->events.push_back(e);
+    }
+    *ev = c->events[c->events_used++];
+    return cudaSuccess;
+}
+
+// Launch one kernel of a step, bracketed by events when profiling.
+template <class F>
+cudaError_t timed(qp_ctx *c, int kernel_id, cudaStream_t st, F launch)
+{
+    if (!c->profiling) return launch();
+    cudaEvent_t a, b;
+    cudaError_t e = next_event(c, &a);
+    if (e == cudaSuccess) e = next_event(c, &b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) c->records.push_back(kernel_id);
+    return e;
+}
+
+qp::SpeciesDev species_dev(const qp_ctx *c, int32_t h)
+{
+    qp::SpeciesDev s{};
+    if (!valid_handle(c, h)) return s;
+    const qp_species_desc &d = c->species[h].d;
+    s.x = d.x;
+    s.y = d.y;
+    s.z = d.dims == 3 ? d.z : nullptr;
+    s.ux = d.ux;
+    s.uy = d.uy;
+    s.uz = d.uz;
+    s.tau = d.tau;
+    s.w = d.w;
+    s.chi = d.chi;
+    s.n_live = d.n_live;
+    s.cap = d.capacity;
+    s.present = 1;
+    s.slot_stats = h;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qp_status_string(int status)
+{
+    switch (status) {
+    case QP_OK: return "QP_OK";
+    case QP_WARN_BUFFER_FULL: return "QP_WARN_BUFFER_FULL";
+    case QP_WARN_TABLE_CLAMPED: return "QP_WARN_TABLE_CLAMPED";
+    case QP_ERR_INVALID_ARG: return "QP_ERR_INVALID_ARG";
+    case QP_ERR_CUDA: return "QP_ERR_CUDA";
+    case QP_ERR_OOM: return "QP_ERR_OOM";
+    case QP_ERR_NOT_INITIALIZED: return "QP_ERR_NOT_INITIALIZED";
+    case QP_ERR_TIMEOUT: return "QP_ERR_TIMEOUT";
+    default: return "QP_UNKNOWN_STATUS";
+    }
+}
+
+int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
+{
+    if (!out_ctx) return QP_ERR_INVALID_ARG;
+    *out_ctx = nullptr;
+    if (!p || !(p->lambda_m > 0.0) || !isfinite(p->lambda_m) || p->device < 0 || p->reserved != 0)
+        return QP_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device >= ndev) return QP_ERR_CUDA;
+    const qp::HostTables *T = host_tables();
+    if (!T) return QP_ERR_OOM;
+
+    qp_ctx *c = new (std::nothrow) qp_ctx;
+    if (!c) return QP_ERR_OOM;
+    memset(c->grid_cache, 0, sizeof(c->grid_cache));
+    c->device = p->device;
+    c->lambda_m = p->lambda_m;
+    qp::units_for_wavelength(p->lambda_m, &c->U);
+    DeviceGuard g(c->device);
+    if (!g.ok) {
+        delete c;
+        return QP_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms < 1) c->num_sms = 1;
+
+    std::vector<double> h64(kTabWords);
+    std::vector<float> h32(kTabWords);
+    memcpy(h64.data(), T->H, sizeof(T->H));
+    memcpy(h64.data() + qp::kNRate, T->Gs, sizeof(T->Gs));
+    memcpy(h64.data() + 2 * qp::kNRate, T->Ts, sizeof(T->Ts));
+    memcpy(h64.data() + kTabRate, T->Cg, sizeof(T->Cg));
+    memcpy(h64.data() + kTabRate + qp::kNCdf * qp::kNNode, T->Cp, sizeof(T->Cp));
+    for (size_t k = 0; k < kTabWords; ++k) h32[k] = (float)h64[k];
+
+    cudaError_t e = cudaSuccess;
+#define QP_TRY(x)                    \
+    do {                             \
+        e = (x);                     \
+        if (e != cudaSuccess) {      \
+            release(c);              \
+            return cuda_status(e);   \
+        }                            \
+    } while (0)
+    QP_TRY(cudaMalloc(&c->d_tab64, kTabWords * sizeof(double)));
+    QP_TRY(cudaMalloc(&c->d_tab32, kTabWords * sizeof(float)));
+    QP_TRY(cudaMemcpy(c->d_tab64, h64.data(), kTabWords * sizeof(double), cudaMemcpyHostToDevice));
+    QP_TRY(cudaMemcpy(c->d_tab32, h32.data(), kTabWords * sizeof(float), cudaMemcpyHostToDevice));
+    QP_TRY(cudaMalloc(&c->d_stats, kMaxSpecies * sizeof(qp::DevStats)));
+    QP_TRY(cudaMemset(c->d_stats, 0, kMaxSpecies * sizeof(qp::DevStats)));
+    QP_TRY(cudaMalloc(&c->d_n_start, 4 * sizeof(int64_t)));
+    QP_TRY(cudaMalloc(&c->d_tickets, 2 * sizeof(unsigned)));
+    QP_TRY(cudaMalloc(&c->d_status, sizeof(int)));
+    QP_TRY(cudaMemset(c->d_status, 0, sizeof(int)));
+    QP_TRY(cudaMalloc(&c->d_diag, (qp::kDiagBlocks + 1) * qp::kDiagWords * sizeof(double)));
+#undef QP_TRY
+    int st = ensure_chain(c, 16);
+    if (st != QP_OK) {
+        release(c);
+        return st;
+    }
+    *out_ctx = c;
+    return QP_OK;
+}
+
+int qp_destroy(qp_ctx *ctx)
+{
+    release(ctx);
+    return QP_OK;
+}
+
+int qp_create_species(qp_ctx *ctx, const qp_species_desc *d, int32_t *out_handle)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!d || !out_handle) return QP_ERR_INVALID_ARG;
+    if (d->kind < QP_ELECTRON || d->kind > QP_PHOTON) return QP_ERR_INVALID_ARG;
+    if (d->dims != 2 && d->dims != 3) return QP_ERR_INVALID_ARG;
+    if (d->capacity < 0 || !d->n_live) return QP_ERR_INVALID_ARG;
+    if (d->dims == 2 && d->z) return QP_ERR_INVALID_ARG;
+    if (d->capacity > 0 && (!d->x || !d->y || !d->ux || !d->uy || !d->uz || !d->tau || !d->w ||
+                            (d->dims == 3 && !d->z)))
+        return QP_ERR_INVALID_ARG;
+    if (ctx->species.size() >= (size_t)kMaxSpecies) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    // scratch for the worst case of this species being in both chains with
+    // every other registered species
+    size_t words = tiles_of(d->capacity) + 4;
+    for (const SpeciesRec &r : ctx->species) words += tiles_of(r.d.capacity) + 4;
+    int st = ensure_chain(ctx, words);
+    if (st != QP_OK) return st;
+    SpeciesRec r;
+    r.d = *d;
+    ctx->species.push_back(r);
+    *out_handle = (int32_t)(ctx->species.size() - 1);
+    return QP_OK;
+}
+
+int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t first,
+                          int64_t count, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &d = ctx->species[handle].d;
+    if (first < 0 || count < 0 || first + count > d.capacity) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    return cuda_status(
+        qp::launch_init_tau(d.tau, first, count, seed, d.kind, (cudaStream_t)stream));
+}
+
+int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!s) return QP_ERR_INVALID_ARG;
+    if (!(s->dt > 0.0) || !isfinite(s->dt) || s->n_steps < 0 || s->step < 0) return QP_ERR_INVALID_ARG;
+    if (s->precision != QP_FP64 && s->precision != QP_MIXED) return QP_ERR_INVALID_ARG;
+    if (s->max_emissions < 1 || s->max_emissions > QP_MAX_EMISSIONS) return QP_ERR_INVALID_ARG;
+    if (!(s->chi_threshold >= 0.0) || !(s->photon_min_gamma >= 0.0)) return QP_ERR_INVALID_ARG;
+    const qp_field &f = s->field;
+    if (f.kind < QP_FIELD_NONE || f.kind > QP_FIELD_UNIFORM_B) return QP_ERR_INVALID_ARG;
+    if (f.kind == QP_FIELD_GAUSSIAN && (!(f.w0 > 0.0) || !(f.tau_fwhm > 0.0)))
+        return QP_ERR_INVALID_ARG;
+    if (f.kind == QP_FIELD_YEE2D) {
+        if (f.nx < 1 || f.ny < 1 || !(f.dx > 0.0) || !(f.dy > 0.0)) return QP_ERR_INVALID_ARG;
+        for (int k = 0; k < 6; ++k)
+            if (!f.yee[k]) return QP_ERR_INVALID_ARG;
+    }
+    const int32_t hs[3] = {s->electron, s->positron, s->photon};
+    const int kinds[3] = {QP_ELECTRON, QP_POSITRON, QP_PHOTON};
+    for (int k = 0; k < 3; ++k) {
+        if (hs[k] == -1) continue;
+        if (!valid_handle(ctx, hs[k])) return QP_ERR_NOT_INITIALIZED;
+        if (ctx->species[hs[k]].d.kind != kinds[k]) return QP_ERR_INVALID_ARG;
+    }
+    if (s->n_steps == 0) return QP_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+
+    qp::StepArgs a{};
+    for (int k = 0; k < 3; ++k)
+        if (hs[k] != -1) a.sp[k] = species_dev(ctx, hs[k]);
+    a.f.kind = f.kind;
+    a.f.a0 = f.a0;
+    a.f.w0 = f.w0;
+    a.f.tau_fwhm = f.tau_fwhm;
+    a.f.x_focus = f.x_focus;
+    a.f.t_focus = f.t_focus;
+    a.f.b0 = f.b0;
+    for (int k = 0; k < 6; ++k) a.f.yee[k] = f.yee[k];
+    a.f.nx = f.nx;
+    a.f.ny = f.ny;
+    a.f.dx = f.dx;
+    a.f.dy = f.dy;
+    a.f.x0 = f.x0;
+    a.f.y0 = f.y0;
+    const size_t R = qp::kNRate, CC = (size_t)qp::kNCdf * qp::kNNode;
+    a.tab.H = ctx->d_tab64;
+    a.tab.Gs = ctx->d_tab64 + R;
+    a.tab.Ts = ctx->d_tab64 + 2 * R;
+    a.tab.Cg = ctx->d_tab64 + 3 * R;
+    a.tab.Cp = ctx->d_tab64 + 3 * R + CC;
+    a.tab.Hf = ctx->d_tab32;
+    a.tab.Gsf = ctx->d_tab32 + R;
+    a.tab.Tsf = ctx->d_tab32 + 2 * R;
+    a.tab.Cgf = ctx->d_tab32 + 3 * R;
+    a.tab.Cpf = ctx->d_tab32 + 3 * R + CC;
+    a.lep.status = ctx->d_chain;
+    a.lep.ticket = ctx->d_tickets;
+    a.pho.status = ctx->d_chain + ctx->chain_words;
+    a.pho.ticket = ctx->d_tickets + 1;
+    a.n_start = ctx->d_n_start;
+    a.stats = ctx->d_stats;
+    a.status = ctx->d_status;
+    a.dt = s->dt;
+    a.seed = s->seed;
+    a.chi_th = s->chi_threshold;
+    a.gmin = s->photon_min_gamma;
+    a.a_S = ctx->U.a_S;
+    a.C_rate = ctx->U.C_rate;
+    a.tau0w = ctx->U.tau0w;
+    a.pairs = s->pairs ? 1 : 0;
+    a.max_emit = s->max_emissions;
+    a.spin_limit = kSpinLimit;
+
+    // persistent grids: resident blocks, never more than the tiles the
+    // registered capacities allow
+    const int prec = s->precision == QP_MIXED ? 1 : 0;
+    int &bl = ctx->grid_cache[prec][0][f.kind];
+    int &bp = ctx->grid_cache[prec][1][f.kind];
+    if (!bl) bl = qp::step_blocks_per_sm(s->precision, false, f.kind);
+    if (!bp) bp = qp::step_blocks_per_sm(s->precision, true, f.kind);
+    int64_t lep_tiles = 0;
+    for (int k = 0; k < 2; ++k)
+        if (hs[k] != -1) lep_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
+    const int64_t ph_tiles = hs[2] != -1 ? (int64_t)tiles_of(ctx->species[hs[2]].d.capacity) : 0;
+    const int64_t res_l = (int64_t)bl * ctx->num_sms, res_p = (int64_t)bp * ctx->num_sms;
+    const int grid_lep = (int)(lep_tiles < res_l ? (lep_tiles > 0 ? lep_tiles : 1) : res_l);
+    const int grid_ph = (int)(ph_tiles < res_p ? (ph_tiles > 0 ? ph_tiles : 1) : res_p);
+    const bool do_lep = hs[0] != -1 || hs[1] != -1;
+    const bool do_ph = hs[2] != -1;
+    const int grid_begin = 2 * ctx->num_sms;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int32_t k = 0; k < s->n_steps; ++k) {
+        a.step = (uint64_t)(s->step + k);
+        a.t = (double)(s->step + k) * s->dt;
+        cudaError_t e = timed(ctx, 0, st, [&] { return qp::launch_step_begin(a, grid_begin, st); });
+        if (e == cudaSuccess && do_lep)
+            e = timed(ctx, 1, st, [&] {
+                return qp::launch_species_kernel(a, s->precision, false, grid_lep, st);
+            });
+        if (e == cudaSuccess && do_ph)
+            e = timed(ctx, 2, st, [&] {
+                return qp::launch_species_kernel(a, s->precision, true, grid_ph, st);
+            });
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return QP_OK;
+}
+
+int qp_diagnostics(qp_ctx *ctx, int32_t handle, qp_diag *out, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!out) return QP_ERR_INVALID_ARG;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const qp_species_desc &d = ctx->species[handle].d;
+    qp::SpeciesDev S = species_dev(ctx, handle);
+    double *partials = ctx->d_diag;
+    double *fin = ctx->d_diag + (size_t)qp::kDiagBlocks * qp::kDiagWords;
+    cudaError_t e = qp::launch_diag(S, d.kind == QP_PHOTON, partials, qp::kDiagBlocks, fin, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    double h[qp::kDiagWords];
+    qp::DevStats ds;
+    int64_t n_live = 0;
+    int status = 0;
+    if ((e = cudaMemcpyAsync(h, fin, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&ds, ctx->d_stats + handle, sizeof(ds), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(&n_live, d.n_live, sizeof(n_live), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_status(e);
+    memset(out, 0, sizeof(*out));
+    out->n_live = n_live;
+    out->n_alive = (int64_t)llround(h[0]);
+    out->weight = h[1];
+    out->energy = h[2];
+    out->px = h[3];
+    out->py = h[4];
+    out->pz = h[5];
+    out->chi_mean = (d.chi && h[1] > 0.0) ? h[6] / h[1] : 0.0;
+    for (int k = 0; k < QP_HIST_BINS; ++k) out->hist[k] = h[8 + k];
+    out->n_emit = (int64_t)ds.n_emit;
+    out->n_photon = (int64_t)ds.n_photon;
+    out->n_photon_drop = (int64_t)ds.n_photon_drop;
+    out->n_subthreshold = (int64_t)ds.n_subthreshold;
+    out->n_pair = (int64_t)ds.n_pair;
+    out->n_pair_drop = (int64_t)ds.n_pair_drop;
+    out->n_saturated = (int64_t)ds.n_saturated;
+    out->n_clamped = (int64_t)ds.n_clamped;
+    out->n_continuous = (int64_t)ds.n_continuous;
+    out->e_subthreshold = ds.e_subthreshold;
+    out->e_dropped = ds.e_dropped;
+    out->status = status;
+    return status;
+}
+
+int qp_export_tables(qp_ctx *ctx, qp_tables_export *out)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!out) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    std::vector<double> h(kTabWords);
+    cudaError_t e = cudaMemcpy(h.data(), ctx->d_tab64, kTabWords * sizeof(double),
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    memcpy(out->H, h.data(), sizeof(out->H));
+    memcpy(out->Gs, h.data() + qp::kNRate, sizeof(out->Gs));
+    memcpy(out->Ts, h.data() + 2 * qp::kNRate, sizeof(out->Ts));
+    memcpy(out->Cg, h.data() + kTabRate, sizeof(out->Cg));
+    memcpy(out->Cp, h.data() + kTabRate + qp::kNCdf * qp::kNNode, sizeof(out->Cp));
+    out->a_S = ctx->U.a_S;
+    out->C_rate = ctx->U.C_rate;
+    out->tau0w = ctx->U.tau0w;
+    return QP_OK;
+}
+
+int qp_reset_counters(qp_ctx *ctx, int32_t handle)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    cudaError_t e = cudaMemset(ctx->d_stats + handle, 0, sizeof(qp::DevStats));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return cuda_status(e);
+}
+
+int qp_profile_enable(qp_ctx *ctx, int enable)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    ctx->profiling = enable != 0;
+    ctx->events_used = 0;
+    ctx->records.clear();
+    return QP_OK;
+}
+
+int qp_profile_read(qp_ctx *ctx, double ms[3], int64_t launches[3])
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!ms || !launches) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (size_t r = 0; r < ctx->records.size(); ++r) {
+        cudaEvent_t a = ctx->events[2 * r], b = ctx->events[2 * r + 1];
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess) return cuda_status(e);
+        ms[ctx->records[r]] += t;
+        launches[ctx->records[r]] += 1;
+    }
+    return QP_OK;
+}
+
+int qp_selftest_wait_timeout(qp_ctx *ctx, uint32_t spin_limit)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    cudaError_t e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_chain, 0, 2 * sizeof(unsigned long long));
+    qp::ChainDev ch{ctx->d_chain, ctx->d_tickets};
+    if (e == cudaSuccess) e = qp::launch_wait_selftest(ch, spin_limit, ctx->d_status, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e);
+    return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// Device building blocks of libqedpic: kernel argument layout, Philox,
+// field models, chi, table lookups and inverse-CDF sampling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qp_internal.h"
+
+namespace qp {
+
+enum Prec { kFP64 = 0, kMixed = 1 };
+constexpr int kTile = 256;   // particles per tile = threads per block
+constexpr int kWarps = kTile / 32;
+
+// ------------------------------------------------------------------ layout
+
+struct SpeciesDev {
+    double *x, *y, *z, *ux, *uy, *uz, *tau, *w, *chi;
+    int64_t *n_live;
+    int64_t cap;
+    int32_t present;
+    int32_t slot_stats;  // index of this species' counter block
+};
+
+// Per-species event counters (device; atomics aggregated per block).
+struct DevStats {
+    unsigned long long n_emit, n_photon, n_photon_drop, n_subthreshold, n_pair, n_pair_drop,
+        n_saturated, n_clamped, n_continuous;
+    double e_subthreshold, e_dropped;
+};
+
+struct FieldDev {
+    int32_t kind;
+    double a0, w0, tau_fwhm, x_focus, t_focus, b0;
+    const float *yee[6];
+    int64_t nx, ny;
+    double dx, dy, x0, y0;
+};
+
+struct TablesDev {
+    const double *H, *Gs, *Ts, *Cg, *Cp;       // FP64
+    const float *Hf, *Gsf, *Tsf, *Cgf, *Cpf;   // FP32 copies
+};
+
+// Scan scratch of one append chain (decoupled look-back).
+struct ChainDev {
+    unsigned long long *status;  // one word per tile: flag (2 bits) | value (62 bits)
+    unsigned int *ticket;        // dynamic tile counter
+};
+
+struct StepArgs {
+    SpeciesDev sp[3];            // electron, positron, photon
+    FieldDev f;
+    TablesDev tab;
+    ChainDev lep, pho;
+    int64_t *n_start;            // [3] live counts at the start of the step
+    DevStats *stats;             // [3] counters of the three species
+    int *status;                 // sticky status word
+    double dt, t;
+    uint64_t step, seed;
+    double chi_th, gmin;
+    double a_S, C_rate, tau0w;
+    int32_t pairs, max_emit;
+    unsigned int spin_limit;     // bound of every look-back wait
+};
+
+// ------------------------------------------------------------------ status
+
+__device__ __forceinline__ void raise_status(int *status, int code)
+{
+    // first error wins; a warning never overwrites an error
+    int old = *((volatile int *)status);
+    if (old < 0) return;
+    if (code < 0)
+        atomicCAS(status, old, code);
+    else if (old == 0)
+        atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+enum RngPurpose { kRngInit = 0, kRngEmit = 1, kRngPhotonTau = 2, kRngPair = 3, kRngPairPos = 4 };
+
+// counter (slot lo, slot hi, step, species<<24 | purpose<<16 | k), key = seed
+__device__ __forceinline__ uint4 draw(uint64_t seed, int species, int purpose, int64_t slot,
+                                      uint64_t step, int k)
+{
+    const uint4 c = make_uint4((unsigned)((uint64_t)slot & 0xFFFFFFFFu),
+                               (unsigned)((uint64_t)slot >> 32), (unsigned)(step & 0xFFFFFFFFu),
+                               ((unsigned)species << 24) | ((unsigned)purpose << 16) |
+                                   ((unsigned)k & 0xFFFFu));
+    return philox4x32_10(c, make_uint2((unsigned)(seed & 0xFFFFFFFFu), (unsigned)(seed >> 32)));
+}
+
+// uniform in ]0,1] with 53 random bits
+__device__ __forceinline__ double u53(unsigned a, unsigned b)
+{
+    const unsigned long long m = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+    return (double)(m + 1ull) * 0x1.0p-53;
+}
+
+// ------------------------------------------------------------------ fields
+
+template <typename R>
+struct Vec3 {
+    R x, y, z;
+};
+
+// Fields at (x, y, z, t); R = double (FP64 path) or float (mixed path, with
+// phases reduced in FP64 before the FP32 trigonometry).
+template <int FK, typename R>
+__device__ __forceinline__ void eval_field(const FieldDev &f, double x, double y, double z,
+                                           double t, Vec3<R> &E, Vec3<R> &B)
+{
+    E = {R(0), R(0), R(0)};
+    B = {R(0), R(0), R(0)};
+    if constexpr (FK == QP_FIELD_PLANE) {
+        R v;
+        if constexpr (sizeof(R) == 8) {
+            v = f.a0 * cos(t - x);
+        } else {
+            const double ph = t - x;
+            const double red = ph - 6.283185307179586 * rint(ph * 0.15915494309189535);
+            v = (float)f.a0 * cosf((float)red);
+        }
+        E.y = v;
+        B.z = v;
+    } else if constexpr (FK == QP_FIELD_GAUSSIAN) {
+        const double xi = x - f.x_focus;
+        const double eta = (t - f.t_focus) - xi;
+        const double zr = 0.5 * f.w0 * f.w0;
+        const double q = xi / zr;
+        const double wr2 = 1.0 + q * q;
+        const double r2 = y * y + z * z;
+        R v;
+        if constexpr (sizeof(R) == 8) {
+            const double env = -r2 / (f.w0 * f.w0 * wr2) -
+                               2.0 * 0.6931471805599453 * eta * eta / (f.tau_fwhm * f.tau_fwhm);
+            const double amp = f.a0 / sqrt(wr2) * exp(env);
+            const double phase = -eta + r2 * xi / (2.0 * (xi * xi + zr * zr)) - atan(q);
+            v = amp * cos(phase);
+        } else {
+            const float env = (float)(-r2 / (f.w0 * f.w0 * wr2)) -
+                              1.3862943611198906f * (float)(eta * eta / (f.tau_fwhm * f.tau_fwhm));
+            const float amp = (float)f.a0 * rsqrtf((float)wr2) * __expf(env);
+            double phase = -eta + r2 * xi / (2.0 * (xi * xi + zr * zr));
+            phase -= 6.283185307179586 * rint(phase * 0.15915494309189535);
+            v = amp * cosf((float)phase - atanf((float)q));
+        }
+        E.y = v;
+        B.z = v;
+    } else if constexpr (FK == QP_FIELD_UNIFORM_B) {
+        B.z = (R)f.b0;
+    } else if constexpr (FK == QP_FIELD_YEE2D) {
+        // linear interpolation of the six staggered components; nodes
+        // outside the grid contribute zero field
+        const double gx0 = (x - f.x0) / f.dx, gy0 = (y - f.y0) / f.dy;
+        R out[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            // Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j) Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2)
+            const bool hx = (c == 0 || c == 4 || c == 5), hy = (c == 1 || c == 3 || c == 5);
+            const double gx = hx ? gx0 - 0.5 : gx0, gy = hy ? gy0 - 0.5 : gy0;
+            const double fi = floor(gx), fj = floor(gy);
+            const R fx = (R)(gx - fi), fy = (R)(gy - fj);
+            const float *F = f.yee[c];
+            R acc = R(0);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const double ii = fi + a, jj = fj + b;
+                    // written so that NaN positions fail the test too
+                    if (!(ii >= 0.0 && jj >= 0.0 && ii < (double)f.nx && jj < (double)f.ny)) continue;
+                    const R wgt = (a ? fx : R(1) - fx) * (b ? fy : R(1) - fy);
+                    acc += wgt * (R)__ldg(F + (int64_t)jj * f.nx + (int64_t)ii);
+                }
+            }
+            out[c] = acc;
+        }
+        E = {out[0], out[1], out[2]};
+        B = {out[3], out[4], out[5]};
+    }
+}
+
+// ------------------------------------------------------------------ chi (Eq. 1)
+
+// chi_e = sqrt(|gamma E + u x B|^2 - (u.E)^2) / a_S, in FP64
+__device__ __forceinline__ double chi_e64(double Ex, double Ey, double Ez, double Bx, double By,
+                                          double Bz, double ux, double uy, double uz, double g,
+                                          double inv_aS)
+{
+    const double ax = g * Ex + (uy * Bz - uz * By);
+    const double ay = g * Ey + (uz * Bx - ux * Bz);
+    const double az = g * Ez + (ux * By - uy * Bx);
+    const double ue = ux * Ex + uy * Ey + uz * Ez;
+    const double s = ax * ax + ay * ay + az * az - ue * ue;
+    return s > 0.0 ? sqrt(s) * inv_aS : 0.0;
+}
+
+// ------------------------------------------------------------------ rate tables
+
+// Index and exact interpolation weight of chi on a grid of 2^k nodes per
+// octave starting at 2^-14, from the bits of chi (no logarithm): the node is
+// 2^e (1 + m/2^k) with m the top k mantissa bits; the weight is the rest of
+// the mantissa.  Requires 2^-14 <= chi < 2^10.
+template <int KBITS>
+__device__ __forceinline__ int grid_index64(double chi, double &f)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(chi);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    const int m = (int)((b >> (52 - KBITS)) & ((1u << KBITS) - 1));
+    f = (double)(b & ((1ull << (52 - KBITS)) - 1)) * (1.0 / (double)(1ull << (52 - KBITS)));
+    return ((e - kChiExp0) << KBITS) + m;
+}
+
+template <int KBITS>
+__device__ __forceinline__ int grid_index32(float chi, float &f)
+{
+    const unsigned b = __float_as_uint(chi);
+    const int e = (int)((b >> 23) & 0xFF) - 127;
+    const int m = (int)((b >> (23 - KBITS)) & ((1u << KBITS) - 1));
+    f = (float)(b & ((1u << (23 - KBITS)) - 1)) * (1.0f / (float)(1u << (23 - KBITS)));
+    return ((e - kChiExp0) << KBITS) + m;
+}
+
+constexpr double kChiLo = 0x1.0p-14, kChiHi = 0x1.0p10;
+constexpr double kPi = 3.14159265358979323846;
+
+// which: 0 H, 1 G (table holds G/chi), 2 T (table holds T exp(8/(3 chi)))
+// V points at the (shared-memory) table of that quantity.
+template <int WHICH>
+__device__ __forceinline__ double rate64(const double *V, double chi, bool &clamped)
+{
+    if (WHICH == 2 && !(chi >= kPairChiMin)) return 0.0;
+    if (!(chi >= kChiLo)) {
+        if (WHICH == 0) return __dmul_rn(2.5 * kPi, chi);
+        return __dmul_rn(__dmul_rn(2.0 * kPi, chi), chi) / 1.7320508075688772;
+    }
+    double v, c = chi;
+    if (chi >= kChiHi) {
+        clamped = true;
+        v = V[kNRate - 1];
+        c = kChiHi;
+    } else {
+        double f;
+        const int j = grid_index64<5>(chi, f);
+        const double a = V[j], d = __dsub_rn(V[j + 1], a);
+        v = __dadd_rn(a, __dmul_rn(f, d));
+    }
+    if (WHICH == 1) return __dmul_rn(v, c);
+    if (WHICH == 2) return __dmul_rn(v, exp(-8.0 / (3.0 * c)));
+    return v;
+}
+
+template <int WHICH>
+__device__ __forceinline__ float rate32(const float *V, float chi, bool &clamped)
+{
+    if (WHICH == 2 && !(chi >= (float)kPairChiMin)) return 0.0f;
+    if (!(chi >= (float)kChiLo)) {
+        if (WHICH == 0) return (float)(2.5 * kPi) * chi;
+        return (float)(2.0 * kPi / 1.7320508075688772) * chi * chi;
+    }
+    float v, c = chi;
+    if (chi >= (float)kChiHi) {
+        clamped = true;
+        v = V[kNRate - 1];
+        c = (float)kChiHi;
+    } else {
+        float f;
+        const int j = grid_index32<5>(chi, f);
+        const float a = V[j];
+        v = fmaf(f, V[j + 1] - a, a);
+    }
+    if (WHICH == 1) return v * c;
+    if (WHICH == 2) return v * __expf(-8.0f / (3.0f * c));
+    return v;
+}
+
+// ------------------------------------------------------------------ inverse CDF (Eq. 7)
+
+// Invert one CDF row C (kNNode logit nodes s_i = smin + span i / 255) at xi.
+// Emission rows follow u^(1/3) below the first node; pair rows clamp.
+template <typename R>
+__device__ __forceinline__ R row_invert(const R *__restrict__ C, R xi, double smin, double span,
+                                        bool power_tail)
+{
+    const R c0 = __ldg(C);
+    if (xi <= c0) {
+        const R x0 = R(1) / (R(1) + (R)exp(-smin));
+        if (power_tail && c0 > R(0)) {
+            const R r = xi / c0;
+            return x0 * r * r * r;
+        }
+        return x0;
+    }
+    const R clast = __ldg(C + kNNode - 1);
+    if (xi >= clast) return R(1) / (R(1) + (R)exp(-(smin + span)));
+    int lo = 0, hi = kNNode - 1;
+#pragma unroll 1
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(C + mid) < xi)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const R clo = __ldg(C + lo), chi_ = __ldg(C + lo + 1);
+    const double s_lo = smin + span * lo / (kNNode - 1);
+    const double s_hi = smin + span * (lo + 1) / (kNNode - 1);
+    if constexpr (sizeof(R) == 8) {
+        const double t = (xi - clo) / (chi_ - clo);
+        const double sv = s_lo + t * (s_hi - s_lo);
+        return 1.0 / (1.0 + exp(-sv));
+    } else {
+        const float t = (xi - clo) / (chi_ - clo);
+        const float sv = (float)s_lo + t * (float)(s_hi - s_lo);
+        return 1.0f / (1.0f + __expf(-sv));
+    }
+}
+
+// Photon fraction u = chi_gamma / chi_e for chi_e (rows j, j+1 interpolated
+// linearly in chi; below the grid the classical scaling u ~ chi).
+template <typename R>
+__device__ __forceinline__ R sample_cdf(const R *__restrict__ rows, R chi, R xi, double smin,
+                                        double span, bool emission, bool &clamped)
+{
+    if (!(chi >= (R)kChiLo)) {
+        const R r0 = row_invert<R>(rows, xi, smin, span, emission);
+        return emission ? (chi / (R)kChiLo) * r0 : r0;
+    }
+    if (chi >= (R)kChiHi) {
+        clamped = true;
+        return row_invert<R>(rows + (kNCdf - 1) * kNNode, xi, smin, span, emission);
+    }
+    R f;
+    int j;
+    if constexpr (sizeof(R) == 8)
+        j = grid_index64<2>(chi, f);
+    else
+        j = grid_index32<2>(chi, f);
+    const R ra = row_invert<R>(rows + j * kNNode, xi, smin, span, emission);
+    const R rb = row_invert<R>(rows + (j + 1) * kNNode, xi, smin, span, emission);
+    return ra + f * (rb - ra);
+}
+
+}  // namespace qp

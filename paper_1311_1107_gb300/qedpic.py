@@ -1,0 +1,216 @@
+"""ctypes binding of libqedpic (include/qedpic.h), same names as the C ABI.
+
+Argument marshalling only: every step of the QED particle path runs in the
+library's CUDA kernels.  Importing this module does not load the library;
+the first call does, and raises if ``libqedpic.so`` has not been built (there
+is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+QP_OK = 0
+QP_WARN_BUFFER_FULL = 1
+QP_WARN_TABLE_CLAMPED = 2
+QP_ERR_INVALID_ARG = -1
+QP_ERR_CUDA = -2
+QP_ERR_OOM = -3
+QP_ERR_NOT_INITIALIZED = -4
+QP_ERR_TIMEOUT = -5
+
+QP_ELECTRON, QP_POSITRON, QP_PHOTON = 0, 1, 2
+QP_FP64, QP_MIXED = 0, 1
+QP_FIELD_NONE, QP_FIELD_PLANE, QP_FIELD_GAUSSIAN, QP_FIELD_YEE2D, QP_FIELD_UNIFORM_B = range(5)
+QP_MAX_EMISSIONS = 8
+QP_HIST_BINS = 64
+QP_NRATE, QP_NCDF, QP_NNODE = 769, 97, 256
+
+FIELD_KINDS = {"none": QP_FIELD_NONE, "plane": QP_FIELD_PLANE, "gaussian": QP_FIELD_GAUSSIAN,
+               "yee2d": QP_FIELD_YEE2D, "uniform_b": QP_FIELD_UNIFORM_B}
+
+_dp = C.POINTER(C.c_double)
+
+
+class qp_table_params(C.Structure):
+    _fields_ = [("lambda_m", C.c_double), ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qp_species_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dims", C.c_int32), ("capacity", C.c_int64),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
+                ("tau", C.c_void_p), ("w", C.c_void_p), ("chi", C.c_void_p),
+                ("n_live", C.c_void_p)]
+
+
+class qp_field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("a0", C.c_double),
+                ("w0", C.c_double), ("tau_fwhm", C.c_double), ("x_focus", C.c_double),
+                ("t_focus", C.c_double), ("b0", C.c_double), ("yee", C.c_void_p * 6),
+                ("nx", C.c_int64), ("ny", C.c_int64), ("dx", C.c_double), ("dy", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double)]
+
+
+class qp_step_params(C.Structure):
+    _fields_ = [("field", qp_field), ("dt", C.c_double), ("step", C.c_int64),
+                ("n_steps", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
+                ("chi_threshold", C.c_double), ("photon_min_gamma", C.c_double),
+                ("pairs", C.c_int32), ("max_emissions", C.c_int32), ("electron", C.c_int32),
+                ("positron", C.c_int32), ("photon", C.c_int32), ("reserved", C.c_int32)]
+
+
+class qp_diag(C.Structure):
+    _fields_ = ([("n_live", C.c_int64), ("n_alive", C.c_int64)]
+                + [(n, C.c_double) for n in ("weight", "energy", "px", "py", "pz", "chi_mean")]
+                + [("hist", C.c_double * QP_HIST_BINS)]
+                + [(n, C.c_int64) for n in ("n_emit", "n_photon", "n_photon_drop",
+                                            "n_subthreshold", "n_pair", "n_pair_drop",
+                                            "n_saturated", "n_clamped", "n_continuous")]
+                + [("e_subthreshold", C.c_double), ("e_dropped", C.c_double),
+                   ("status", C.c_int32), ("reserved", C.c_int32)])
+
+    def as_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("hist", "reserved")}
+        d["hist"] = list(self.hist)
+        return d
+
+
+class qp_tables_export(C.Structure):
+    _fields_ = [("H", C.c_double * QP_NRATE), ("Gs", C.c_double * QP_NRATE),
+                ("Ts", C.c_double * QP_NRATE), ("Cg", C.c_double * (QP_NCDF * QP_NNODE)),
+                ("Cp", C.c_double * (QP_NCDF * QP_NNODE)), ("a_S", C.c_double),
+                ("C_rate", C.c_double), ("tau0w", C.c_double)]
+
+
+class QPError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} returned {status_name(status)} ({status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
+           "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
+           "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
+           "qp_status_string")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded libqedpic (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with "
+                                   "`python -m paper_1311_1107_gb300.build` (no CPU fallback)")
+            _build.build()
+        L = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.qp_init_tables.argtypes = [C.POINTER(qp_table_params), C.POINTER(vp)]
+        L.qp_destroy.argtypes = [vp]
+        L.qp_create_species.argtypes = [vp, C.POINTER(qp_species_desc), C.POINTER(i32)]
+        L.qp_init_optical_depth.argtypes = [vp, i32, C.c_uint64, i64, i64, vp]
+        L.qp_step.argtypes = [vp, C.POINTER(qp_step_params), vp]
+        L.qp_diagnostics.argtypes = [vp, i32, C.POINTER(qp_diag), vp]
+        L.qp_export_tables.argtypes = [vp, C.POINTER(qp_tables_export)]
+        L.qp_reset_counters.argtypes = [vp, i32]
+        L.qp_selftest_wait_timeout.argtypes = [vp, C.c_uint32]
+        L.qp_profile_enable.argtypes = [vp, C.c_int]
+        L.qp_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.qp_status_string.argtypes = [C.c_int]
+        L.qp_status_string.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "qp_status_string":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def status_name(status: int) -> str:
+    return lib().qp_status_string(int(status)).decode()
+
+
+def _check(fn, st, allow_warn=True):
+    if st < 0 or (st > 0 and not allow_warn):
+        raise QPError(fn, st)
+    return st
+
+
+# ---------------------------------------------------------------- the C calls
+
+def qp_init_tables(lambda_m: float = 0.8e-6, device: int = 0) -> C.c_void_p:
+    p = qp_table_params(lambda_m, device, 0)
+    ctx = C.c_void_p()
+    _check("qp_init_tables", lib().qp_init_tables(C.byref(p), C.byref(ctx)))
+    return ctx
+
+
+def qp_destroy(ctx) -> int:
+    return lib().qp_destroy(ctx)
+
+
+def qp_create_species(ctx, desc: qp_species_desc) -> int:
+    h = C.c_int32(-1)
+    _check("qp_create_species", lib().qp_create_species(ctx, C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def qp_init_optical_depth(ctx, handle: int, seed: int, first: int, count: int, stream=None):
+    return _check("qp_init_optical_depth",
+                  lib().qp_init_optical_depth(ctx, handle, seed, first, count, stream))
+
+
+def qp_step(ctx, params: qp_step_params, stream=None) -> int:
+    return _check("qp_step", lib().qp_step(ctx, C.byref(params), stream))
+
+
+def qp_diagnostics(ctx, handle: int, stream=None) -> qp_diag:
+    d = qp_diag()
+    st = lib().qp_diagnostics(ctx, handle, C.byref(d), stream)
+    if st < 0 and d.status != st:
+        raise QPError("qp_diagnostics", st)
+    return d
+
+
+def qp_export_tables(ctx) -> qp_tables_export:
+    t = qp_tables_export()
+    _check("qp_export_tables", lib().qp_export_tables(ctx, C.byref(t)))
+    return t
+
+
+def qp_reset_counters(ctx, handle: int) -> int:
+    return _check("qp_reset_counters", lib().qp_reset_counters(ctx, handle))
+
+
+def qp_selftest_wait_timeout(ctx, spin_limit: int) -> int:
+    """Status raised by a deliberately unsatisfiable, bounded device wait."""
+    return lib().qp_selftest_wait_timeout(ctx, int(spin_limit))
+
+
+def qp_profile_enable(ctx, enable: bool = True) -> int:
+    return _check("qp_profile_enable", lib().qp_profile_enable(ctx, 1 if enable else 0))
+
+
+def qp_profile_read(ctx):
+    """(ms[3], launches[3]) per kernel: step-begin, lepton, photon."""
+    ms = (C.c_double * 3)()
+    n = (C.c_int64 * 3)()
+    _check("qp_profile_read", lib().qp_profile_read(ctx, ms, n))
+    return list(ms), list(n)
+
+
+def qp_status_string(status: int) -> str:
+    return status_name(status)

@@ -1,0 +1,161 @@
+"""Device-resident species and simulations on top of the C ABI.
+
+PyTorch supplies the device memory (caller-owned buffers of the C ABI) and
+streams; every step of the QED path runs in libqedpic's kernels.  A
+``Simulation`` is built from a workload description of
+``paper_1311_1107_gb300.workloads``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import qedpic as Q
+from .workloads import LAMBDA_M
+
+NAMES = ("x", "y", "z", "ux", "uy", "uz", "tau", "w")
+KIND = {"electron": Q.QP_ELECTRON, "positron": Q.QP_POSITRON, "photon": Q.QP_PHOTON}
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def stream_handle(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class DeviceSpecies:
+    """FP64 SoA buffers of one species on the GPU, registered with a context."""
+
+    def __init__(self, ctx, kind: int, capacity: int, dims: int = 3, device="cuda:0",
+                 track_chi: bool = True):
+        self.kind, self.cap, self.dims = kind, int(capacity), dims
+        n = max(self.cap, 1)
+        self.t = {nm: torch.zeros(n, dtype=torch.float64, device=device)
+                  for nm in NAMES if not (nm == "z" and dims == 2)}
+        self.chi = torch.zeros(n, dtype=torch.float64, device=device) if track_chi else None
+        self.n_live = torch.zeros(1, dtype=torch.int64, device=device)
+        d = Q.qp_species_desc()
+        d.kind, d.dims, d.capacity = kind, dims, self.cap
+        for nm in NAMES:
+            setattr(d, nm, _ptr(self.t.get(nm)))
+        d.chi = _ptr(self.chi)
+        d.n_live = _ptr(self.n_live)
+        self._desc = d
+        self.handle = Q.qp_create_species(ctx, d)
+
+    def load(self, arrays: dict, n: int | None = None):
+        """Copy initial particles into slots [0, n) and set the live count."""
+        n = len(arrays["x"]) if n is None else n
+        if n > self.cap:
+            raise ValueError(f"{n} particles exceed capacity {self.cap}")
+        for nm, t in self.t.items():
+            if nm in arrays and n:
+                t[:n].copy_(torch.as_tensor(np.asarray(arrays[nm][:n], dtype=np.float64)))
+        self.n_live.fill_(n)
+
+    def count(self) -> int:
+        return int(self.n_live.item())
+
+    def host(self, n: int | None = None) -> dict:
+        n = self.count() if n is None else n
+        out = {nm: t[:n].cpu().numpy() for nm, t in self.t.items()}
+        if self.chi is not None:
+            out["chi"] = self.chi[:n].cpu().numpy()
+        return out
+
+
+def make_field(desc: dict, device="cuda:0"):
+    """qp_field from a workload field description (Yee components are
+    uploaded to device float32 arrays that the field keeps alive)."""
+    f = Q.qp_field()
+    f.kind = Q.FIELD_KINDS[desc["kind"]]
+    f.a0 = desc.get("a0", 0.0)
+    f.w0 = desc.get("w0", 0.0)
+    f.tau_fwhm = desc.get("tau_fwhm", 0.0)
+    f.x_focus = desc.get("x_focus", 0.0)
+    f.t_focus = desc.get("t_focus", 0.0)
+    f.b0 = desc.get("b0", 0.0)
+    keep = []
+    if desc["kind"] == "yee2d":
+        comps = [torch.as_tensor(np.ascontiguousarray(c, dtype=np.float32)).to(device)
+                 for c in desc["comps"]]
+        keep = comps
+        for k, c in enumerate(comps):
+            f.yee[k] = c.data_ptr()
+        f.ny, f.nx = comps[0].shape
+        f.dx, f.dy = desc["dx"], desc["dy"]
+        f.x0, f.y0 = desc.get("x0", 0.0), desc.get("y0", 0.0)
+    return f, keep
+
+
+class Simulation:
+    """One run: a context, three species and the step parameters."""
+
+    def __init__(self, workload: dict, precision: str = "fp64", device: int = 0, ctx=None,
+                 track_chi: bool = True, init_tau: bool = True, load: bool = True):
+        self.dev = f"cuda:{device}"
+        self.own_ctx = ctx is None
+        self.ctx = ctx if ctx is not None else Q.qp_init_tables(LAMBDA_M, device)
+        self.workload = workload
+        dims = workload["dims"]
+        cap = workload["capacity"]
+        self.species = {
+            name: DeviceSpecies(self.ctx, KIND[name], cap[name], dims, self.dev, track_chi)
+            for name in ("electron", "positron", "photon")
+        }
+        self.field, self._keep = make_field(workload["field"], self.dev)
+        p = workload["params"]
+        s = Q.qp_step_params()
+        s.field = self.field
+        s.dt = p["dt"]
+        s.precision = Q.QP_MIXED if precision == "mixed" else Q.QP_FP64
+        s.seed = int(p.get("seed", 0))
+        s.chi_threshold = float(p.get("chi_th", 0.0))
+        s.photon_min_gamma = float(p.get("photon_min_gamma", 2.0))
+        s.pairs = 1 if p.get("pairs", False) else 0
+        s.max_emissions = int(p.get("max_emit", 8))
+        s.electron = self.species["electron"].handle
+        s.positron = self.species["positron"].handle
+        s.photon = self.species["photon"].handle
+        self.params = s
+        self.step_index = int(p.get("step", 0))
+        if load:
+            self.load_initial(init_tau)
+
+    def load_initial(self, init_tau: bool = True, stream=None):
+        el = self.species["electron"]
+        el.load(self.workload["electrons"])
+        for sp in ("positron", "photon"):
+            self.species[sp].n_live.zero_()
+        if init_tau:
+            n = len(self.workload["electrons"]["x"])
+            Q.qp_init_optical_depth(self.ctx, el.handle, self.params.seed, 0, n,
+                                    stream_handle(stream))
+        for sp in self.species.values():
+            Q.qp_reset_counters(self.ctx, sp.handle)
+        self.step_index = int(self.workload["params"].get("step", 0))
+
+    def run(self, n_steps: int, stream=None) -> int:
+        self.params.step = self.step_index
+        self.params.n_steps = int(n_steps)
+        st = Q.qp_step(self.ctx, self.params, stream_handle(stream))
+        self.step_index += int(n_steps)
+        return st
+
+    def diagnostics(self, name: str, stream=None) -> Q.qp_diag:
+        return Q.qp_diagnostics(self.ctx, self.species[name].handle, stream_handle(stream))
+
+    def live_counts(self) -> dict:
+        return {k: v.count() for k, v in self.species.items()}
+
+    def close(self):
+        if self.own_ctx and self.ctx is not None:
+            torch.cuda.synchronize()
+            Q.qp_destroy(self.ctx)
+            self.ctx = None
