@@ -327,7 +327,9 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     if (f.kind == QP_FIELD_GAUSSIAN && (!(f.w0 > 0.0) || !(f.tau_fwhm > 0.0)))
         return QP_ERR_INVALID_ARG;
     if (f.kind == QP_FIELD_YEE2D) {
-        if (f.nx < 1 || f.ny < 1 || !(f.dx > 0.0) || !(f.dy > 0.0)) return QP_ERR_INVALID_ARG;
+        if (f.nx < 1 || f.ny < 1 || f.nx > (1 << 30) || f.ny > (1 << 30) || !(f.dx > 0.0) ||
+            !(f.dy > 0.0) || f.nx * f.ny > ((int64_t)1 << 40))
+            return QP_ERR_INVALID_ARG;
         for (int k = 0; k < 6; ++k)
             if (!f.yee[k]) return QP_ERR_INVALID_ARG;
     }
@@ -359,6 +361,12 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     a.f.dy = f.dy;
     a.f.x0 = f.x0;
     a.f.y0 = f.y0;
+    if (f.kind == QP_FIELD_YEE2D) {
+        a.f.inv_dx = 1.0 / f.dx;
+        a.f.inv_dy = 1.0 / f.dy;
+        a.f.x0s = f.x0 / f.dx;
+        a.f.y0s = f.y0 / f.dy;
+    }
     const size_t R = qp::kNRate, CC = (size_t)qp::kNCdf * qp::kNNode;
     a.tab.H = ctx->d_tab64;
     a.tab.Gs = ctx->d_tab64 + R;

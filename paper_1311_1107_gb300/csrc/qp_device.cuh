@@ -36,6 +36,7 @@ struct FieldDev {
     const float *yee[6];
     int64_t nx, ny;
     double dx, dy, x0, y0;
+    double inv_dx, inv_dy, x0s, y0s;  // 1/dx, 1/dy, x0/dx, y0/dy (mixed gather)
 };
 
 struct TablesDev {
@@ -168,28 +169,53 @@ __device__ __forceinline__ void eval_field(const FieldDev &f, double x, double y
     } else if constexpr (FK == QP_FIELD_UNIFORM_B) {
         B.z = (R)f.b0;
     } else if constexpr (FK == QP_FIELD_YEE2D) {
-        // linear interpolation of the six staggered components; nodes
-        // outside the grid contribute zero field
-        const double gx0 = (x - f.x0) / f.dx, gy0 = (y - f.y0) / f.dy;
+        // linear interpolation of the six staggered components
+        //   Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j) Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2);
+        // nodes outside the grid contribute zero field.  The cell index and
+        // weight of each axis are found once for the node and the half-node
+        // grids (FP64 path: in FP64; mixed path: the cell coordinate is formed
+        // with one FP64 FMA, the rest in FP32).
+        int ix[2], iy[2];
+        R wx[2], wy[2];
+        if constexpr (sizeof(R) == 8) {
+            const double gx = (x - f.x0) / f.dx, gy = (y - f.y0) / f.dy;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const double ax = h ? gx - 0.5 : gx, ay = h ? gy - 0.5 : gy;
+                const double fx = floor(ax), fy = floor(ay);
+                wx[h] = ax - fx;
+                wy[h] = ay - fy;
+                // clamp before the conversion (NaN and huge values included)
+                ix[h] = (int)fmax(-2.0, fmin((double)f.nx + 1.0, fx));
+                iy[h] = (int)fmax(-2.0, fmin((double)f.ny + 1.0, fy));
+            }
+        } else {
+            const float gx = (float)fma(x, f.inv_dx, -f.x0s), gy = (float)fma(y, f.inv_dy, -f.y0s);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float ax = h ? gx - 0.5f : gx, ay = h ? gy - 0.5f : gy;
+                const float fx = floorf(ax), fy = floorf(ay);
+                wx[h] = ax - fx;
+                wy[h] = ay - fy;
+                ix[h] = (int)fmaxf(-2.0f, fminf((float)f.nx + 1.0f, fx));
+                iy[h] = (int)fmaxf(-2.0f, fminf((float)f.ny + 1.0f, fy));
+            }
+        }
+        const int nx = (int)f.nx, ny = (int)f.ny;
         R out[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            // Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j) Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2)
-            const bool hx = (c == 0 || c == 4 || c == 5), hy = (c == 1 || c == 3 || c == 5);
-            const double gx = hx ? gx0 - 0.5 : gx0, gy = hy ? gy0 - 0.5 : gy0;
-            const double fi = floor(gx), fj = floor(gy);
-            const R fx = (R)(gx - fi), fy = (R)(gy - fj);
+            const int hx = (c == 0 || c == 4 || c == 5), hy = (c == 1 || c == 3 || c == 5);
             const float *F = f.yee[c];
             R acc = R(0);
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    const double ii = fi + a, jj = fj + b;
-                    // written so that NaN positions fail the test too
-                    if (!(ii >= 0.0 && jj >= 0.0 && ii < (double)f.nx && jj < (double)f.ny)) continue;
-                    const R wgt = (a ? fx : R(1) - fx) * (b ? fy : R(1) - fy);
-                    acc += wgt * (R)__ldg(F + (int64_t)jj * f.nx + (int64_t)ii);
+                    const int ii = ix[hx] + a, jj = iy[hy] + b;
+                    if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+                    const R wgt = (a ? wx[hx] : R(1) - wx[hx]) * (b ? wy[hy] : R(1) - wy[hy]);
+                    acc += wgt * (R)__ldg(F + (int64_t)jj * nx + ii);
                 }
             }
             out[c] = acc;

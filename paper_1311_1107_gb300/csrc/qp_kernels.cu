@@ -183,6 +183,8 @@ __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepAr
     const bool photons = Ph.present != 0;
     const int64_t ph_base = a.n_start[2];
     bool loaded = false;
+    // blocks beyond the tile count leave before touching the ticket
+    if ((int64_t)blockIdx.x >= n_tiles) return;
 
     for (;;) {
         if (tid == 0) s_ticket = atomicAdd(a.lep.ticket, 1u);
@@ -473,6 +475,7 @@ __global__ void __launch_bounds__(kTile) k_photon(const __grid_constant__ StepAr
     }
     const bool pairs = a.pairs != 0;
     bool loaded = false;
+    if ((int64_t)blockIdx.x >= n_tiles) return;
 
     for (;;) {
         if (tid == 0) s_ticket = atomicAdd(a.pho.ticket, 1u);
