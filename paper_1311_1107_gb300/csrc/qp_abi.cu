@@ -66,7 +66,8 @@ struct qp_ctx {
 
 namespace {
 
-constexpr size_t kTabRate = 3 * (size_t)qp::kNRate;
+// device layout: H Gs Ts rows of kNRatePad entries, then the CDF rows
+constexpr size_t kTabRate = 3 * (size_t)qp::kNRatePad;
 constexpr size_t kTabCdf = 2 * (size_t)qp::kNCdf * qp::kNNode;
 constexpr size_t kTabWords = kTabRate + kTabCdf;
 
@@ -229,11 +230,11 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (c->num_sms < 1) c->num_sms = 1;
 
-    std::vector<double> h64(kTabWords);
+    std::vector<double> h64(kTabWords, 0.0);
     std::vector<float> h32(kTabWords);
     memcpy(h64.data(), T->H, sizeof(T->H));
-    memcpy(h64.data() + qp::kNRate, T->Gs, sizeof(T->Gs));
-    memcpy(h64.data() + 2 * qp::kNRate, T->Ts, sizeof(T->Ts));
+    memcpy(h64.data() + qp::kNRatePad, T->Gs, sizeof(T->Gs));
+    memcpy(h64.data() + 2 * qp::kNRatePad, T->Ts, sizeof(T->Ts));
     memcpy(h64.data() + kTabRate, T->Cg, sizeof(T->Cg));
     memcpy(h64.data() + kTabRate + qp::kNCdf * qp::kNNode, T->Cp, sizeof(T->Cp));
     for (size_t k = 0; k < kTabWords; ++k) h32[k] = (float)h64[k];
@@ -367,7 +368,7 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
         a.f.x0s = f.x0 / f.dx;
         a.f.y0s = f.y0 / f.dy;
     }
-    const size_t R = qp::kNRate, CC = (size_t)qp::kNCdf * qp::kNNode;
+    const size_t R = qp::kNRatePad, CC = (size_t)qp::kNCdf * qp::kNNode;
     a.tab.H = ctx->d_tab64;
     a.tab.Gs = ctx->d_tab64 + R;
     a.tab.Ts = ctx->d_tab64 + 2 * R;
@@ -494,8 +495,8 @@ int qp_export_tables(qp_ctx *ctx, qp_tables_export *out)
                                cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
     memcpy(out->H, h.data(), sizeof(out->H));
-    memcpy(out->Gs, h.data() + qp::kNRate, sizeof(out->Gs));
-    memcpy(out->Ts, h.data() + 2 * qp::kNRate, sizeof(out->Ts));
+    memcpy(out->Gs, h.data() + qp::kNRatePad, sizeof(out->Gs));
+    memcpy(out->Ts, h.data() + 2 * qp::kNRatePad, sizeof(out->Ts));
     memcpy(out->Cg, h.data() + kTabRate, sizeof(out->Cg));
     memcpy(out->Cp, h.data() + kTabRate + qp::kNCdf * qp::kNNode, sizeof(out->Cp));
     out->a_S = ctx->U.a_S;

@@ -9,6 +9,7 @@ namespace qp {
 
 // Table grids (the specification published in qedpic.h).
 constexpr int kNRate = QP_NRATE;        // rate nodes, 32 per octave over [2^-14, 2^10]
+constexpr int kNRatePad = 776;          // device rows padded to a multiple of 16 bytes
 constexpr int kRatePerOct = 32;
 constexpr int kNCdf = QP_NCDF;          // CDF rows, 4 per octave over [2^-14, 2^10]
 constexpr int kCdfPerOct = 4;

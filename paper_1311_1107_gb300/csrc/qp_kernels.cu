@@ -31,37 +31,50 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *((const volatile unsigned long long *)p);
 }
 
-// Exclusive prefix of this tile in its chain (called by one thread).
-// Waits are bounded by spin_limit; on time-out the status is raised and the
-// prefix is taken as what was summed so far (the output is then wrong, the
-// status says so, and the kernel still terminates).
+// Exclusive prefix of this tile in its chain, computed by one full warp
+// (decoupled look-back with a 32-tile window): lane l inspects tile
+// base - l; the window is consumed up to the nearest tile that published its
+// inclusive prefix, summing the aggregates in between.  Waits are bounded by
+// spin_limit; on time-out the status is raised and the prefix is taken as
+// what was summed so far (the output is then wrong, the status says so, and
+// the kernel still terminates).  Returns the prefix in every lane.
 __device__ long long chain_prefix(const ChainDev &ch, unsigned tile, long long aggregate,
                                   unsigned spin_limit, int *status)
 {
+    const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        atomicExch(ch.status, kFlagPre | (unsigned long long)aggregate);
+        if (lane == 0) atomicExch(ch.status, kFlagPre | (unsigned long long)aggregate);
         return 0;
     }
-    atomicExch(ch.status + tile, kFlagAgg | (unsigned long long)aggregate);
+    if (lane == 0) atomicExch(ch.status + tile, kFlagAgg | (unsigned long long)aggregate);
     long long excl = 0;
-    int p = (int)tile - 1;
+    long long base = (long long)tile - 1;
     unsigned spins = 0;
-    while (p >= 0) {
-        const unsigned long long w = ld_volatile(ch.status + p);
+    for (;;) {
+        const long long idx = base - lane;
+        // before tile 0 the chain is complete: read as "prefix 0"
+        const unsigned long long w = idx >= 0 ? ld_volatile(ch.status + idx) : kFlagPre;
         const unsigned long long flag = w & ~kValMask;
-        if (flag == 0) {
+        const unsigned pre = __ballot_sync(0xFFFFFFFFu, flag == kFlagPre);
+        const unsigned empty = __ballot_sync(0xFFFFFFFFu, flag == 0ull);
+        const int first = pre ? __ffs(pre) - 1 : 32;  // nearest inclusive prefix
+        const unsigned need = first == 32 ? 0xFFFFFFFFu : (2u << first) - 1u;
+        if (empty & need) {
             if (++spins > spin_limit) {
-                raise_status(status, QP_ERR_TIMEOUT);
+                if (lane == 0) raise_status(status, QP_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
             continue;
         }
-        excl += (long long)(w & kValMask);
-        if (flag == kFlagPre) break;
-        --p;
+        long long v = lane <= first ? (long long)(w & kValMask) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+        excl += v;
+        if (first < 32) break;
+        base -= 32;
     }
-    atomicExch(ch.status + tile, kFlagPre | (unsigned long long)(excl + aggregate));
+    if (lane == 0) atomicExch(ch.status + tile, kFlagPre | (unsigned long long)(excl + aggregate));
     return excl;
 }
 
@@ -165,8 +178,9 @@ template <int PREC, int FK>
 __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepArgs a)
 {
     using R = typename std::conditional<PREC == kFP64, double, float>::type;
-    __shared__ R s_H[kNRate];
-    __shared__ R s_G[kNRate];
+    __shared__ __align__(16) R s_H[kNRatePad];
+    __shared__ __align__(16) R s_G[kNRatePad];
+    __shared__ __align__(8) unsigned long long s_bar;   // TMA completion of the tables
     __shared__ double s_gg[QP_MAX_EMISSIONS][kTile];   // stashed photon energies
     __shared__ double s_tg[QP_MAX_EMISSIONS][kTile];   // and their optical depths
     __shared__ int s_warp[kWarps];
@@ -192,16 +206,20 @@ __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepAr
         const unsigned tile = s_ticket;
         if ((int64_t)tile >= n_tiles) break;
         if (!loaded) {
-            for (int k = tid; k < kNRate; k += kTile) {
+            // stage the rate tables with one TMA bulk copy each; the copy
+            // overlaps the particle loads, gather and push below
+            if (tid == 0) {
+                const unsigned bytes = kNRatePad * sizeof(R);
+                mbar_init(&s_bar, 1);
+                mbar_expect_tx(&s_bar, 2 * bytes);
                 if constexpr (PREC == kFP64) {
-                    s_H[k] = a.tab.H[k];
-                    s_G[k] = a.tab.Gs[k];
+                    bulk_g2s(s_H, a.tab.H, bytes, &s_bar);
+                    bulk_g2s(s_G, a.tab.Gs, bytes, &s_bar);
                 } else {
-                    s_H[k] = a.tab.Hf[k];
-                    s_G[k] = a.tab.Gsf[k];
+                    bulk_g2s(s_H, a.tab.Hf, bytes, &s_bar);
+                    bulk_g2s(s_G, a.tab.Gsf, bytes, &s_bar);
                 }
             }
-            loaded = true;
             __syncthreads();
         }
         const int sp = (int64_t)tile < tiles_e ? 0 : 1;
@@ -260,6 +278,13 @@ __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepAr
             }
             double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
             const double Ex = E.x, Ey = E.y, Ez = E.z, Bx = B.x, By = B.y, Bz = B.z;
+            if (!loaded) {
+                // tables are needed from here on
+                if (!mbar_wait_bounded(&s_bar, 0, a.spin_limit)) {
+                    raise_status(a.status, QP_ERR_TIMEOUT);
+                    (void)mbar_wait_bounded(&s_bar, 0, a.spin_limit);
+                }
+            }
             const double inv_aS = 1.0 / a.a_S;
             double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, inv_aS);
             if (S.chi) S.chi[i] = chi;
@@ -386,6 +411,15 @@ __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepAr
             if (nph || n_sub) wgt = S.w[i];
         }
 
+        if (!loaded) {
+            // threads without a particle also wait, so the block never leaves
+            // (or reuses the tables) with the copy in flight
+            if (!active && !mbar_wait_bounded(&s_bar, 0, a.spin_limit)) {
+                raise_status(a.status, QP_ERR_TIMEOUT);
+                (void)mbar_wait_bounded(&s_bar, 0, a.spin_limit);
+            }
+            loaded = true;
+        }
         // ---- counters (warp-aggregated into shared memory)
         warp_count(&bs.c[sp][cCont], cont);
         warp_count(&bs.c[sp][cSat], sat);
@@ -401,7 +435,10 @@ __global__ void __launch_bounds__(kTile) k_lepton(const __grid_constant__ StepAr
         // ---- ordered append of the new photons
         int tile_total;
         const int local = block_scan(nph, s_warp, &tile_total);
-        if (tid == 0) s_excl = chain_prefix(a.lep, tile, tile_total, a.spin_limit, a.status);
+        if (tid < 32) {
+            const long long e = chain_prefix(a.lep, tile, tile_total, a.spin_limit, a.status);
+            if (tid == 0) s_excl = e;
+        }
         __syncthreads();
         if (nph) {
             const int64_t base = ph_base + s_excl + local;
@@ -454,7 +491,8 @@ template <int PREC, int FK>
 __global__ void __launch_bounds__(kTile) k_photon(const __grid_constant__ StepArgs a)
 {
     using R = typename std::conditional<PREC == kFP64, double, float>::type;
-    __shared__ R s_T[kNRate];
+    __shared__ __align__(16) R s_T[kNRatePad];
+    __shared__ __align__(8) unsigned long long s_bar;
     __shared__ int s_warp[kWarps];
     __shared__ unsigned s_ticket;
     __shared__ long long s_excl;
@@ -483,14 +521,21 @@ __global__ void __launch_bounds__(kTile) k_photon(const __grid_constant__ StepAr
         const unsigned tile = s_ticket;
         if ((int64_t)tile >= n_tiles) break;
         if (pairs && !loaded) {
-            for (int k = tid; k < kNRate; k += kTile) {
+            if (tid == 0) {
+                const unsigned bytes = kNRatePad * sizeof(R);
+                mbar_init(&s_bar, 1);
+                mbar_expect_tx(&s_bar, bytes);
                 if constexpr (PREC == kFP64)
-                    s_T[k] = a.tab.Ts[k];
+                    bulk_g2s(s_T, a.tab.Ts, bytes, &s_bar);
                 else
-                    s_T[k] = a.tab.Tsf[k];
+                    bulk_g2s(s_T, a.tab.Tsf, bytes, &s_bar);
+            }
+            __syncthreads();
+            if (!mbar_wait_bounded(&s_bar, 0, a.spin_limit)) {
+                raise_status(a.status, QP_ERR_TIMEOUT);
+                (void)mbar_wait_bounded(&s_bar, 0, a.spin_limit);
             }
             loaded = true;
-            __syncthreads();
         }
         const int64_t i = (int64_t)tile * kTile + tid;
         int npair = 0;
@@ -577,7 +622,10 @@ __global__ void __launch_bounds__(kTile) k_photon(const __grid_constant__ StepAr
         if (pairs) {
             int tile_total;
             const int local = block_scan(npair, s_warp, &tile_total);
-            if (tid == 0) s_excl = chain_prefix(a.pho, tile, tile_total, a.spin_limit, a.status);
+            if (tid < 32) {
+                const long long e = chain_prefix(a.pho, tile, tile_total, a.spin_limit, a.status);
+                if (tid == 0) s_excl = e;
+            }
             __syncthreads();
             if (npair) {
                 const int64_t ord = s_excl + local;
@@ -630,8 +678,9 @@ __global__ void __launch_bounds__(kTile) k_photon(const __grid_constant__ StepAr
 // give up, raise QP_ERR_TIMEOUT and return.
 __global__ void k_wait_selftest(ChainDev ch, unsigned spin_limit, int *status)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        ch.status[0] = 0ull;
+    if (threadIdx.x < 32 && blockIdx.x == 0) {
+        if (threadIdx.x == 0) ch.status[0] = 0ull;
+        __syncwarp();
         (void)chain_prefix(ch, 1u, 0, spin_limit, status);
     }
 }
