@@ -253,6 +253,32 @@ typedef struct {
  * (caller-owned).  Synchronous. */
 int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
 
+/*
+ * Allocation-free diagnostics, for callers that cannot allocate device
+ * memory: code that runs while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), or a host application whose device memory is
+ * owned by its own pool allocator and must not be allocated behind its back.
+ * It needs no context: the caller passes the species' buffers (`d`, device
+ * pointers as for qp_create_species) and a host `out`, and gets the same
+ * state reductions as qp_diagnostics (n_live, n_alive, weight, energy,
+ * momentum, chi_mean, hist; equal to within rounding, the partition of the
+ * sums differs).  The event counters and `status` are context data and come
+ * back as 0.
+ * Scratch is a static device array of the library sized for
+ * QP_NOALLOC_MAX_TILES tiles of 256 slots (QP_NOALLOC_MAX_SLOTS slots, about
+ * 2.4 MB), which every GPU that loads the library holds until the process
+ * exits.  A species whose capacity exceeds QP_NOALLOC_MAX_SLOTS is rejected
+ * with QP_ERR_INVALID_ARG before anything is enqueued.  The first call on a
+ * device looks the array up on that device (make it before any stream
+ * capture).  Every call overwrites the part of the array it reads, but all
+ * calls share it: calls that overlap on the GPU (other streams, no ordering
+ * between them) race and return wrong results.  Synchronises `stream`.
+ * The paper has no counterpart: this is plumbing of the library.
+ */
+#define QP_NOALLOC_MAX_TILES 4096
+#define QP_NOALLOC_MAX_SLOTS (QP_NOALLOC_MAX_TILES * 256)
+int qp_diagnostics_noalloc(const qp_species_desc *d, qp_diag *out, void *stream);
+
 /* Reset the species' event counters and the context's sticky status. */
 int qp_reset_counters(qp_ctx *ctx, int32_t handle);
 

@@ -98,7 +98,7 @@ _lib = None
 EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
            "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
            "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
-           "qp_status_string")
+           "qp_diagnostics_noalloc", "qp_status_string")
 
 
 def library_path() -> str:
@@ -125,6 +125,7 @@ def lib(build_if_missing: bool = False):
         L.qp_init_optical_depth.argtypes = [vp, i32, C.c_uint64, i64, i64, vp]
         L.qp_step.argtypes = [vp, C.POINTER(qp_step_params), vp]
         L.qp_diagnostics.argtypes = [vp, i32, C.POINTER(qp_diag), vp]
+        L.qp_diagnostics_noalloc.argtypes = [C.POINTER(qp_species_desc), C.POINTER(qp_diag), vp]
         L.qp_export_tables.argtypes = [vp, C.POINTER(qp_tables_export)]
         L.qp_reset_counters.argtypes = [vp, i32]
         L.qp_selftest_wait_timeout.argtypes = [vp, C.c_uint32]
@@ -183,6 +184,17 @@ def qp_diagnostics(ctx, handle: int, stream=None) -> qp_diag:
     if st < 0 and d.status != st:
         raise QPError("qp_diagnostics", st)
     return d
+
+
+def qp_diagnostics_noalloc(desc: qp_species_desc, stream=None) -> qp_diag:
+    """Allocation-free reduction of one species (no context; see the header:
+    a static scratch array limits the species to QP_NOALLOC_MAX_SLOTS)."""
+    d = qp_diag()
+    _check("qp_diagnostics_noalloc", lib().qp_diagnostics_noalloc(C.byref(desc), C.byref(d), stream))
+    return d
+
+
+QP_NOALLOC_MAX_SLOTS = 4096 * 256
 
 
 def qp_export_tables(ctx) -> qp_tables_export:

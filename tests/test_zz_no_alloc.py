@@ -1,0 +1,70 @@
+"""qp_diagnostics_noalloc against qp_diagnostics (GPU only).
+
+The allocation-free entry point serves callers that cannot allocate device
+memory (for instance while a CUDA graph is being captured, or when the host
+application's pool owns all device memory).  It must give the same species
+reductions as the context-based qp_diagnostics, call after call, although
+every call shares one static scratch array.  This file is collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1311_1107_gb300 import qedpic as Q
+from paper_1311_1107_gb300 import workloads as W
+from paper_1311_1107_gb300.sim import Simulation
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+FIELDS = ("weight", "energy", "px", "py", "pz", "chi_mean")
+
+
+def _same(a, b):
+    assert a.n_live == b.n_live and a.n_alive == b.n_alive
+    for f in FIELDS:
+        x, y = getattr(a, f), getattr(b, f)
+        assert x == pytest.approx(y, rel=RTOL, abs=1e-12 * max(1.0, abs(y))), f
+    np.testing.assert_allclose(np.array(a.hist), np.array(b.hist), rtol=RTOL, atol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.beam_collision(n=3000, n_steps=120, buffer=200_000)
+    s = Simulation(w)
+    s.run(120)
+    torch.cuda.synchronize()
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["electron", "photon"])
+def test_noalloc_matches_context_diagnostics_twice(sim, name):
+    sp = sim.species[name]
+    assert sp.count() > 0
+    ref = sim.diagnostics(name)
+    first = Q.qp_diagnostics_noalloc(sp._desc)
+    second = Q.qp_diagnostics_noalloc(sp._desc)
+    _same(first, ref)
+    _same(second, ref)
+    assert first.n_emit == 0 and first.status == 0   # context data is not reported
+
+
+def test_noalloc_alternating_species_share_the_scratch(sim):
+    el, ph = sim.species["electron"], sim.species["photon"]
+    ref_e, ref_p = sim.diagnostics("electron"), sim.diagnostics("photon")
+    for _ in range(2):
+        _same(Q.qp_diagnostics_noalloc(ph._desc), ref_p)
+        _same(Q.qp_diagnostics_noalloc(el._desc), ref_e)
+
+
+def test_noalloc_rejects_capacity_above_its_scratch(sim):
+    d = Q.qp_species_desc.from_buffer_copy(sim.species["electron"]._desc)
+    d.capacity = Q.QP_NOALLOC_MAX_SLOTS + 1
+    out = Q.qp_diag()
+    assert Q.lib().qp_diagnostics_noalloc(C.byref(d), C.byref(out), None) == Q.QP_ERR_INVALID_ARG
