@@ -196,24 +196,22 @@ def run_path(w, precision, steps, warmup, dev, dist, flush):
 
 
 def roofline(res, dims, pairs, hbm_peak, peak_kind):
+    """Roofline of k_step (the only kernel of a step): algorithmic bytes of
+    all lepton and photon slot-steps and appended particles in the timed
+    steps, over the summed k_step device time (CUDA events on its stream)."""
     lep_b, pho_b, new_b = species_bytes(dims, pairs)
-    lep_bytes = res["lep_slots"] * lep_b + res["photons_added"] * new_b
-    pho_bytes = res["pho_slots"] * pho_b + 2 * res["pairs_added"] * new_b
-    ms = res["kernel_ms"]
-    cand = []
-    if ms[1] > 0:
-        cand.append(("k_lepton", lep_bytes, ms[1], res["launches"][1]))
-    if ms[2] > 0:
-        cand.append(("k_photon", pho_bytes, ms[2], res["launches"][2]))
-    name, b, t, n = max(cand, key=lambda x: x[2])
-    achieved = b / (t * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+    nbytes = (res["lep_slots"] * lep_b + res["pho_slots"] * pho_b
+              + (res["photons_added"] + 2 * res["pairs_added"]) * new_b)
+    t_ms = res["kernel_ms"][0]
+    n = max(res["launches"][0], 1)
+    achieved = nbytes / (t_ms * 1e-3) / 1e9
+    return {"kernel": "k_step", "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
             "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
-            "bytes_per_launch": round(b / max(n, 1)), "avg_launch_us": round(t * 1e3 / max(n, 1), 3),
-            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
-            else "fallback 6.8 TB/s", "kernel_share": {
-                "k_step_begin": round(ms[0] / sum(ms), 4), "k_lepton": round(ms[1] / sum(ms), 4),
-                "k_photon": round(ms[2] / sum(ms), 4)}}
+            "bytes_per_launch": round(nbytes / n), "avg_launch_us": round(t_ms * 1e3 / n, 3),
+            "bytes_model": f"{lep_b} B per lepton slot-step, {pho_b} B per photon slot-step, "
+                           f"{new_b} B per appended particle",
+            "peak_source": ("measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
+                            else "fallback 6.8 TB/s")}
 
 
 def e2e(w, precision, steps, dev):

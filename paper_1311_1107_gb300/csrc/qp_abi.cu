@@ -49,14 +49,13 @@ struct qp_ctx {
     double *d_tab64 = nullptr;
     float *d_tab32 = nullptr;
     qp::DevStats *d_stats = nullptr;  // [kMaxSpecies]
-    int64_t *d_n_start = nullptr;     // [3]
-    unsigned *d_tickets = nullptr;    // [2]
+    qp::StepCtl *d_ctl = nullptr;     // ticket, done, epoch, pending counts
     int *d_status = nullptr;
     unsigned long long *d_chain = nullptr;  // lepton chain then photon chain
     size_t chain_words = 0;           // words per chain
     double *d_diag = nullptr;         // partials + final
     std::vector<SpeciesRec> species;
-    int grid_cache[2][2][5];          // [precision][photon][field] blocks per SM, 0 = unknown
+    int grid_cache[2][5];             // [precision][field] blocks per SM, 0 = unknown
     // kernel timing (qp_profile_*): event pool and (kernel, start event) records
     bool profiling = false;
     std::vector<cudaEvent_t> events;
@@ -88,8 +87,7 @@ void release(qp_ctx *c)
     cudaFree(c->d_tab64);
     cudaFree(c->d_tab32);
     cudaFree(c->d_stats);
-    cudaFree(c->d_n_start);
-    cudaFree(c->d_tickets);
+    cudaFree(c->d_ctl);
     cudaFree(c->d_status);
     cudaFree(c->d_chain);
     cudaFree(c->d_diag);
@@ -254,8 +252,8 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
     QP_TRY(cudaMemcpy(c->d_tab32, h32.data(), kTabWords * sizeof(float), cudaMemcpyHostToDevice));
     QP_TRY(cudaMalloc(&c->d_stats, kMaxSpecies * sizeof(qp::DevStats)));
     QP_TRY(cudaMemset(c->d_stats, 0, kMaxSpecies * sizeof(qp::DevStats)));
-    QP_TRY(cudaMalloc(&c->d_n_start, 4 * sizeof(int64_t)));
-    QP_TRY(cudaMalloc(&c->d_tickets, 2 * sizeof(unsigned)));
+    QP_TRY(cudaMalloc(&c->d_ctl, sizeof(qp::StepCtl)));
+    QP_TRY(cudaMemset(c->d_ctl, 0, sizeof(qp::StepCtl)));
     QP_TRY(cudaMalloc(&c->d_status, sizeof(int)));
     QP_TRY(cudaMemset(c->d_status, 0, sizeof(int)));
     QP_TRY(cudaMalloc(&c->d_diag, (qp::kDiagBlocks + 1) * qp::kDiagWords * sizeof(double)));
@@ -379,11 +377,9 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     a.tab.Tsf = ctx->d_tab32 + 2 * R;
     a.tab.Cgf = ctx->d_tab32 + 3 * R;
     a.tab.Cpf = ctx->d_tab32 + 3 * R + CC;
-    a.lep.status = ctx->d_chain;
-    a.lep.ticket = ctx->d_tickets;
-    a.pho.status = ctx->d_chain + ctx->chain_words;
-    a.pho.ticket = ctx->d_tickets + 1;
-    a.n_start = ctx->d_n_start;
+    a.lep_words = ctx->d_chain;
+    a.pho_words = ctx->d_chain + ctx->chain_words;
+    a.ctl = ctx->d_ctl;
     a.stats = ctx->d_stats;
     a.status = ctx->d_status;
     a.dt = s->dt;
@@ -397,36 +393,21 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     a.max_emit = s->max_emissions;
     a.spin_limit = kSpinLimit;
 
-    // persistent grids: resident blocks, never more than the tiles the
+    // persistent grid: resident blocks, never more than the tiles the
     // registered capacities allow
     const int prec = s->precision == QP_MIXED ? 1 : 0;
-    int &bl = ctx->grid_cache[prec][0][f.kind];
-    int &bp = ctx->grid_cache[prec][1][f.kind];
-    if (!bl) bl = qp::step_blocks_per_sm(s->precision, false, f.kind);
-    if (!bp) bp = qp::step_blocks_per_sm(s->precision, true, f.kind);
-    int64_t lep_tiles = 0;
-    for (int k = 0; k < 2; ++k)
-        if (hs[k] != -1) lep_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
-    const int64_t ph_tiles = hs[2] != -1 ? (int64_t)tiles_of(ctx->species[hs[2]].d.capacity) : 0;
-    const int64_t res_l = (int64_t)bl * ctx->num_sms, res_p = (int64_t)bp * ctx->num_sms;
-    const int grid_lep = (int)(lep_tiles < res_l ? (lep_tiles > 0 ? lep_tiles : 1) : res_l);
-    const int grid_ph = (int)(ph_tiles < res_p ? (ph_tiles > 0 ? ph_tiles : 1) : res_p);
-    const bool do_lep = hs[0] != -1 || hs[1] != -1;
-    const bool do_ph = hs[2] != -1;
-    const int grid_begin = 2 * ctx->num_sms;
+    int &bpsm = ctx->grid_cache[prec][f.kind];
+    if (!bpsm) bpsm = qp::step_blocks_per_sm(s->precision, f.kind);
+    int64_t cap_tiles = 0;
+    for (int k = 0; k < 3; ++k)
+        if (hs[k] != -1) cap_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
+    const int64_t resident = (int64_t)bpsm * ctx->num_sms;
+    const int grid = (int)(cap_tiles < resident ? (cap_tiles > 0 ? cap_tiles : 1) : resident);
     cudaStream_t st = (cudaStream_t)stream;
     for (int32_t k = 0; k < s->n_steps; ++k) {
         a.step = (uint64_t)(s->step + k);
         a.t = (double)(s->step + k) * s->dt;
-        cudaError_t e = timed(ctx, 0, st, [&] { return qp::launch_step_begin(a, grid_begin, st); });
-        if (e == cudaSuccess && do_lep)
-            e = timed(ctx, 1, st, [&] {
-                return qp::launch_species_kernel(a, s->precision, false, grid_lep, st);
-            });
-        if (e == cudaSuccess && do_ph)
-            e = timed(ctx, 2, st, [&] {
-                return qp::launch_species_kernel(a, s->precision, true, grid_ph, st);
-            });
+        cudaError_t e = timed(ctx, 0, st, [&] { return qp::launch_step(a, s->precision, grid, st); });
         if (e != cudaSuccess) return cuda_status(e);
     }
     return QP_OK;
@@ -555,12 +536,13 @@ int qp_selftest_wait_timeout(qp_ctx *ctx, uint32_t spin_limit)
     if (!g.ok) return QP_ERR_CUDA;
     cudaError_t e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_chain, 0, 2 * sizeof(unsigned long long));
-    qp::ChainDev ch{ctx->d_chain, ctx->d_tickets};
-    if (e == cudaSuccess) e = qp::launch_wait_selftest(ch, spin_limit, ctx->d_status, 0);
+    if (e == cudaSuccess) e = qp::launch_wait_selftest(ctx->d_chain, spin_limit, ctx->d_status, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     int status = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    // the test wrote look-back words with a made-up epoch: clear them
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_chain, 0, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_status(e);
     return status;
 }

@@ -44,26 +44,30 @@ struct TablesDev {
     const float *Hf, *Gsf, *Tsf, *Cgf, *Cpf;   // FP32 copies
 };
 
-// Scan scratch of one append chain (decoupled look-back).
-struct ChainDev {
-    unsigned long long *status;  // one word per tile: flag (2 bits) | value (62 bits)
-    unsigned int *ticket;        // dynamic tile counter
+// Device-resident control block of a context's steps: the tile ticket, the
+// count of finished blocks, the launch epoch that tags look-back words, and
+// the new live counts (e-, e+, photons) applied by the last block.
+struct StepCtl {
+    unsigned ticket, done, epoch, pad;
+    long long pending[3];
+    long long pad2;
 };
 
 struct StepArgs {
-    SpeciesDev sp[3];            // electron, positron, photon
+    SpeciesDev sp[3];                 // electron, positron, photon
     FieldDev f;
     TablesDev tab;
-    ChainDev lep, pho;
-    int64_t *n_start;            // [3] live counts at the start of the step
-    DevStats *stats;             // [3] counters of the three species
-    int *status;                 // sticky status word
+    unsigned long long *lep_words;    // look-back words of the lepton chain
+    unsigned long long *pho_words;    // look-back words of the photon chain
+    StepCtl *ctl;
+    DevStats *stats;                  // counters, indexed by species handle
+    int *status;                      // sticky status word
     double dt, t;
     uint64_t step, seed;
     double chi_th, gmin;
     double a_S, C_rate, tau0w;
     int32_t pairs, max_emit;
-    unsigned int spin_limit;     // bound of every look-back wait
+    unsigned int spin_limit;          // bound of every device-side wait
 };
 
 // ------------------------------------------------------------------ status

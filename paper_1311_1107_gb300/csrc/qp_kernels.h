@@ -7,15 +7,14 @@
 
 namespace qp {
 
-cudaError_t launch_step_begin(const StepArgs &a, int grid, cudaStream_t st);
-cudaError_t launch_species_kernel(const StepArgs &a, int precision, bool photon, int grid,
-                                  cudaStream_t st);
+cudaError_t launch_step(const StepArgs &a, int precision, int grid, cudaStream_t st);
+int step_blocks_per_sm(int precision, int field_kind);
+size_t step_smem_bytes(int precision);
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, uint64_t seed, int species,
                             cudaStream_t st);
 cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, int nblocks,
                         double *out, cudaStream_t st);
-int step_blocks_per_sm(int precision, bool photon, int field_kind);
-cudaError_t launch_wait_selftest(const ChainDev &ch, unsigned spin_limit, int *status,
+cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit, int *status,
                                  cudaStream_t st);
 
 constexpr int kDiagBlocks = 256;
