@@ -114,6 +114,10 @@ typedef struct {
     double *w;          /* super-particle weight                                 */
     double *chi;        /* optional (may be NULL): chi of the particle's last
                            step (chi_e, or chi_gamma for photons above 2 m c^2)  */
+    int32_t *nemit;     /* optional (may be NULL): events caused by the particle,
+                           accumulated over steps (emissions of a lepton, stored
+                           or not; 1 for a photon that decayed into a pair);
+                           set to 0 for particles the library appends          */
     int64_t *n_live;    /* device counter of live slots; the library updates it
                            when it appends; the caller sets its initial value    */
 } qp_species_desc;

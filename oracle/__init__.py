@@ -74,7 +74,7 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("step", C.c_int64), ("seed", C.c_uint64),
                 ("chi_th", C.c_double), ("photon_min_gamma", C.c_double),
                 ("pairs", C.c_int32), ("max_emit", C.c_int32), ("recoil", C.c_int32),
-                ("dims", C.c_int32)]
+                ("dims", C.c_int32), ("noise", C.c_double), ("noise_key", C.c_uint64)]
 
 
 class Stats(C.Structure):
@@ -398,6 +398,8 @@ class Sim:
         self.P.max_emit = int(params.get("max_emit", 8))
         self.P.recoil = int(params.get("recoil", 1))
         self.P.dims = int(params.get("dims", 3))
+        self.P.noise = float(params.get("noise", 0.0))
+        self.P.noise_key = int(params.get("noise_key", 0))
         self.sp = [electrons, positrons, photons]
         self.stats = Stats()
 

@@ -738,6 +738,10 @@ typedef struct {
     int32_t max_emit;        /* emissions allowed per particle per step      */
     int32_t recoil;          /* 1 = apply Eq. 8 (0 only for spectrum tests)  */
     int32_t dims;            /* 2 or 3                                       */
+    double noise;            /* test-only sensitivity probe: relative kick of
+                                +-noise given to each lepton's momentum after
+                                every step (0 = the method itself)           */
+    uint64_t noise_key;      /* selects an independent pattern of kick signs  */
 } or_params;
 
 typedef struct {
@@ -810,6 +814,11 @@ static void or_lepton_step(const or_units *U, const or_tables *T, const or_field
     double chi = or_chi_e(E, B, u, gam, U->a_S);
     if (S->chi) S->chi[i] = chi;
     double dv[3] = {0.0, 0.0, 0.0};
+    /* the regime choice is a decision too: record how close it was */
+    if (S->margin && P->chi_th > 0.0) {
+        double m = fabs(chi - P->chi_th) / P->chi_th;
+        if (m < S->margin[i]) S->margin[i] = m;
+    }
 
     if (chi < P->chi_th) {
         /* Eq. 4-5, continuous regime: f_l = q (E + v x B),
@@ -897,6 +906,13 @@ static void or_lepton_step(const or_units *U, const or_tables *T, const or_field
 
     /* Eq. 4: dx/dt = v + dv */
     for (int c = 0; c < 3; c++) x[c] = x[c] + dt * (u[c] / gam + dv[c]);
+    if (P->noise != 0.0) {
+        /* test-only: deterministic +-noise kick (sign from the slot and step) */
+        uint32_t rn[4];
+        or_draw(P->seed ^ 0x5EEDull ^ (P->noise_key * 0x9E3779B97F4A7C15ull), species, 7,
+                or_id(S, i), P->step, 0, rn);
+        for (int c = 0; c < 3; c++) u[c] *= 1.0 + ((rn[c] & 1u) ? P->noise : -P->noise);
+    }
     S->x[i] = x[0];
     S->y[i] = x[1];
     if (S->z) S->z[i] = x[2];
@@ -961,6 +977,7 @@ static void or_photon_step(const or_units *U, const or_tables *T, const or_field
             double omv = 1.0 - v;
             double up[3] = {omv * u[0], omv * u[1], omv * u[2]};
             st->n_pair++;
+            if (Ph->nemit) Ph->nemit[i]++;
             int64_t ord = (*pair_ord)++;
             int64_t se = be + ord, sp = bp + ord;
             if (El && Po && se < El->cap && sp < Po->cap) {

@@ -69,6 +69,9 @@ namespace {
 constexpr size_t kTabRate = 3 * (size_t)qp::kNRatePad;
 constexpr size_t kTabCdf = 2 * (size_t)qp::kNCdf * qp::kNNode;
 constexpr size_t kTabWords = kTabRate + kTabCdf;
+// FP32 layout: the rate rows, the CDF rows and their complements as float
+// pairs (4 kTabCdf floats), then e^(-s_j) at the 2 x kNNode logit nodes
+constexpr size_t kTab32 = kTabRate + 4 * kTabCdf + 2 * (size_t)qp::kNNode;
 
 int cuda_status(cudaError_t e)
 {
@@ -177,6 +180,7 @@ qp::SpeciesDev species_dev(const qp_ctx *c, int32_t h)
     s.tau = d.tau;
     s.w = d.w;
     s.chi = d.chi;
+    s.nemit = d.nemit;
     s.n_live = d.n_live;
     s.cap = d.capacity;
     s.present = 1;
@@ -229,13 +233,29 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
     if (c->num_sms < 1) c->num_sms = 1;
 
     std::vector<double> h64(kTabWords, 0.0);
-    std::vector<float> h32(kTabWords);
+    std::vector<float> h32(kTab32);
     memcpy(h64.data(), T->H, sizeof(T->H));
     memcpy(h64.data() + qp::kNRatePad, T->Gs, sizeof(T->Gs));
     memcpy(h64.data() + 2 * qp::kNRatePad, T->Ts, sizeof(T->Ts));
     memcpy(h64.data() + kTabRate, T->Cg, sizeof(T->Cg));
     memcpy(h64.data() + kTabRate + qp::kNCdf * qp::kNNode, T->Cp, sizeof(T->Cp));
-    for (size_t k = 0; k < kTabWords; ++k) h32[k] = (float)h64[k];
+    for (size_t k = 0; k < kTabRate; ++k) h32[k] = (float)h64[k];
+    // CDF rows (emission then pair) as hi + lo pairs, then their complements
+    for (size_t k = 0; k < kTabCdf; ++k) {
+        const double c = h64[kTabRate + k], q = 1.0 - c;
+        const float ch = (float)c, qh = (float)q;
+        h32[kTabRate + 2 * k] = ch;
+        h32[kTabRate + 2 * k + 1] = (float)(c - (double)ch);
+        h32[kTabRate + 2 * kTabCdf + 2 * k] = qh;
+        h32[kTabRate + 2 * kTabCdf + 2 * k + 1] = (float)(q - (double)qh);
+    }
+    // e^(-s_j) at the logit nodes of the emission and pair rows
+    for (int j = 0; j < qp::kNNode; ++j) {
+        h32[kTabRate + 4 * kTabCdf + j] =
+            (float)exp(-(qp::kSgMin + qp::kSgSpan * j / (qp::kNNode - 1)));
+        h32[kTabRate + 4 * kTabCdf + qp::kNNode + j] =
+            (float)exp(-(qp::kSpMin + qp::kSpSpan * j / (qp::kNNode - 1)));
+    }
 
     cudaError_t e = cudaSuccess;
 #define QP_TRY(x)                    \
@@ -247,9 +267,10 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
         }                            \
     } while (0)
     QP_TRY(cudaMalloc(&c->d_tab64, kTabWords * sizeof(double)));
-    QP_TRY(cudaMalloc(&c->d_tab32, kTabWords * sizeof(float)));
+    QP_TRY(cudaMalloc(&c->d_tab32, kTab32 * sizeof(float)));
     QP_TRY(cudaMemcpy(c->d_tab64, h64.data(), kTabWords * sizeof(double), cudaMemcpyHostToDevice));
-    QP_TRY(cudaMemcpy(c->d_tab32, h32.data(), kTabWords * sizeof(float), cudaMemcpyHostToDevice));
+    QP_TRY(cudaMemcpy(c->d_tab32, h32.data(), kTab32 * sizeof(float),
+                      cudaMemcpyHostToDevice));
     QP_TRY(cudaMalloc(&c->d_stats, kMaxSpecies * sizeof(qp::DevStats)));
     QP_TRY(cudaMemset(c->d_stats, 0, kMaxSpecies * sizeof(qp::DevStats)));
     QP_TRY(cudaMalloc(&c->d_ctl, sizeof(qp::StepCtl)));
@@ -326,8 +347,9 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     if (f.kind == QP_FIELD_GAUSSIAN && (!(f.w0 > 0.0) || !(f.tau_fwhm > 0.0)))
         return QP_ERR_INVALID_ARG;
     if (f.kind == QP_FIELD_YEE2D) {
-        if (f.nx < 1 || f.ny < 1 || f.nx > (1 << 30) || f.ny > (1 << 30) || !(f.dx > 0.0) ||
-            !(f.dy > 0.0) || f.nx * f.ny > ((int64_t)1 << 40))
+        // node indices are 32-bit: nx * ny (plus a row) must stay below 2^31
+        if (f.nx < 1 || f.ny < 1 || f.nx > (1 << 24) || f.ny > (1 << 24) || !(f.dx > 0.0) ||
+            !(f.dy > 0.0) || (f.nx + 2) * (f.ny + 2) >= ((int64_t)1 << 31))
             return QP_ERR_INVALID_ARG;
         for (int k = 0; k < 6; ++k)
             if (!f.yee[k]) return QP_ERR_INVALID_ARG;
@@ -375,8 +397,13 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     a.tab.Hf = ctx->d_tab32;
     a.tab.Gsf = ctx->d_tab32 + R;
     a.tab.Tsf = ctx->d_tab32 + 2 * R;
-    a.tab.Cgf = ctx->d_tab32 + 3 * R;
-    a.tab.Cpf = ctx->d_tab32 + 3 * R + CC;
+    const float2 *c2 = reinterpret_cast<const float2 *>(ctx->d_tab32 + kTabRate);
+    a.tab.Cg2 = c2;
+    a.tab.Cp2 = c2 + CC;
+    a.tab.Qg2 = c2 + 2 * CC;
+    a.tab.Qp2 = c2 + 3 * CC;
+    a.tab.Eg = ctx->d_tab32 + kTabRate + 4 * kTabCdf;
+    a.tab.Ep = a.tab.Eg + qp::kNNode;
     a.lep_words = ctx->d_chain;
     a.pho_words = ctx->d_chain + ctx->chain_words;
     a.ctl = ctx->d_ctl;
@@ -403,10 +430,50 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
         if (hs[k] != -1) cap_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
     const int64_t resident = (int64_t)bpsm * ctx->num_sms;
     const int grid = (int)(cap_tiles < resident ? (cap_tiles > 0 ? cap_tiles : 1) : resident);
+    // constants of the mixed path (FP32, or double-float pairs split here)
+    auto hi_of = [](double v) { return (float)v; };
+    auto lo_of = [](double v) { return (float)(v - (double)(float)v); };
+    qp::MixedConsts &m = a.mc;
+    m.xf_hi = hi_of(f.x_focus);
+    m.xf_lo = lo_of(f.x_focus);
+    if (f.kind == QP_FIELD_YEE2D) {
+        m.idx_hi = hi_of(a.f.inv_dx);
+        m.idx_lo = lo_of(a.f.inv_dx);
+        m.idy_hi = hi_of(a.f.inv_dy);
+        m.idy_lo = lo_of(a.f.inv_dy);
+        m.x0s_hi = hi_of(a.f.x0s);
+        m.x0s_lo = lo_of(a.f.x0s);
+        m.y0s_hi = hi_of(a.f.y0s);
+        m.y0s_lo = lo_of(a.f.y0s);
+        m.nxf = (float)f.nx;
+        m.nyf = (float)f.ny;
+    }
+    m.h[0] = (float)(-0.5 * s->dt);
+    m.h[1] = (float)(0.5 * s->dt);
+    m.dt = (float)s->dt;
+    m.C_rate = (float)ctx->U.C_rate;
+    m.inv_aS = (float)(1.0 / ctx->U.a_S);
+    m.inv_aS_lo = (float)(1.0 / ctx->U.a_S - (double)m.inv_aS);
+    m.tau0w = (float)ctx->U.tau0w;
+    m.chi_th = (float)s->chi_threshold;
+    m.gmin = (float)s->photon_min_gamma;
+    m.a0 = (float)f.a0;
+    m.b0 = (float)f.b0;
+    if (f.kind == QP_FIELD_GAUSSIAN) {
+        const double zr = 0.5 * f.w0 * f.w0;
+        m.zr = (float)zr;
+        m.inv_zr = (float)(1.0 / zr);
+        m.inv_w0sq = (float)(1.0 / (f.w0 * f.w0));
+        m.k_env = (float)(2.0 * 0.6931471805599453 / (f.tau_fwhm * f.tau_fwhm));
+    }
     cudaStream_t st = (cudaStream_t)stream;
     for (int32_t k = 0; k < s->n_steps; ++k) {
         a.step = (uint64_t)(s->step + k);
         a.t = (double)(s->step + k) * s->dt;
+        m.t_hi = hi_of(a.t);
+        m.t_lo = lo_of(a.t);
+        m.tr_hi = hi_of(a.t - f.t_focus);
+        m.tr_lo = lo_of(a.t - f.t_focus);
         cudaError_t e = timed(ctx, 0, st, [&] { return qp::launch_step(a, s->precision, grid, st); });
         if (e != cudaSuccess) return cuda_status(e);
     }

@@ -10,13 +10,15 @@
 namespace qp {
 
 enum Prec { kFP64 = 0, kMixed = 1 };
-constexpr int kTile = 256;   // particles per tile = threads per block
+constexpr int kTile = 128;      // particles per step tile = threads per block
 constexpr int kWarps = kTile / 32;
+constexpr int kDiagTile = 256;  // slots per block tile of the diagnostics
 
 // ------------------------------------------------------------------ layout
 
 struct SpeciesDev {
     double *x, *y, *z, *ux, *uy, *uz, *tau, *w, *chi;
+    int32_t *nemit;
     int64_t *n_live;
     int64_t cap;
     int32_t present;
@@ -41,7 +43,26 @@ struct FieldDev {
 
 struct TablesDev {
     const double *H, *Gs, *Ts, *Cg, *Cp;       // FP64
-    const float *Hf, *Gsf, *Tsf, *Cgf, *Cpf;   // FP32 copies
+    const float *Hf, *Gsf, *Tsf;               // FP32 copies of the rate rows
+    // CDF rows C and their complements Q = 1 - C as hi + lo float pairs
+    const float2 *Cg2, *Cp2, *Qg2, *Qp2;
+    const float *Eg, *Ep;                      // e^(-s_j) at the logit nodes
+};
+
+// Step constants of the mixed path as FP32 values or double-float pairs
+// (split on the host), so the kernel needs no FP64 arithmetic for them.
+struct MixedConsts {
+    float t_hi, t_lo;           // t = n dt
+    float tr_hi, tr_lo;         // t - t_focus (Gaussian pulse)
+    float xf_hi, xf_lo;         // x_focus
+    float idx_hi, idx_lo, idy_hi, idy_lo;  // 1/dx, 1/dy (Yee grid)
+    float x0s_hi, x0s_lo, y0s_hi, y0s_lo;  // x0/dx, y0/dy
+    float h[2];                 // 0.5 q dt for electrons, positrons
+    float dt, C_rate, inv_aS, tau0w, chi_th, gmin;
+    float inv_aS_lo;            // 1/a_S - inv_aS: chi is scaled by the pair, so
+                                // that no rounding of the constant biases every chi
+    float a0, b0, zr, inv_zr, inv_w0sq, k_env;  // field shape (k_env = 2 ln2 / tau_fwhm^2)
+    float nxf, nyf;                            // Yee grid size
 };
 
 // Device-resident control block of a context's steps: the tile ticket, the
@@ -68,6 +89,7 @@ struct StepArgs {
     double a_S, C_rate, tau0w;
     int32_t pairs, max_emit;
     unsigned int spin_limit;          // bound of every device-side wait
+    MixedConsts mc;
 };
 
 // ------------------------------------------------------------------ status
@@ -182,6 +204,70 @@ struct Vec3 {
     R x, y, z;
 };
 
+// Linear interpolation of the Yee components on their four staggered
+// stencils (node/half-node in x and y): stencil (hx, hy) serves
+// (0,0) Ez, (1,0) Ex and By, (0,1) Ey and Bx, (1,1) Bz.  Each stencil is
+// bounds-checked once; nodes outside the grid contribute zero field.  The
+// sum over the four nodes runs in the order (i,j), (i+1,j), (i,j+1),
+// (i+1,j+1).
+template <typename R>
+struct YeeStencil {
+    int base;      // index of node (i, j)
+    int ix, iy;
+    bool inside;   // all four nodes inside the grid
+    R wx, wy;
+};
+
+template <typename R>
+__device__ __forceinline__ R yee_interp(const float *__restrict__ F, const YeeStencil<R> &st,
+                                        int nx, int ny)
+{
+    const R w00 = (R(1) - st.wx) * (R(1) - st.wy), w10 = st.wx * (R(1) - st.wy);
+    const R w01 = (R(1) - st.wx) * st.wy, w11 = st.wx * st.wy;
+    if (st.inside) {
+        const float *p = F + st.base;
+        R acc = R(0);
+        acc += w00 * (R)__ldg(p);
+        acc += w10 * (R)__ldg(p + 1);
+        acc += w01 * (R)__ldg(p + nx);
+        acc += w11 * (R)__ldg(p + nx + 1);
+        return acc;
+    }
+    R acc = R(0);
+    const R w[4] = {w00, w10, w01, w11};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ii = st.ix + (k & 1), jj = st.iy + (k >> 1);
+        if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+        acc += w[k] * (R)__ldg(F + jj * nx + ii);
+    }
+    return acc;
+}
+
+template <typename R>
+__device__ __forceinline__ void yee_gather(const FieldDev &f, const int ix[2], const int iy[2],
+                                           const R wx[2], const R wy[2], Vec3<R> &E, Vec3<R> &B)
+{
+    const int nx = (int)f.nx, ny = (int)f.ny;
+    YeeStencil<R> st[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int hx = k & 1, hy = k >> 1;
+        st[k].ix = ix[hx];
+        st[k].iy = iy[hy];
+        st[k].wx = wx[hx];
+        st[k].wy = wy[hy];
+        st[k].inside = ix[hx] >= 0 && iy[hy] >= 0 && ix[hx] + 1 < nx && iy[hy] + 1 < ny;
+        st[k].base = iy[hy] * nx + ix[hx];
+    }
+    E.x = yee_interp<R>(f.yee[0], st[1], nx, ny);
+    E.y = yee_interp<R>(f.yee[1], st[2], nx, ny);
+    E.z = yee_interp<R>(f.yee[2], st[0], nx, ny);
+    B.x = yee_interp<R>(f.yee[3], st[2], nx, ny);
+    B.y = yee_interp<R>(f.yee[4], st[1], nx, ny);
+    B.z = yee_interp<R>(f.yee[5], st[3], nx, ny);
+}
+
 // Fields at (x, y, z, t); R = double (FP64 path) or float (mixed path, with
 // phases reduced in FP64 before the FP32 trigonometry).
 template <int FK, typename R>
@@ -236,51 +322,18 @@ __device__ __forceinline__ void eval_field(const FieldDev &f, double x, double y
         // with one FP64 FMA, the rest in FP32).
         int ix[2], iy[2];
         R wx[2], wy[2];
-        if constexpr (sizeof(R) == 8) {
-            const double gx = (x - f.x0) / f.dx, gy = (y - f.y0) / f.dy;
+        const double gx = (x - f.x0) / f.dx, gy = (y - f.y0) / f.dy;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const double ax = h ? gx - 0.5 : gx, ay = h ? gy - 0.5 : gy;
-                const double fx = floor(ax), fy = floor(ay);
-                wx[h] = ax - fx;
-                wy[h] = ay - fy;
-                // clamp before the conversion (NaN and huge values included)
-                ix[h] = (int)fmax(-2.0, fmin((double)f.nx + 1.0, fx));
-                iy[h] = (int)fmax(-2.0, fmin((double)f.ny + 1.0, fy));
-            }
-        } else {
-            const float gx = (float)fma(x, f.inv_dx, -f.x0s), gy = (float)fma(y, f.inv_dy, -f.y0s);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float ax = h ? gx - 0.5f : gx, ay = h ? gy - 0.5f : gy;
-                const float fx = floorf(ax), fy = floorf(ay);
-                wx[h] = ax - fx;
-                wy[h] = ay - fy;
-                ix[h] = (int)fmaxf(-2.0f, fminf((float)f.nx + 1.0f, fx));
-                iy[h] = (int)fmaxf(-2.0f, fminf((float)f.ny + 1.0f, fy));
-            }
+        for (int h = 0; h < 2; ++h) {
+            const double ax = h ? gx - 0.5 : gx, ay = h ? gy - 0.5 : gy;
+            const double fx = floor(ax), fy = floor(ay);
+            wx[h] = (R)(ax - fx);
+            wy[h] = (R)(ay - fy);
+            // clamp before the conversion (NaN and huge values included)
+            ix[h] = (int)fmax(-2.0, fmin((double)f.nx + 1.0, fx));
+            iy[h] = (int)fmax(-2.0, fmin((double)f.ny + 1.0, fy));
         }
-        const int nx = (int)f.nx, ny = (int)f.ny;
-        R out[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const int hx = (c == 0 || c == 4 || c == 5), hy = (c == 1 || c == 3 || c == 5);
-            const float *F = f.yee[c];
-            R acc = R(0);
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const int ii = ix[hx] + a, jj = iy[hy] + b;
-                    if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
-                    const R wgt = (a ? wx[hx] : R(1) - wx[hx]) * (b ? wy[hy] : R(1) - wy[hy]);
-                    acc += wgt * (R)__ldg(F + (int64_t)jj * nx + ii);
-                }
-            }
-            out[c] = acc;
-        }
-        E = {out[0], out[1], out[2]};
-        B = {out[3], out[4], out[5]};
+        yee_gather<R>(f, ix, iy, wx, wy, E, B);
     }
 }
 
@@ -289,14 +342,14 @@ __device__ __forceinline__ void eval_field(const FieldDev &f, double x, double y
 // chi_e = sqrt(|gamma E + u x B|^2 - (u.E)^2) / a_S, in FP64
 __device__ __forceinline__ double chi_e64(double Ex, double Ey, double Ez, double Bx, double By,
                                           double Bz, double ux, double uy, double uz, double g,
-                                          double inv_aS)
+                                          double a_S)
 {
     const double ax = g * Ex + (uy * Bz - uz * By);
     const double ay = g * Ey + (uz * Bx - ux * Bz);
     const double az = g * Ez + (ux * By - uy * Bx);
     const double ue = ux * Ex + uy * Ey + uz * Ez;
     const double s = ax * ax + ay * ay + az * az - ue * ue;
-    return s > 0.0 ? sqrt(s) * inv_aS : 0.0;
+    return s > 0.0 ? sqrt(s) / a_S : 0.0;
 }
 
 // ------------------------------------------------------------------ rate tables
@@ -445,4 +498,10 @@ __device__ __forceinline__ R sample_cdf(const R *__restrict__ rows, R chi, R xi,
     return ra + f * (rb - ra);
 }
 
+// ------------------------------------------------------------------ FP32 inverse CDF with complement
+
+// Mixed path: the same inversion in FP32, returning x and 1 - x, both
+// accurate (1 - x from the logit, not by subtraction), so that the recoil
+// (|p| - u gamma) and the pair split (1 - v) keep their precision when the
+// photon or the electron takes nearly everything.
 }  // namespace qp

@@ -22,6 +22,7 @@
 
 #include "qp_device.cuh"
 #include "qp_kernels.h"
+#include "qp_mixed.cuh"
 
 namespace qp {
 
@@ -212,6 +213,7 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
     int n_emit = 0, n_sub = 0;
     double e_sub = 0.0;
 
+    if constexpr (PREC == kFP64) {
     if (active) {
         const double q = sp == 0 ? -1.0 : 1.0;
         const double dt = a.dt;
@@ -256,8 +258,7 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
         double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
         const double Ex = E.x, Ey = E.y, Ez = E.z, Bx = B.x, By = B.y, Bz = B.z;
         if (!loaded) wait_tables(bar, a);  // tables are needed from here on
-        const double inv_aS = 1.0 / a.a_S;
-        double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, inv_aS);
+        double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
         if (S.chi) S.chi[i] = chi;
         double dvx = 0.0, dvy = 0.0, dvz = 0.0;
 
@@ -328,11 +329,7 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
                 const uint4 rr = draw(a.seed, sp, kRngEmit, i, a.step, k);
                 const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
                 double ufrac;
-                if constexpr (PREC == kFP64)
-                    ufrac = sample_cdf<double>(a.tab.Cg, chi, xi_p, kSgMin, kSgSpan, true, clamped);
-                else
-                    ufrac = sample_cdf<float>(a.tab.Cgf, (float)chi, (float)xi_p, kSgMin, kSgSpan,
-                                              true, clamped);
+                ufrac = sample_cdf<double>(a.tab.Cg, chi, xi_p, kSgMin, kSgSpan, true, clamped);
                 const double pmag = sqrt(ux * ux + uy * uy + uz * uz);
                 double gg = ufrac * gam;
                 if (gg > pmag) gg = pmag;
@@ -359,7 +356,7 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
                 }
                 tau = -log(xi);
                 gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-                chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, inv_aS);
+                chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
             }
         }
 
@@ -380,6 +377,158 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
         S.tau[i] = tau;
         if (nph || n_sub) wgt = S.w[i];
     }
+    } else {
+    if (active) {
+        // ---- mixed precision: FP32 physics; the FP64 state is read once,
+        // increments are formed in FP32 and added back by integer
+        // instructions; chi_e falls back to double-float where FP32 cancels
+        const MixedConsts &m = a.mc;
+        const double xd = S.x[i], yd = S.y[i], zd = S.z ? S.z[i] : 0.0;
+        x0 = xd;
+        y0 = yd;
+        z0 = zd;
+        const double uxd = S.ux[i], uyd = S.uy[i], uzd = S.uz[i];
+        const double taud = S.tau[i];
+        Vec3<float> E, B;
+        eval_field_mixed<FK>(a.f, m, split_d(xd), split_d(yd), split_d(zd), E, B);
+
+        // Boris on the leading FP32 parts; the increment is kept in FP32
+        const float u0x = hi_d(uxd), u0y = hi_d(uyd), u0z = hi_d(uzd);
+        const float h = m.h[sp];
+        const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
+        const float mx = u0x + hx, my = u0y + hy, mz = u0z + hz;
+        const float ig = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+        const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
+        const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+        const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
+        const float px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+                    pz = mz + (mx * ty - my * tx);
+        float dux = (py * sz - pz * sy) + 2.0f * hx, duy = (pz * sx - px * sz) + 2.0f * hy,
+              duz = (px * sy - py * sx) + 2.0f * hz;
+        float ux = u0x + dux, uy = u0y + duy, uz = u0z + duz;
+        float gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        if (!loaded) wait_tables(bar, a);  // tables are needed from here on
+        float chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B, m.inv_aS,
+                                   m.inv_aS_lo);
+        if (S.chi) S.chi[i] = f_to_d(chi);
+        float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
+        float dtau_once = 0.0f;
+        bool events = false;
+        df2 TAU = {0.0f, 0.0f};
+
+        if (chi < m.chi_th) {
+            // ---- Sokolov (Eq. 4, 5); denominator 1 + tau0 v.f_l in double-float
+            cont = true;
+            const float q = sp == 0 ? -1.0f : 1.0f;
+            const float gi = 1.0f / gam;
+            const float vx = ux * gi, vy = uy * gi, vz = uz * gi;
+            const float fx = q * (E.x + (vy * B.z - vz * B.y));
+            const float fy = q * (E.y + (vz * B.x - vx * B.z));
+            const float fz = q * (E.z + (vx * B.y - vy * B.x));
+            const float vf = vx * fx + vy * fy + vz * fz;
+            const df2 den = two_sum(1.0f, m.tau0w * vf);
+            const float c = m.tau0w / den.hi * (1.0f - den.lo / den.hi);
+            dvx = c * (fx - vx * vf);
+            dvy = c * (fy - vy * vf);
+            dvz = c * (fz - vz * vf);
+            const float prad = m.C_rate * rate32<1>(sm.G, chi, clamped);
+            const float sx_ = m.dt * (q * (dvy * B.z - dvz * B.y) - prad * vx);
+            const float sy_ = m.dt * (q * (dvz * B.x - dvx * B.z) - prad * vy);
+            const float sz_ = m.dt * (q * (dvx * B.y - dvy * B.x) - prad * vz);
+            dux += sx_;
+            duy += sy_;
+            duz += sz_;
+            ux += sx_;
+            uy += sy_;
+            uz += sz_;
+            gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        } else {
+            // ---- optical depth (Eq. 6) with the residual-time sub-loop
+            TAU = split_d(taud);
+            float r = 1.0f;
+            for (int k = 0;; ++k) {
+                const float H = rate32<0>(sm.H, chi, clamped);
+                const float wdt = m.C_rate * H / gam * m.dt;
+                const float dtau = wdt * r;
+                // tau > dtau decided on the double-float optical depth
+                if (!(dtau > 0.0f) || TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f)) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    break;
+                }
+                if (k == a.max_emit) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    sat = true;
+                    break;
+                }
+                events = true;
+                r = r - df_to_f(TAU) / wdt;
+                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
+                const uint4 rr = draw(a.seed, sp, kRngEmit, i, a.step, k);
+                const float xi = u53f(rr.z, rr.w);
+                const FracPair uf = sample_cdf_f(
+                    a.tab.Cg2, a.tab.Qg2, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
+                    u53_pair_complement(rr.x, rr.y), (float)(kSgSpan / (kNNode - 1)), true,
+                    clamped);
+                const float pmag = sqrtf(ux * ux + uy * uy + uz * uz);
+                float gg = uf.x * gam;
+                // what the electron keeps, |p| - u gamma = (1-u) gamma - 1/(gamma + |p|),
+                // formed without cancellation
+                float keep = uf.omx * gam - 1.0f / (gam + pmag);
+                if (gg > pmag || keep < 0.0f) {
+                    gg = pmag;
+                    keep = 0.0f;
+                }
+                if (n_emit == 0 && pmag > 0.0f) {
+                    const float ip = 1.0f / pmag;
+                    kx = f_to_d(ux * ip);
+                    ky = f_to_d(uy * ip);
+                    kz = f_to_d(uz * ip);
+                }
+                ++n_emit;
+                if (gg > m.gmin) {
+                    const uint4 rp = draw(a.seed, sp, kRngPhotonTau, i, a.step, k);
+                    sm.gg[nph][tid] = f_to_d(gg);
+                    sm.tg[nph][tid] = f_to_d(-logf(u53f(rp.x, rp.y)));
+                    ++nph;
+                } else {
+                    ++n_sub;
+                    e_sub += f_to_d(gg);
+                }
+                if (pmag > 0.0f) {
+                    const float s1 = keep / pmag;
+                    const float s1m = s1 - 1.0f;  // exact (Sterbenz) for s1 in [1/2, 1]
+                    dux = fmaf(ux, s1m, dux);
+                    duy = fmaf(uy, s1m, duy);
+                    duz = fmaf(uz, s1m, duz);
+                    ux *= s1;
+                    uy *= s1;
+                    uz *= s1;
+                }
+                TAU = {-logf(xi), 0.0f};
+                gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B,
+                                     m.inv_aS, m.inv_aS_lo);
+            }
+        }
+
+        // ---- position and write-back: FP64 accumulation of FP32 increments
+        const float gi = 1.0f / gam;
+        S.x[i] = add_fd(xd, m.dt * (ux * gi + dvx));
+        S.y[i] = add_fd(yd, m.dt * (uy * gi + dvy));
+        if (S.z) S.z[i] = add_fd(zd, m.dt * (uz * gi + dvz));
+        S.ux[i] = add_fd(uxd, dux);
+        S.uy[i] = add_fd(uyd, duy);
+        S.uz[i] = add_fd(uzd, duz);
+        if (events)
+            S.tau[i] = merge_df(TAU);
+        else if (dtau_once != 0.0f)
+            S.tau[i] = add_fd(taud, -dtau_once);
+        if (nph || n_sub) wgt = S.w[i];
+    }
+    }
+    if (active && n_emit && S.nemit) S.nemit[i] += n_emit;
     if (!loaded) {
         // threads without a particle also wait, so the block never leaves
         // (or reuses the tables) with the copy in flight
@@ -426,6 +575,7 @@ __device__ void lepton_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
                 Ph.tau[slot] = sm.tg[j][tid];
                 Ph.w[slot] = wgt;
                 if (Ph.chi) Ph.chi[slot] = 0.0;
+                if (Ph.nemit) Ph.nemit[slot] = 0;
                 ++stored;
             } else {
                 ++dropped;
@@ -470,9 +620,10 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
     }
     const int64_t i = (int64_t)chain_tile * kTile + tid;
     int npair = 0;
-    double px = 0, py = 0, pz = 0, gux = 0, guy = 0, guz = 0, wg = 0, v = 0, tm = 0, tp = 0;
+    double px = 0, py = 0, pz = 0, gux = 0, guy = 0, guz = 0, wg = 0, v = 0, omv = 0, tm = 0, tp = 0;
     bool clamped = false;
 
+    if constexpr (PREC == kFP64) {
     if (i < n) {
         double tau = Ph.tau[i];
         if (tau >= 0.0) {
@@ -517,12 +668,9 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
                     // ---- pair creation at the photon position
                     const uint4 r1 = draw(a.seed, QP_PHOTON, kRngPair, i, a.step, 0);
                     const uint4 r2 = draw(a.seed, QP_PHOTON, kRngPairPos, i, a.step, 0);
-                    if constexpr (PREC == kFP64)
-                        v = sample_cdf<double>(a.tab.Cp, chi, u53(r1.x, r1.y), kSpMin, kSpSpan, false,
-                                               clamped);
-                    else
-                        v = sample_cdf<float>(a.tab.Cpf, (float)chi, (float)u53(r1.x, r1.y), kSpMin,
-                                              kSpSpan, false, clamped);
+                    v = sample_cdf<double>(a.tab.Cp, chi, u53(r1.x, r1.y), kSpMin, kSpSpan, false,
+                                           clamped);
+                    omv = 1.0 - v;
                     tm = -log(u53(r1.z, r1.w));
                     tp = -log(u53(r2.x, r2.y));
                     wg = Ph.w[i];
@@ -547,6 +695,67 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
             }
         }
     }
+    } else {
+    if (i < n) {
+        const double taud = Ph.tau[i];
+        if (taud >= 0.0) {
+            // ---- mixed precision: FP32 physics, FP64 accumulation by
+            // integer instructions
+            const MixedConsts &m = a.mc;
+            px = Ph.x[i];
+            py = Ph.y[i];
+            pz = Ph.z ? Ph.z[i] : 0.0;
+            gux = Ph.ux[i];
+            guy = Ph.uy[i];
+            guz = Ph.uz[i];
+            const float fx = hi_d(gux), fy = hi_d(guy), fz = hi_d(guz);
+            const float g = sqrtf(fx * fx + fy * fy + fz * fz);
+            bool decayed = false;
+            if (pairs && g > 2.0f) {
+                Vec3<float> E, B;
+                eval_field_mixed<FK>(a.f, m, split_d(px), split_d(py), split_d(pz), E, B);
+                const float ig = 1.0f / g;
+                const float kx = fx * ig, ky = fy * ig, kz = fz * ig;
+                const float ax = E.x + (ky * B.z - kz * B.y);
+                const float ay = E.y + (kz * B.x - kx * B.z);
+                const float az = E.z + (kx * B.y - ky * B.x);
+                const float ke = kx * E.x + ky * E.y + kz * E.z;
+                const float s2 = ax * ax + ay * ay + az * az - ke * ke;
+                const float chi = s2 > 0.0f ? over_aS(g * sqrtf(s2), m.inv_aS, m.inv_aS_lo) : 0.0f;
+                const float Tr = rate32<2>(sm.T, chi, clamped);
+                const float dtau = m.C_rate * Tr / g * m.dt;
+                if (Ph.chi) Ph.chi[i] = f_to_d(chi);
+                const df2 TAU = split_d(taud);
+                if (dtau > 0.0f && !(TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f))) {
+                    // ---- pair creation at the photon position
+                    const uint4 r1 = draw(a.seed, QP_PHOTON, kRngPair, i, a.step, 0);
+                    const uint4 r2 = draw(a.seed, QP_PHOTON, kRngPairPos, i, a.step, 0);
+                    const FracPair vf = sample_cdf_f(
+                        a.tab.Cp2, a.tab.Qp2, a.tab.Ep, chi, u53_pair(r1.x, r1.y),
+                        u53_pair_complement(r1.x, r1.y), (float)(kSpSpan / (kNNode - 1)), false,
+                        clamped);
+                    v = f_to_d(vf.x);
+                    omv = f_to_d(vf.omx);
+                    tm = f_to_d(-logf(u53f(r1.z, r1.w)));
+                    tp = f_to_d(-logf(u53f(r2.x, r2.y)));
+                    wg = Ph.w[i];
+                    npair = 1;
+                    decayed = true;
+                    Ph.tau[i] = -1.0;
+                } else if (dtau != 0.0f) {
+                    Ph.tau[i] = add_fd(taud, -dtau);
+                }
+            }
+            if (!decayed && g > 0.0f) {
+                const float c = m.dt / g;
+                Ph.x[i] = add_fd(px, c * fx);
+                Ph.y[i] = add_fd(py, c * fy);
+                if (Ph.z) Ph.z[i] = add_fd(pz, c * fz);
+            }
+        }
+    }
+    }
+    if (npair && Ph.nemit) Ph.nemit[i] += 1;
     warp_count(&bs.c[2][cClamp], clamped);
     warp_count(&bs.c[2][cPair], npair != 0);
     *tile_total_out = 0;
@@ -566,7 +775,7 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
         const int64_t ord = excl + local;
         if (leptons && ord < room) {
             const int64_t se = be + ord, spo = bp + ord;
-            const double om = 1.0 - v;
+            const double om = omv;
             El.x[se] = px;
             El.y[se] = py;
             if (El.z) El.z[se] = pz;
@@ -576,6 +785,7 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
             El.tau[se] = tm;
             El.w[se] = wg;
             if (El.chi) El.chi[se] = 0.0;
+            if (El.nemit) El.nemit[se] = 0;
             Po.x[spo] = px;
             Po.y[spo] = py;
             if (Po.z) Po.z[spo] = pz;
@@ -585,6 +795,7 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
             Po.tau[spo] = tp;
             Po.w[spo] = wg;
             if (Po.chi) Po.chi[spo] = 0.0;
+            if (Po.nemit) Po.nemit[spo] = 0;
         } else {
             atomicAdd(&bs.c[2][cPairDrop], 1ull);
             atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
@@ -596,8 +807,11 @@ __device__ void photon_tile(const StepArgs &a, Smem<R> &sm, unsigned long long *
 
 // -------------------------------------------------------------------- the step
 
+// FP64: 4 blocks of 128 per SM (128 registers, no spills); mixed: 8 blocks
+// (64 registers; the few spills cost less than the extra resident warps gain)
 template <int PREC, int FK>
-__global__ void __launch_bounds__(kTile) k_step(const __grid_constant__ StepArgs a)
+__global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
+    k_step(const __grid_constant__ StepArgs a)
 {
     using R = typename std::conditional<PREC == kFP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -738,19 +952,19 @@ __global__ void k_init_tau(double *tau, int64_t first, int64_t count, uint64_t s
 // blocks have a fixed shape, so the result is independent of timing.
 constexpr int kDiagScalars = 8;  // n_alive, weight, energy, px, py, pz, w chi, (spare)
 
-__global__ void __launch_bounds__(kTile) k_diag_partial(SpeciesDev S, int is_photon,
+__global__ void __launch_bounds__(kDiagTile) k_diag_partial(SpeciesDev S, int is_photon,
                                                        double *partials)
 {
-    __shared__ double s_red[kDiagScalars][kTile];
-    __shared__ int s_bin[kTile];
-    __shared__ double s_w[kTile];
+    __shared__ double s_red[kDiagScalars][kDiagTile];
+    __shared__ int s_bin[kDiagTile];
+    __shared__ double s_w[kDiagTile];
     const int tid = threadIdx.x;
     int64_t n = *S.n_live;
     n = n < 0 ? 0 : (n > S.cap ? S.cap : n);
     double acc[kDiagScalars] = {0, 0, 0, 0, 0, 0, 0, 0};
     double hist = 0.0;  // thread tid < QP_HIST_BINS owns bin tid
     const double bin_scale = QP_HIST_BINS / (QP_HIST_LOG10_MAX - QP_HIST_LOG10_MIN);
-    for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
+    for (int64_t base = (int64_t)blockIdx.x * kDiagTile; base < n; base += (int64_t)gridDim.x * kDiagTile) {
         const int64_t i = base + tid;
         int bin = -1;
         double wv = 0.0;
@@ -777,14 +991,14 @@ __global__ void __launch_bounds__(kTile) k_diag_partial(SpeciesDev S, int is_pho
         s_w[tid] = wv;
         __syncthreads();
         if (tid < QP_HIST_BINS)
-            for (int k = 0; k < kTile; ++k)
+            for (int k = 0; k < kDiagTile; ++k)
                 if (s_bin[k] == tid) hist += s_w[k];
         __syncthreads();
     }
 #pragma unroll
     for (int k = 0; k < kDiagScalars; ++k) s_red[k][tid] = acc[k];
     __syncthreads();
-    for (int h = kTile / 2; h > 0; h >>= 1) {
+    for (int h = kDiagTile / 2; h > 0; h >>= 1) {
         if (tid < h)
 #pragma unroll
             for (int k = 0; k < kDiagScalars; ++k) s_red[k][tid] += s_red[k][tid + h];
@@ -856,16 +1070,16 @@ cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, uint64_t 
                             cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    int64_t blocks = (count + kTile - 1) / kTile;
+    int64_t blocks = (count + kDiagTile - 1) / kDiagTile;
     if (blocks > 4096) blocks = 4096;
-    k_init_tau<<<(int)blocks, kTile, 0, st>>>(tau, first, count, seed, species);
+    k_init_tau<<<(int)blocks, kDiagTile, 0, st>>>(tau, first, count, seed, species);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, int nblocks,
                         double *out, cudaStream_t st)
 {
-    k_diag_partial<<<nblocks, kTile, 0, st>>>(S, is_photon, partials);
+    k_diag_partial<<<nblocks, kDiagTile, 0, st>>>(S, is_photon, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_diag_final<<<1, 128, 0, st>>>(partials, nblocks, out);

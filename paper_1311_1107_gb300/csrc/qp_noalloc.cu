@@ -60,12 +60,13 @@ extern "C" int qp_diagnostics_noalloc(const qp_species_desc *d, qp_diag *out, vo
     S.tau = d->tau;
     S.w = d->w;
     S.chi = d->chi;
+    S.nemit = d->nemit;
     S.n_live = d->n_live;
     S.cap = d->capacity;
     S.present = 1;
     // one block per tile: every partial row read by the final pass is
     // written by this call (tiles past the live count write zeros)
-    int tiles = (int)((d->capacity + qp::kTile - 1) / qp::kTile);
+    int tiles = (int)((d->capacity + qp::kDiagTile - 1) / qp::kDiagTile);
     if (tiles < 1) tiles = 1;
     double *partials = scratch;
     double *fin = scratch + (size_t)QP_NOALLOC_MAX_TILES * qp::kDiagWords;

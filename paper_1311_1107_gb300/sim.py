@@ -39,12 +39,14 @@ class DeviceSpecies:
         self.t = {nm: torch.zeros(n, dtype=torch.float64, device=device)
                   for nm in NAMES if not (nm == "z" and dims == 2)}
         self.chi = torch.zeros(n, dtype=torch.float64, device=device) if track_chi else None
+        self.nemit = torch.zeros(n, dtype=torch.int32, device=device) if track_chi else None
         self.n_live = torch.zeros(1, dtype=torch.int64, device=device)
         d = Q.qp_species_desc()
         d.kind, d.dims, d.capacity = kind, dims, self.cap
         for nm in NAMES:
             setattr(d, nm, _ptr(self.t.get(nm)))
         d.chi = _ptr(self.chi)
+        d.nemit = _ptr(self.nemit)
         d.n_live = _ptr(self.n_live)
         self._desc = d
         self.handle = Q.qp_create_species(ctx, d)
@@ -54,6 +56,8 @@ class DeviceSpecies:
         n = len(arrays["x"]) if n is None else n
         if n > self.cap:
             raise ValueError(f"{n} particles exceed capacity {self.cap}")
+        if self.nemit is not None:
+            self.nemit.zero_()
         for nm, t in self.t.items():
             if nm in arrays and n:
                 t[:n].copy_(torch.as_tensor(np.asarray(arrays[nm][:n], dtype=np.float64)))
@@ -67,6 +71,8 @@ class DeviceSpecies:
         out = {nm: t[:n].cpu().numpy() for nm, t in self.t.items()}
         if self.chi is not None:
             out["chi"] = self.chi[:n].cpu().numpy()
+        if self.nemit is not None:
+            out["nemit"] = self.nemit[:n].cpu().numpy()
         return out
 
 

