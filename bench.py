@@ -5,17 +5,23 @@ Default workload: the 2D laser-on-foil case (2048x512 Yee grid, 131072 e-,
 fixed Gaussian-pulse fields, Sokolov below chi 1e-3, Monte-Carlo above,
 photons and pairs tracked), run on the mixed-precision path (the headline
 `value`) and on the FP64 path (`fp64`) on the same GPU.  A step is one
-qp_step (step-begin, lepton and photon kernels) over every live particle;
+qp_step (one launch of the fused step kernel) over every live particle;
 K steps are timed from the initial state (K = 500 is the whole job).
+The line also carries `serving`: a stream of beam-collision requests served
+with continuous batching (Poisson arrivals at ~70 % of the measured batched
+throughput), its throughput and p50/p99 request latency; `--workload
+serving` runs the full 256-request stream on its own.
 L2 is flushed (256 MB write) between timed steps; each step is timed with
 CUDA events on its stream; clocks are sampled with nvidia-smi meanwhile.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload foil|collision|plane]
+                  [--workload foil|collision|plane|serving] [--requests R]
 
-Under torchrun each rank runs an independent replica (seed = rank) on its
-own GPU: weak scaling with no collective in the data path; the barrier and
-the max over ranks of the timed region come from torch.distributed.
+Under torchrun each rank steps its own shard of a population of N copies of
+the workload (particle ids offset by rank x n, so every particle has its own
+random streams) on its own GPU: weak scaling with no collective in the data
+path; the barrier and the max over ranks of the timed region come from
+torch.distributed.
 """
 from __future__ import annotations
 
@@ -47,7 +53,15 @@ def parse():
     p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--workload", choices=("foil", "collision", "plane"), default="foil")
+    p.add_argument("--workload", choices=("foil", "collision", "plane", "serving"),
+                   default="foil")
+    p.add_argument("--requests", type=int, default=None,
+                   help="serving: requests in the stream (default 256 for --workload serving, "
+                        "32 inside the default line)")
+    p.add_argument("--serving-nmax", type=float, default=None,
+                   help="serving: largest electron count of a request (default 1e6; 1e5 "
+                        "inside the default line)")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=100)
@@ -60,6 +74,8 @@ def workload(name: str, seed: int):
         return W.laser_on_foil(seed=seed)
     if name == "collision":
         return W.beam_collision(seed=seed)
+    if name == "serving":
+        return W.serving_request_workload(W.serving_requests(n_requests=1, seed=seed)[0])
     return W.plane_wave_collision(seed=seed)
 
 
@@ -139,7 +155,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU path
 
-def run_path(w, precision, steps, warmup, dev, dist, flush):
+def run_path(w, precision, steps, warmup, dev, dist, flush, id_base=0):
     import torch
 
     from paper_1311_1107_gb300 import qedpic as Q
@@ -147,7 +163,8 @@ def run_path(w, precision, steps, warmup, dev, dist, flush):
     from paper_1311_1107_gb300.workloads import LAMBDA_M
 
     ctx = Q.qp_init_tables(LAMBDA_M, dev)
-    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False)
+    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False,
+                     id_base=id_base)
     stream = torch.cuda.current_stream()
     # warm-up steps on the initial state, then back to the initial state
     for _ in range(warmup):
@@ -271,6 +288,70 @@ def e2e(w, precision, steps, dev):
             "steps": steps, "precision": precision}
 
 
+# ----------------------------------------------------------------------------- serving
+
+def serving(dev, n_requests: int, n_max: float, load: float = 0.7):
+    """Serve a stream of beam-collision requests (electron counts log-uniform
+    in [1e3, n_max], gamma U[1000, 5000], a0 U[50, 500], steps U[200, 2000],
+    seeds = ids) with Poisson arrivals.  The arrival rate is set so that the
+    offered load is `load` of the batched throughput measured on the first
+    8 requests served together (calibration, not timed).  Request payloads
+    (initial electrons) are generated before the clock starts, as a client
+    would send them."""
+    import torch
+
+    from paper_1311_1107_gb300 import qedpic as Q
+    from paper_1311_1107_gb300 import workloads as W
+    from paper_1311_1107_gb300.serve import ServingEngine
+
+    reqs = W.serving_requests(n_requests=n_requests, arrival_rate=1.0, seed=0, n_max=n_max)
+    payloads = {r["id"]: W.serving_request_workload(r, 8) for r in reqs}
+    eng = ServingEngine(max_slots=Q.QP_MAX_BATCH, arena_bytes=96 << 30, graph_steps=8,
+                        device=dev)
+    try:
+        cal_reqs = [dict(r, arrival_s=0.0) for r in reqs[:8]]
+        cal = eng.run(cal_reqs, payloads)
+        per_es = cal["particle_steps"] / sum(r["n"] * r["n_steps"] for r in cal_reqs)
+        mean_work = per_es * float(np.mean([r["n"] * r["n_steps"] for r in reqs]))
+        lam = load * cal["throughput"] / mean_work
+        eng.max_concurrent = 0
+        out = eng.run(reqs, payloads, time_scale=1.0 / lam)
+    finally:
+        eng.close()
+    torch.cuda.synchronize(dev)
+    lat = np.array([r["latency_s"] for r in out["results"]])
+    return {
+        "requests": n_requests, "completed": len(out["results"]),
+        "throughput": round(out["throughput"], 1), "unit": UNIT,
+        "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+        "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+        "arrival_rate_per_s": round(lam, 3), "offered_load": load,
+        "calibration_throughput": round(cal["throughput"], 1),
+        "makespan_s": round(out["makespan_s"], 2), "max_concurrent": out["max_concurrent"],
+        "particle_steps": int(out["particle_steps"]), "graph_steps": 8, "precision": "mixed",
+        "config": (f"{n_requests} requests: n_e log-uniform [1e3, {n_max:.0e}], gamma U[1000, 5000], "
+                   "a0 U[50, 500], steps U[200, 2000], seeds 0.., Poisson arrivals; photon and "
+                   "pair buffers 8 n_e; mixed path, CUDA graphs of 8 shared launches"),
+    }
+
+
+def serving_arm(args):
+    import torch
+    torch.cuda.set_device(0)
+    n_req = args.requests or 256
+    n_max = args.serving_nmax or 1e6
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = serving(0, n_req, n_max)
+    clk = clocks.stop()
+    line = {"metric": "serving: request latency and throughput (continuous batching)",
+            "value": res["throughput"], "unit": UNIT, "n_gpus": 1, "steps": None,
+            "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed path)", "data": "synthetic",
+            "config": {"workload": res["config"]}, "serving": res, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(w, n_sample: int, n_steps: int):
@@ -355,10 +436,16 @@ def reference_arm(args):
 def ours_arm(args):
     import torch
 
+    from paper_1311_1107_gb300.shard import aggregate
+
     world, rank, local, dist = dist_setup(args)
     dev = local
     torch.cuda.set_device(dev)
-    w = workload(args.workload, rank)
+    # every rank steps its own shard of one population of `world` copies of
+    # the workload: the same initial state, particle ids offset by the rank
+    # (independent random streams), no exchange between ranks
+    w = workload(args.workload, 0)
+    id_base = rank * len(w["electrons"]["x"])
     dims = w["dims"]
     pairs = bool(w["params"].get("pairs", False))
     hbm_peak, peak_kind = peaks()
@@ -366,24 +453,21 @@ def ours_arm(args):
 
     clocks = ClockSampler(dev)
     clocks.start()
-    mixed = run_path(w, "mixed", args.steps, args.warmup, dev, dist, flush)
-    fp64 = run_path(w, "fp64", args.steps, args.warmup, dev, dist, flush)
+    mixed = run_path(w, "mixed", args.steps, args.warmup, dev, dist, flush, id_base)
+    fp64 = run_path(w, "fp64", args.steps, args.warmup, dev, dist, flush, id_base)
     clk = clocks.stop()
 
     def agg(res):
-        t_ms = sum(res["step_ms"])
-        slots = res["lep_slots"] + res["pho_slots"]
-        if dist:
-            tt = torch.tensor([t_ms], dtype=torch.float64, device=f"cuda:{dev}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ss = torch.tensor([slots], dtype=torch.float64, device=f"cuda:{dev}")
-            dist.all_reduce(ss, op=dist.ReduceOp.SUM)
-            t_ms, slots = float(tt.item()), float(ss.item())
+        t_ms, slots = aggregate(sum(res["step_ms"]), res["lep_slots"] + res["pho_slots"], dist,
+                                f"cuda:{dev}")
         return slots / (t_ms * 1e-3), t_ms
 
     v_mixed, t_mixed = agg(mixed)
     v_fp64, t_fp64 = agg(fp64)
     line = None
+    serv = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serv = serving(dev, args.requests or 32, args.serving_nmax or 1e5)
     if rank == 0:
         e2e_res = None
         if not args.no_e2e:
@@ -402,14 +486,14 @@ def ours_arm(args):
                        "l2": "flushed between timed steps (256 MB write)",
                        "particle_steps": "live slots of e-, e+ and photons at each step start",
                        "steps_timed": "steps 0..K-1 of the job from the initial state",
-                       "final_live": mixed["final_live"], "parallelism": f"replicas x{world}"},
+                       "final_live": mixed["final_live"], "parallelism": f"shards x{world} (ids offset by rank, no exchange)"},
             "fp64": {"value": round(v_fp64, 1), "unit": UNIT,
                      "ms_per_step": round(t_fp64 / args.steps, 4), "dtype": "f64",
                      "roofline": roofline(fp64, dims, pairs, hbm_peak, peak_kind),
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
                      "final_live": fp64["final_live"]},
             "roofline": roofline(mixed, dims, pairs, hbm_peak, peak_kind),
-            "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
+            "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
             "clocks": clk, "status": {"mixed": mixed["status"], "fp64": fp64["status"]},
         }
         print(json.dumps(line), flush=True)
@@ -422,6 +506,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "serving":
+        serving_arm(args)
     else:
         ours_arm(args)
 

@@ -70,6 +70,7 @@ enum {
     QP_FIELD_UNIFORM_B = 4  /* B = b0 z^ (the paper's section 4 test)            */
 };
 #define QP_MAX_EMISSIONS 8  /* upper bound of qp_step_params.max_emissions     */
+#define QP_MAX_BATCH 64     /* problems (independent runs) per batch            */
 #define QP_HIST_BINS 64     /* diagnostic spectrum bins in log10(gamma)        */
 #define QP_HIST_LOG10_MIN (-1.0)
 #define QP_HIST_LOG10_MAX (5.0)
@@ -120,6 +121,10 @@ typedef struct {
                            set to 0 for particles the library appends          */
     int64_t *n_live;    /* device counter of live slots; the library updates it
                            when it appends; the caller sets its initial value    */
+    int64_t id_base;    /* particle id of slot 0 (>= 0): slot i is particle
+                           id_base + i, the counter of its random streams.  A
+                           population split over GPUs keeps every particle's
+                           draws when each part gets the id of its first slot */
 } qp_species_desc;
 
 /*
@@ -191,14 +196,84 @@ typedef struct {
  * Appended particles fill slots [n_live, ...) in the order of their parent's
  * slot (then emission index); photons emitted by electrons precede those of
  * positrons.  Particles that do not fit are counted as dropped and their
- * energy recorded; the step still completes.  No allocation, no host
- * synchronisation, no host reads: the call can be captured in a CUDA graph.
+ * energy recorded; the step still completes.  The first step with species
+ * larger than any stepped before grows the context's look-back scratch (one
+ * allocation, synchronous); otherwise no allocation, no host synchronisation,
+ * no host reads: the call can then be captured in a CUDA graph.
  * Returns QP_ERR_INVALID_ARG (nothing enqueued) for bad parameters, a
  * missing photon species while species emit, or a YEE2D grid with a NULL
  * component; QP_ERR_CUDA if a launch fails.  Overflow, table clamping and
  * wait time-outs are reported by the next qp_diagnostics.
  */
 int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream);
+
+/* ---- batches: several independent runs in shared launches --------------
+ *
+ * A batch is a device table of up to max_problems independent problems
+ * (runs), each with its own species, field parameters, seed, first step and
+ * number of steps, all of one precision and field kind.  One launch takes one
+ * step of every active problem (the same arithmetic as qp_step, tile by tile,
+ * so a problem's results do not depend on what else is in the batch); each
+ * problem's step counter lives on the device and advances with every launch,
+ * and a problem becomes idle by itself when its steps are done.  The table
+ * is read by the kernel at every launch, so problems can be set and cleared
+ * between launches without touching a captured CUDA graph of qp_batch_step.
+ * This is the batching layer of a serving loop (requests = problems).
+ */
+typedef struct qp_batch qp_batch;
+
+/* Allocate a batch (device table, counters, pinned staging) for problems of
+ * one precision (QP_FP64 / QP_MIXED) and field kind.  Synchronous.
+ * QP_ERR_INVALID_ARG unless 1 <= max_problems <= QP_MAX_BATCH. */
+int qp_batch_create(qp_ctx *ctx, int32_t max_problems, int32_t precision, int32_t field_kind,
+                    qp_batch **out);
+
+/* Release the batch (waits for the device first).  The context must outlive
+ * its batches. */
+int qp_batch_destroy(qp_batch *b);
+
+/* Look-back scratch a problem needs: 64-bit words, from the capacities of
+ * the species named in s (one word per 128 slots of each chain, plus a few). */
+int qp_batch_scratch_words(qp_ctx *ctx, const qp_step_params *s, int64_t *words);
+
+/*
+ * Put a problem in slot `slot`: species handles, field, dt, seed, chi
+ * threshold, photon cut, pairs and max emissions as for qp_step; s->step is
+ * its first step index and s->n_steps the launches it takes part in.
+ * `scratch` is caller-owned device memory of at least qp_batch_scratch_words
+ * words, used by this problem alone until it is done or cleared.  Enqueued on
+ * `stream` (the stream of the batch's launches): clears the scratch and the
+ * species' counters, copies the descriptor, and activates the slot last, so
+ * the problem is stepped from the next launch on.  The host side returns
+ * without waiting for the device (staging buffers are reused only after
+ * their copy completed).  QP_ERR_INVALID_ARG for a bad slot, a precision or
+ * field kind other than the batch's, too little scratch, or what qp_step
+ * rejects.  The species' initial state (positions, momenta, optical depths,
+ * live counts) must be in place, in stream order, before the next launch.
+ */
+int qp_batch_set(qp_batch *b, int32_t slot, const qp_step_params *s, uint64_t *scratch,
+                 int64_t scratch_words, void *stream);
+
+/* Deactivate a slot (stream-ordered): it takes no part in later launches. */
+int qp_batch_clear(qp_batch *b, int32_t slot, void *stream);
+
+/* Enqueue n_launches launches; each takes one step of every active problem
+ * and advances its step counter.  No allocation, no host synchronisation:
+ * capturable in a CUDA graph, and a captured graph stays valid while the
+ * batch's problems change. */
+int qp_batch_step(qp_batch *b, int32_t n_launches, void *stream);
+
+/* Enqueue copies of every slot's remaining launches (0 = idle or done) and,
+ * where the pointers are not NULL, of its next step index and of the live
+ * slots (all three species) stepped since it was set, into caller-owned host
+ * arrays of max_problems entries (pinned memory for an asynchronous copy);
+ * valid once the stream has reached this point. */
+int qp_batch_progress(qp_batch *b, int64_t *steps_left, int64_t *next_step, int64_t *work,
+                      void *stream);
+
+/* Free a species handle (host-side registry only; the caller still owns
+ * the buffers).  A later qp_create_species may reuse the handle. */
+int qp_destroy_species(qp_ctx *ctx, int32_t handle);
 
 /* ---- qp_diagnostics ---------------------------------------------------- */
 typedef struct {

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqedpic.so")
 
-SOURCES = ["qp_kernels.cu", "qp_abi.cu", "qp_noalloc.cu", "qp_tables.cpp"]
+SOURCES = ["qp_step_fp64.cu", "qp_step_mixed.cu", "qp_kernels.cu", "qp_abi.cu", "qp_noalloc.cu",
+           "qp_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

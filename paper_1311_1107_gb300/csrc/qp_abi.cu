@@ -20,6 +20,7 @@ constexpr unsigned kSpinLimit = 1u << 24;
 
 struct SpeciesRec {
     qp_species_desc d;
+    bool live = false;
 };
 
 // FP64 tables are built once per process and shared by every context.
@@ -49,13 +50,14 @@ struct qp_ctx {
     double *d_tab64 = nullptr;
     float *d_tab32 = nullptr;
     qp::DevStats *d_stats = nullptr;  // [kMaxSpecies]
-    qp::StepCtl *d_ctl = nullptr;     // ticket, done, epoch, pending counts
+    qp::StepCtl *d_ctl = nullptr;     // ticket, done, epoch of qp_step launches
+    long long *d_pending = nullptr;   // [3] new live counts of a qp_step launch
     int *d_status = nullptr;
     unsigned long long *d_chain = nullptr;  // lepton chain then photon chain
     size_t chain_words = 0;           // words per chain
     double *d_diag = nullptr;         // partials + final
     std::vector<SpeciesRec> species;
-    int grid_cache[2][5];             // [precision][field] blocks per SM, 0 = unknown
+    int grid_cache[2][2][5];          // [batch][precision][field] blocks per SM, 0 = unknown
     // kernel timing (qp_profile_*): event pool and (kernel, start event) records
     bool profiling = false;
     std::vector<cudaEvent_t> events;
@@ -91,6 +93,7 @@ void release(qp_ctx *c)
     cudaFree(c->d_tab32);
     cudaFree(c->d_stats);
     cudaFree(c->d_ctl);
+    cudaFree(c->d_pending);
     cudaFree(c->d_status);
     cudaFree(c->d_chain);
     cudaFree(c->d_diag);
@@ -115,7 +118,7 @@ struct DeviceGuard {
 
 bool valid_handle(const qp_ctx *c, int32_t h)
 {
-    return c && h >= 0 && (size_t)h < c->species.size();
+    return c && h >= 0 && (size_t)h < c->species.size() && c->species[h].live;
 }
 
 // Make the look-back scratch large enough for `words` tiles per chain.
@@ -183,6 +186,7 @@ qp::SpeciesDev species_dev(const qp_ctx *c, int32_t h)
     s.nemit = d.nemit;
     s.n_live = d.n_live;
     s.cap = d.capacity;
+    s.id_base = d.id_base;
     s.present = 1;
     s.slot_stats = h;
     return s;
@@ -275,6 +279,8 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
     QP_TRY(cudaMemset(c->d_stats, 0, kMaxSpecies * sizeof(qp::DevStats)));
     QP_TRY(cudaMalloc(&c->d_ctl, sizeof(qp::StepCtl)));
     QP_TRY(cudaMemset(c->d_ctl, 0, sizeof(qp::StepCtl)));
+    QP_TRY(cudaMalloc(&c->d_pending, 4 * sizeof(long long)));
+    QP_TRY(cudaMemset(c->d_pending, 0, 4 * sizeof(long long)));
     QP_TRY(cudaMalloc(&c->d_status, sizeof(int)));
     QP_TRY(cudaMemset(c->d_status, 0, sizeof(int)));
     QP_TRY(cudaMalloc(&c->d_diag, (qp::kDiagBlocks + 1) * qp::kDiagWords * sizeof(double)));
@@ -300,24 +306,32 @@ int qp_create_species(qp_ctx *ctx, const qp_species_desc *d, int32_t *out_handle
     if (!d || !out_handle) return QP_ERR_INVALID_ARG;
     if (d->kind < QP_ELECTRON || d->kind > QP_PHOTON) return QP_ERR_INVALID_ARG;
     if (d->dims != 2 && d->dims != 3) return QP_ERR_INVALID_ARG;
-    if (d->capacity < 0 || !d->n_live) return QP_ERR_INVALID_ARG;
+    if (d->capacity < 0 || !d->n_live || d->id_base < 0) return QP_ERR_INVALID_ARG;
     if (d->dims == 2 && d->z) return QP_ERR_INVALID_ARG;
     if (d->capacity > 0 && (!d->x || !d->y || !d->ux || !d->uy || !d->uz || !d->tau || !d->w ||
                             (d->dims == 3 && !d->z)))
         return QP_ERR_INVALID_ARG;
-    if (ctx->species.size() >= (size_t)kMaxSpecies) return QP_ERR_INVALID_ARG;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return QP_ERR_CUDA;
-    // scratch for the worst case of this species being in both chains with
-    // every other registered species
-    size_t words = tiles_of(d->capacity) + 4;
-    for (const SpeciesRec &r : ctx->species) words += tiles_of(r.d.capacity) + 4;
-    int st = ensure_chain(ctx, words);
-    if (st != QP_OK) return st;
+    // a free record (of a destroyed species) is reused; its counter block is
+    // cleared by qp_reset_counters or qp_batch_set
+    size_t h = 0;
+    while (h < ctx->species.size() && ctx->species[h].live) ++h;
+    if (h >= (size_t)kMaxSpecies) return QP_ERR_INVALID_ARG;
     SpeciesRec r;
     r.d = *d;
-    ctx->species.push_back(r);
-    *out_handle = (int32_t)(ctx->species.size() - 1);
+    r.live = true;
+    if (h == ctx->species.size())
+        ctx->species.push_back(r);
+    else
+        ctx->species[h] = r;
+    *out_handle = (int32_t)h;
+    return QP_OK;
+}
+
+int qp_destroy_species(qp_ctx *ctx, int32_t handle)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    ctx->species[handle].live = false;
     return QP_OK;
 }
 
@@ -330,15 +344,19 @@ int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t fi
     if (first < 0 || count < 0 || first + count > d.capacity) return QP_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return QP_ERR_CUDA;
-    return cuda_status(
-        qp::launch_init_tau(d.tau, first, count, seed, d.kind, (cudaStream_t)stream));
+    return cuda_status(qp::launch_init_tau(d.tau, first, count, d.id_base, seed, d.kind,
+                                           (cudaStream_t)stream));
 }
 
-int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
+namespace {
+
+// Checks of a step description (everything but the species' precision and
+// field kind, which the caller compares) and the problem it defines: species,
+// field, constants; scratch, control words and time are set by the caller.
+int build_problem(const qp_ctx *ctx, const qp_step_params *s, qp::Problem &P)
 {
-    if (!ctx) return QP_ERR_NOT_INITIALIZED;
-    if (!s) return QP_ERR_INVALID_ARG;
-    if (!(s->dt > 0.0) || !isfinite(s->dt) || s->n_steps < 0 || s->step < 0) return QP_ERR_INVALID_ARG;
+    if (!(s->dt > 0.0) || !isfinite(s->dt) || s->n_steps < 0 || s->step < 0)
+        return QP_ERR_INVALID_ARG;
     if (s->precision != QP_FP64 && s->precision != QP_MIXED) return QP_ERR_INVALID_ARG;
     if (s->max_emissions < 1 || s->max_emissions > QP_MAX_EMISSIONS) return QP_ERR_INVALID_ARG;
     if (!(s->chi_threshold >= 0.0) || !(s->photon_min_gamma >= 0.0)) return QP_ERR_INVALID_ARG;
@@ -361,90 +379,52 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
         if (!valid_handle(ctx, hs[k])) return QP_ERR_NOT_INITIALIZED;
         if (ctx->species[hs[k]].d.kind != kinds[k]) return QP_ERR_INVALID_ARG;
     }
-    if (s->n_steps == 0) return QP_OK;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return QP_ERR_CUDA;
 
-    qp::StepArgs a{};
+    P = qp::Problem{};
     for (int k = 0; k < 3; ++k)
-        if (hs[k] != -1) a.sp[k] = species_dev(ctx, hs[k]);
-    a.f.kind = f.kind;
-    a.f.a0 = f.a0;
-    a.f.w0 = f.w0;
-    a.f.tau_fwhm = f.tau_fwhm;
-    a.f.x_focus = f.x_focus;
-    a.f.t_focus = f.t_focus;
-    a.f.b0 = f.b0;
-    for (int k = 0; k < 6; ++k) a.f.yee[k] = f.yee[k];
-    a.f.nx = f.nx;
-    a.f.ny = f.ny;
-    a.f.dx = f.dx;
-    a.f.dy = f.dy;
-    a.f.x0 = f.x0;
-    a.f.y0 = f.y0;
+        if (hs[k] != -1) P.sp[k] = species_dev(ctx, hs[k]);
+    P.f.kind = f.kind;
+    P.f.a0 = f.a0;
+    P.f.w0 = f.w0;
+    P.f.tau_fwhm = f.tau_fwhm;
+    P.f.x_focus = f.x_focus;
+    P.f.t_focus = f.t_focus;
+    P.f.b0 = f.b0;
+    for (int k = 0; k < 6; ++k) P.f.yee[k] = f.yee[k];
+    P.f.nx = f.nx;
+    P.f.ny = f.ny;
+    P.f.dx = f.dx;
+    P.f.dy = f.dy;
+    P.f.x0 = f.x0;
+    P.f.y0 = f.y0;
     if (f.kind == QP_FIELD_YEE2D) {
-        a.f.inv_dx = 1.0 / f.dx;
-        a.f.inv_dy = 1.0 / f.dy;
-        a.f.x0s = f.x0 / f.dx;
-        a.f.y0s = f.y0 / f.dy;
+        P.f.inv_dx = 1.0 / f.dx;
+        P.f.inv_dy = 1.0 / f.dy;
+        P.f.x0s = f.x0 / f.dx;
+        P.f.y0s = f.y0 / f.dy;
     }
-    const size_t R = qp::kNRatePad, CC = (size_t)qp::kNCdf * qp::kNNode;
-    a.tab.H = ctx->d_tab64;
-    a.tab.Gs = ctx->d_tab64 + R;
-    a.tab.Ts = ctx->d_tab64 + 2 * R;
-    a.tab.Cg = ctx->d_tab64 + 3 * R;
-    a.tab.Cp = ctx->d_tab64 + 3 * R + CC;
-    a.tab.Hf = ctx->d_tab32;
-    a.tab.Gsf = ctx->d_tab32 + R;
-    a.tab.Tsf = ctx->d_tab32 + 2 * R;
-    const float2 *c2 = reinterpret_cast<const float2 *>(ctx->d_tab32 + kTabRate);
-    a.tab.Cg2 = c2;
-    a.tab.Cp2 = c2 + CC;
-    a.tab.Qg2 = c2 + 2 * CC;
-    a.tab.Qp2 = c2 + 3 * CC;
-    a.tab.Eg = ctx->d_tab32 + kTabRate + 4 * kTabCdf;
-    a.tab.Ep = a.tab.Eg + qp::kNNode;
-    a.lep_words = ctx->d_chain;
-    a.pho_words = ctx->d_chain + ctx->chain_words;
-    a.ctl = ctx->d_ctl;
-    a.stats = ctx->d_stats;
-    a.status = ctx->d_status;
-    a.dt = s->dt;
-    a.seed = s->seed;
-    a.chi_th = s->chi_threshold;
-    a.gmin = s->photon_min_gamma;
-    a.a_S = ctx->U.a_S;
-    a.C_rate = ctx->U.C_rate;
-    a.tau0w = ctx->U.tau0w;
-    a.pairs = s->pairs ? 1 : 0;
-    a.max_emit = s->max_emissions;
-    a.spin_limit = kSpinLimit;
-
-    // persistent grid: resident blocks, never more than the tiles the
-    // registered capacities allow
-    const int prec = s->precision == QP_MIXED ? 1 : 0;
-    int &bpsm = ctx->grid_cache[prec][f.kind];
-    if (!bpsm) bpsm = qp::step_blocks_per_sm(s->precision, f.kind);
-    int64_t cap_tiles = 0;
-    for (int k = 0; k < 3; ++k)
-        if (hs[k] != -1) cap_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
-    const int64_t resident = (int64_t)bpsm * ctx->num_sms;
-    const int grid = (int)(cap_tiles < resident ? (cap_tiles > 0 ? cap_tiles : 1) : resident);
+    P.dt = s->dt;
+    P.step = (uint64_t)s->step;
+    P.seed = s->seed;
+    P.chi_th = s->chi_threshold;
+    P.gmin = s->photon_min_gamma;
+    P.pairs = s->pairs ? 1 : 0;
+    P.max_emit = s->max_emissions;
     // constants of the mixed path (FP32, or double-float pairs split here)
     auto hi_of = [](double v) { return (float)v; };
     auto lo_of = [](double v) { return (float)(v - (double)(float)v); };
-    qp::MixedConsts &m = a.mc;
+    qp::MixedConsts &m = P.mc;
     m.xf_hi = hi_of(f.x_focus);
     m.xf_lo = lo_of(f.x_focus);
     if (f.kind == QP_FIELD_YEE2D) {
-        m.idx_hi = hi_of(a.f.inv_dx);
-        m.idx_lo = lo_of(a.f.inv_dx);
-        m.idy_hi = hi_of(a.f.inv_dy);
-        m.idy_lo = lo_of(a.f.inv_dy);
-        m.x0s_hi = hi_of(a.f.x0s);
-        m.x0s_lo = lo_of(a.f.x0s);
-        m.y0s_hi = hi_of(a.f.y0s);
-        m.y0s_lo = lo_of(a.f.y0s);
+        m.idx_hi = hi_of(P.f.inv_dx);
+        m.idx_lo = lo_of(P.f.inv_dx);
+        m.idy_hi = hi_of(P.f.inv_dy);
+        m.idy_lo = lo_of(P.f.inv_dy);
+        m.x0s_hi = hi_of(P.f.x0s);
+        m.x0s_lo = lo_of(P.f.x0s);
+        m.y0s_hi = hi_of(P.f.y0s);
+        m.y0s_lo = lo_of(P.f.y0s);
         m.nxf = (float)f.nx;
         m.nyf = (float)f.ny;
     }
@@ -466,18 +446,330 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
         m.inv_w0sq = (float)(1.0 / (f.w0 * f.w0));
         m.k_env = (float)(2.0 * 0.6931471805599453 / (f.tau_fwhm * f.tau_fwhm));
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    return QP_OK;
+}
+
+// Context-wide launch arguments: tables, counters, status, units.
+void fill_globals(const qp_ctx *ctx, qp::StepArgs &a)
+{
+    const size_t R = qp::kNRatePad, CC = (size_t)qp::kNCdf * qp::kNNode;
+    a.tab.H = ctx->d_tab64;
+    a.tab.Gs = ctx->d_tab64 + R;
+    a.tab.Ts = ctx->d_tab64 + 2 * R;
+    a.tab.Cg = ctx->d_tab64 + 3 * R;
+    a.tab.Cp = ctx->d_tab64 + 3 * R + CC;
+    a.tab.Hf = ctx->d_tab32;
+    a.tab.Gsf = ctx->d_tab32 + R;
+    a.tab.Tsf = ctx->d_tab32 + 2 * R;
+    const float2 *c2 = reinterpret_cast<const float2 *>(ctx->d_tab32 + kTabRate);
+    a.tab.Cg2 = c2;
+    a.tab.Cp2 = c2 + CC;
+    a.tab.Qg2 = c2 + 2 * CC;
+    a.tab.Qp2 = c2 + 3 * CC;
+    a.tab.Eg = ctx->d_tab32 + kTabRate + 4 * kTabCdf;
+    a.tab.Ep = a.tab.Eg + qp::kNNode;
+    a.stats = ctx->d_stats;
+    a.status = ctx->d_status;
+    a.a_S = ctx->U.a_S;
+    a.C_rate = ctx->U.C_rate;
+    a.tau0w = ctx->U.tau0w;
+    a.spin_limit = kSpinLimit;
+}
+
+int blocks_per_sm(qp_ctx *ctx, int precision, int field_kind, bool batch)
+{
+    const int prec = precision == QP_MIXED ? 1 : 0;
+    int &bpsm = ctx->grid_cache[batch ? 1 : 0][prec][field_kind];
+    if (!bpsm) bpsm = qp::step_blocks_per_sm(precision, field_kind, batch);
+    return bpsm;
+}
+
+// Time of step `step` and the FP32 / double-float time constants of the
+// mixed path (the kernel of a batch computes the same values on the device).
+void set_time_host(qp::Problem &P, int64_t step)
+{
+    P.step = (uint64_t)step;
+    P.t = (double)step * P.dt;
+    const double tr = P.t - P.f.t_focus;
+    P.mc.t_hi = (float)P.t;
+    P.mc.t_lo = (float)(P.t - (double)P.mc.t_hi);
+    P.mc.tr_hi = (float)tr;
+    P.mc.tr_lo = (float)(tr - (double)P.mc.tr_hi);
+}
+
+// Look-back words of a problem's two chains: lepton tiles, photon tiles.
+void chain_words_of(const qp_ctx *ctx, const qp_step_params *s, size_t &lep, size_t &pho)
+{
+    auto cap = [&](int32_t h) { return h == -1 ? (int64_t)0 : ctx->species[h].d.capacity; };
+    lep = tiles_of(cap(s->electron)) + tiles_of(cap(s->positron)) + 4;
+    pho = tiles_of(cap(s->photon)) + 4;
+}
+
+}  // namespace
+
+int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!s) return QP_ERR_INVALID_ARG;
+    qp::StepArgs a{};
+    int st = build_problem(ctx, s, a.single);
+    if (st != QP_OK) return st;
+    if (s->n_steps == 0) return QP_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    size_t lep = 0, pho = 0;
+    chain_words_of(ctx, s, lep, pho);
+    st = ensure_chain(ctx, lep > pho ? lep : pho);
+    if (st != QP_OK) return st;
+    fill_globals(ctx, a);
+    a.ctl = ctx->d_ctl;
+    a.n_problems = 0;
+    a.problems = nullptr;
+    qp::Problem &P = a.single;
+    P.lep_words = ctx->d_chain;
+    P.pho_words = ctx->d_chain + ctx->chain_words;
+    P.pending = ctx->d_pending;
+    P.device_step = 0;
+
+    // persistent grid: resident blocks, never more than the tiles the
+    // species' capacities allow
+    const int bpsm = blocks_per_sm(ctx, s->precision, s->field.kind, false);
+    int64_t cap_tiles = 0;
+    const int32_t hs[3] = {s->electron, s->positron, s->photon};
+    for (int k = 0; k < 3; ++k)
+        if (hs[k] != -1) cap_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
+    const int64_t resident = (int64_t)bpsm * ctx->num_sms;
+    const int grid = (int)(cap_tiles < resident ? (cap_tiles > 0 ? cap_tiles : 1) : resident);
+    cudaStream_t cs = (cudaStream_t)stream;
     for (int32_t k = 0; k < s->n_steps; ++k) {
-        a.step = (uint64_t)(s->step + k);
-        a.t = (double)(s->step + k) * s->dt;
-        m.t_hi = hi_of(a.t);
-        m.t_lo = lo_of(a.t);
-        m.tr_hi = hi_of(a.t - f.t_focus);
-        m.tr_lo = lo_of(a.t - f.t_focus);
-        cudaError_t e = timed(ctx, 0, st, [&] { return qp::launch_step(a, s->precision, grid, st); });
+        set_time_host(P, s->step + k);
+        cudaError_t e = timed(ctx, 0, cs, [&] {
+            return qp::launch_step(a, s->precision, s->field.kind, false, grid, cs);
+        });
         if (e != cudaSuccess) return cuda_status(e);
     }
     return QP_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+struct qp_batch {
+    qp_ctx *ctx = nullptr;
+    int max = 0, precision = 0, field_kind = 0, grid = 1;
+    qp::Problem *d_table = nullptr;   // [max]
+    long long *d_step = nullptr;      // [max] next step of each problem
+    long long *d_left = nullptr;      // [max] launches still to run (0 = idle slot)
+    long long *d_pending = nullptr;   // [max][3]
+    long long *d_work = nullptr;      // [max] live slots stepped so far
+    qp::StepCtl *d_ctl = nullptr;
+    // pinned staging of the descriptors copied by qp_batch_set; entry k is
+    // reused only after the copy that read it has completed (its event)
+    qp::Problem *h_stage = nullptr;   // [2 max]
+    long long *h_stage_ctl = nullptr; // [2 max][2]: first step, steps
+    std::vector<cudaEvent_t> stage_ev;
+    int stage_next = 0;
+};
+
+namespace {
+
+void batch_release(qp_batch *b)
+{
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    for (cudaEvent_t e : b->stage_ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(b->d_table);
+    cudaFree(b->d_step);
+    cudaFree(b->d_left);
+    cudaFree(b->d_pending);
+    cudaFree(b->d_work);
+    cudaFree(b->d_ctl);
+    cudaFreeHost(b->h_stage);
+    cudaFreeHost(b->h_stage_ctl);
+    delete b;
+}
+
+}  // namespace
+
+int qp_batch_create(qp_ctx *ctx, int32_t max_problems, int32_t precision, int32_t field_kind,
+                    qp_batch **out)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!out || max_problems < 1 || max_problems > QP_MAX_BATCH) return QP_ERR_INVALID_ARG;
+    if (precision != QP_FP64 && precision != QP_MIXED) return QP_ERR_INVALID_ARG;
+    if (field_kind < QP_FIELD_NONE || field_kind > QP_FIELD_UNIFORM_B) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    qp_batch *b = new (std::nothrow) qp_batch;
+    if (!b) return QP_ERR_OOM;
+    b->ctx = ctx;
+    b->max = max_problems;
+    b->precision = precision;
+    b->field_kind = field_kind;
+    b->grid = blocks_per_sm(ctx, precision, field_kind, true) * ctx->num_sms;
+    const size_t n = (size_t)max_problems;
+    cudaError_t e = cudaSuccess;
+#define QP_TRY(x)                    \
+    do {                             \
+        e = (x);                     \
+        if (e != cudaSuccess) {      \
+            batch_release(b);        \
+            return cuda_status(e);   \
+        }                            \
+    } while (0)
+    QP_TRY(cudaMalloc(&b->d_table, n * sizeof(qp::Problem)));
+    QP_TRY(cudaMemset(b->d_table, 0, n * sizeof(qp::Problem)));
+    QP_TRY(cudaMalloc(&b->d_step, n * sizeof(long long)));
+    QP_TRY(cudaMemset(b->d_step, 0, n * sizeof(long long)));
+    QP_TRY(cudaMalloc(&b->d_left, n * sizeof(long long)));
+    QP_TRY(cudaMemset(b->d_left, 0, n * sizeof(long long)));
+    QP_TRY(cudaMalloc(&b->d_pending, 3 * n * sizeof(long long)));
+    QP_TRY(cudaMemset(b->d_pending, 0, 3 * n * sizeof(long long)));
+    QP_TRY(cudaMalloc(&b->d_work, n * sizeof(long long)));
+    QP_TRY(cudaMemset(b->d_work, 0, n * sizeof(long long)));
+    QP_TRY(cudaMalloc(&b->d_ctl, sizeof(qp::StepCtl)));
+    QP_TRY(cudaMemset(b->d_ctl, 0, sizeof(qp::StepCtl)));
+    QP_TRY(cudaMallocHost(&b->h_stage, 2 * n * sizeof(qp::Problem)));
+    QP_TRY(cudaMallocHost(&b->h_stage_ctl, 4 * n * sizeof(long long)));
+    b->stage_ev.assign(2 * n, nullptr);
+    for (size_t k = 0; k < 2 * n; ++k)
+        QP_TRY(cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming));
+    // empty slots hold a zeroed problem whose launch counter points at d_left
+    for (size_t k = 0; k < n; ++k) {
+        qp::Problem P{};
+        P.device_step = 1;
+        P.left_ctr = b->d_left + k;
+        P.step_ctr = b->d_step + k;
+        P.pending = b->d_pending + 3 * k;
+        P.work_ctr = b->d_work + k;
+        P.dt = 1.0;
+        QP_TRY(cudaMemcpy(b->d_table + k, &P, sizeof(P), cudaMemcpyHostToDevice));
+    }
+    QP_TRY(cudaDeviceSynchronize());
+#undef QP_TRY
+    *out = b;
+    return QP_OK;
+}
+
+int qp_batch_destroy(qp_batch *b)
+{
+    if (!b) return QP_ERR_NOT_INITIALIZED;
+    {
+        DeviceGuard g(b->ctx->device);
+        cudaDeviceSynchronize();
+    }
+    batch_release(b);
+    return QP_OK;
+}
+
+int qp_batch_scratch_words(qp_ctx *ctx, const qp_step_params *s, int64_t *words)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!s || !words) return QP_ERR_INVALID_ARG;
+    qp::Problem P;
+    const int st = build_problem(ctx, s, P);
+    if (st != QP_OK) return st;
+    size_t lep = 0, pho = 0;
+    chain_words_of(ctx, s, lep, pho);
+    *words = (int64_t)(lep + pho);
+    return QP_OK;
+}
+
+int qp_batch_set(qp_batch *b, int32_t slot, const qp_step_params *s, uint64_t *scratch,
+                 int64_t scratch_words, void *stream)
+{
+    if (!b) return QP_ERR_NOT_INITIALIZED;
+    if (!s || slot < 0 || slot >= b->max || !scratch) return QP_ERR_INVALID_ARG;
+    if (s->precision != b->precision || s->field.kind != b->field_kind) return QP_ERR_INVALID_ARG;
+    qp_ctx *ctx = b->ctx;
+    qp::Problem P;
+    int st = build_problem(ctx, s, P);
+    if (st != QP_OK) return st;
+    size_t lep = 0, pho = 0;
+    chain_words_of(ctx, s, lep, pho);
+    if (scratch_words < (int64_t)(lep + pho)) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    P.lep_words = (unsigned long long *)scratch;
+    P.pho_words = (unsigned long long *)scratch + lep;
+    P.pending = b->d_pending + 3 * (size_t)slot;
+    P.step_ctr = b->d_step + slot;
+    P.left_ctr = b->d_left + slot;
+    P.work_ctr = b->d_work + slot;
+    P.device_step = 1;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int k = b->stage_next;
+    b->stage_next = (k + 1) % (2 * b->max);
+    cudaError_t e = cudaEventSynchronize(b->stage_ev[k]);  // the entry's last copy is done
+    if (e != cudaSuccess) return cuda_status(e);
+    b->h_stage[k] = P;
+    b->h_stage_ctl[2 * k] = s->step;
+    b->h_stage_ctl[2 * k + 1] = s->n_steps;
+    const int32_t hs[3] = {s->electron, s->positron, s->photon};
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        if (hs[q] != -1) e = cudaMemsetAsync(ctx->d_stats + hs[q], 0, sizeof(qp::DevStats), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, (lep + pho) * sizeof(uint64_t), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_work + slot, 0, sizeof(long long), cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_table + slot, &b->h_stage[k], sizeof(qp::Problem),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_step + slot, &b->h_stage_ctl[2 * k], sizeof(long long),
+                            cudaMemcpyHostToDevice, cs);
+    // activation last: the slot is stepped from the next launch on
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_left + slot, &b->h_stage_ctl[2 * k + 1], sizeof(long long),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(b->stage_ev[k], cs);
+    return cuda_status(e);
+}
+
+int qp_batch_clear(qp_batch *b, int32_t slot, void *stream)
+{
+    if (!b) return QP_ERR_NOT_INITIALIZED;
+    if (slot < 0 || slot >= b->max) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(b->ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    return cuda_status(
+        cudaMemsetAsync(b->d_left + slot, 0, sizeof(long long), (cudaStream_t)stream));
+}
+
+int qp_batch_step(qp_batch *b, int32_t n_launches, void *stream)
+{
+    if (!b) return QP_ERR_NOT_INITIALIZED;
+    if (n_launches < 0) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(b->ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    qp::StepArgs a{};
+    fill_globals(b->ctx, a);
+    a.ctl = b->d_ctl;
+    a.n_problems = b->max;
+    a.problems = b->d_table;
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (int32_t k = 0; k < n_launches; ++k) {
+        cudaError_t e = timed(b->ctx, 0, cs, [&] {
+            return qp::launch_step(a, b->precision, b->field_kind, true, b->grid, cs);
+        });
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return QP_OK;
+}
+
+int qp_batch_progress(qp_batch *b, int64_t *steps_left, int64_t *next_step, int64_t *work,
+                      void *stream)
+{
+    if (!b) return QP_ERR_NOT_INITIALIZED;
+    if (!steps_left) return QP_ERR_INVALID_ARG;
+    DeviceGuard g(b->ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const size_t bytes = (size_t)b->max * sizeof(long long);
+    cudaError_t e = cudaMemcpyAsync(steps_left, b->d_left, bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && next_step)
+        e = cudaMemcpyAsync(next_step, b->d_step, bytes, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && work)
+        e = cudaMemcpyAsync(work, b->d_work, bytes, cudaMemcpyDeviceToHost, cs);
+    return cuda_status(e);
 }
 
 int qp_diagnostics(qp_ctx *ctx, int32_t handle, qp_diag *out, void *stream)

@@ -21,6 +21,7 @@ struct SpeciesDev {
     int32_t *nemit;
     int64_t *n_live;
     int64_t cap;
+    int64_t id_base;     // global number of slot 0: particle id = id_base + slot
     int32_t present;
     int32_t slot_stats;  // index of this species' counter block
 };
@@ -65,31 +66,46 @@ struct MixedConsts {
     float nxf, nyf;                            // Yee grid size
 };
 
-// Device-resident control block of a context's steps: the tile ticket, the
-// count of finished blocks, the launch epoch that tags look-back words, and
-// the new live counts (e-, e+, photons) applied by the last block.
+// Device-resident control block of a launch sequence: the tile ticket, the
+// count of finished blocks and the launch epoch that tags look-back words.
 struct StepCtl {
     unsigned ticket, done, epoch, pad;
-    long long pending[3];
-    long long pad2;
+};
+
+constexpr int kMaxProblems = 64;  // problems (independent runs) per launch
+
+// One independent run stepped by a launch: its species, field, step
+// constants, look-back scratch and control words.  A launch steps either a
+// single problem passed by value (qp_step) or a device table of problems
+// (a batch); the kernel copies the problem of each tile to shared memory.
+struct Problem {
+    SpeciesDev sp[3];                 // electron, positron, photon
+    FieldDev f;
+    MixedConsts mc;                   // t_*, tr_* set per launch on the device
+    unsigned long long *lep_words;    // look-back words of the lepton chain
+    unsigned long long *pho_words;    // look-back words of the photon chain
+    long long *pending;               // [3] new live counts, applied by the last block
+    long long *step_ctr;              // device-stepped: next step index
+    long long *left_ctr;              // device-stepped: launches still to run (0 = idle)
+    long long *work_ctr;              // device-stepped: live slots stepped so far
+    double dt, t;                     // t = step dt, set per launch on the device
+    uint64_t step, seed;
+    double chi_th, gmin;
+    int32_t pairs, max_emit;
+    int32_t device_step;              // 1: step and activity from step_ctr/left_ctr
+    int32_t pad;
 };
 
 struct StepArgs {
-    SpeciesDev sp[3];                 // electron, positron, photon
-    FieldDev f;
     TablesDev tab;
-    unsigned long long *lep_words;    // look-back words of the lepton chain
-    unsigned long long *pho_words;    // look-back words of the photon chain
     StepCtl *ctl;
     DevStats *stats;                  // counters, indexed by species handle
     int *status;                      // sticky status word
-    double dt, t;
-    uint64_t step, seed;
-    double chi_th, gmin;
     double a_S, C_rate, tau0w;
-    int32_t pairs, max_emit;
     unsigned int spin_limit;          // bound of every device-side wait
-    MixedConsts mc;
+    int32_t n_problems;               // 0: the single problem below
+    const Problem *problems;          // device table of n_problems entries
+    Problem single;
 };
 
 // ------------------------------------------------------------------ status

@@ -7,11 +7,17 @@
 
 namespace qp {
 
-cudaError_t launch_step(const StepArgs &a, int precision, int grid, cudaStream_t st);
-int step_blocks_per_sm(int precision, int field_kind);
+cudaError_t launch_step(const StepArgs &a, int precision, int field_kind, bool batch, int grid,
+                        cudaStream_t st);
+int step_blocks_per_sm(int precision, int field_kind, bool batch);
+// per-precision instantiations of the step kernel (qp_step_fp64.cu, qp_step_mixed.cu)
+const void *step_kernel_fp64(int field_kind, bool batch);
+const void *step_kernel_mixed(int field_kind, bool batch);
+size_t step_smem_fp64();
+size_t step_smem_mixed();
 size_t step_smem_bytes(int precision);
-cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, uint64_t seed, int species,
-                            cudaStream_t st);
+cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
+                            uint64_t seed, int species, cudaStream_t st);
 cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, int nblocks,
                         double *out, cudaStream_t st);
 cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit, int *status,

@@ -1,0 +1,1074 @@
+// The step kernel of libqedpic (sm_103a), instantiated per precision in
+// qp_step_fp64.cu and qp_step_mixed.cu.
+//
+// One QED particle step is ONE launch of the persistent kernel k_step.  Its
+// blocks take 128-particle tiles from one atomic ticket over a single tile
+// space: per problem, first the electron tiles, then the positron tiles
+// (together: the lepton chain), then the photon tiles (the photon chain).
+//   lepton tile : gather, Boris, chi_e, Sokolov or optical depth + emission,
+//                 position update; new photons appended in slot order;
+//   photon tile : chi_gamma, pair optical depth, decay into an e-/e+ pair
+//                 appended in slot order, ballistic motion.
+// Lepton tiles only append photons at slots >= the photon count of the step
+// start and photon tiles only append leptons at slots >= the lepton counts,
+// so the two chains never touch the same slots and both run in the same
+// launch.  The live counts are read-only during the launch; the last block to
+// finish applies the new counts, resets the ticket and advances the launch
+// epoch (device memory), which tags the look-back words: no memset and no
+// host-side state between steps, so a step can be replayed in a CUDA graph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <type_traits>
+
+#include "qp_device.cuh"
+#include "qp_kernels.h"
+#include "qp_mixed.cuh"
+
+namespace qp {
+
+namespace {
+
+// Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).
+constexpr int kEpochShift = 40, kFlagShift = 38;
+constexpr unsigned long long kValMask = (1ull << kFlagShift) - 1;
+constexpr unsigned kEpochMask = 0xFFFFFFu;
+constexpr unsigned kFlagAgg = 1u, kFlagPre = 2u;
+
+__device__ __forceinline__ unsigned long long make_word(unsigned epoch, unsigned flag,
+                                                        long long value)
+{
+    return ((unsigned long long)(epoch & kEpochMask) << kEpochShift) |
+           ((unsigned long long)flag << kFlagShift) | ((unsigned long long)value & kValMask);
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p)
+{
+    return *((const volatile unsigned long long *)p);
+}
+
+// Exclusive prefix of this tile in its chain, computed by one full warp
+// (decoupled look-back with a 32-tile window): lane l inspects tile
+// base - l; a word counts only if it carries this launch's epoch.  The
+// window is consumed up to the nearest tile that published its inclusive
+// prefix, summing the aggregates in between.  Waits are bounded by
+// spin_limit; on time-out the status is raised and the prefix is what was
+// summed so far (the output is then wrong, the status says so, and the
+// kernel still terminates).  Returns the prefix in every lane.
+__device__ long long chain_prefix(unsigned long long *words, unsigned tile, long long aggregate,
+                                  unsigned epoch, unsigned spin_limit, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) atomicExch(words, make_word(epoch, kFlagPre, aggregate));
+        return 0;
+    }
+    if (lane == 0) atomicExch(words + tile, make_word(epoch, kFlagAgg, aggregate));
+    long long excl = 0;
+    long long base = (long long)tile - 1;
+    unsigned spins = 0;
+    for (;;) {
+        const long long idx = base - lane;
+        // before tile 0 the chain is complete: read as "prefix 0"
+        const unsigned long long w =
+            idx >= 0 ? ld_volatile(words + idx) : make_word(epoch, kFlagPre, 0);
+        const bool current = (unsigned)(w >> kEpochShift) == (epoch & kEpochMask);
+        const unsigned flag = current ? (unsigned)(w >> kFlagShift) & 3u : 0u;
+        const unsigned pre = __ballot_sync(0xFFFFFFFFu, flag == kFlagPre);
+        const unsigned empty = __ballot_sync(0xFFFFFFFFu, flag == 0u);
+        const int first = pre ? __ffs(pre) - 1 : 32;  // nearest inclusive prefix
+        const unsigned need = first == 32 ? 0xFFFFFFFFu : (2u << first) - 1u;
+        if (empty & need) {
+            if (++spins > spin_limit) {
+                if (lane == 0) raise_status(status, QP_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+            continue;
+        }
+        long long v = lane <= first ? (long long)(w & kValMask) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+        excl += v;
+        if (first < 32) break;
+        base -= 32;
+    }
+    if (lane == 0) atomicExch(words + tile, make_word(epoch, kFlagPre, excl + aggregate));
+    return excl;
+}
+
+// Block-wide exclusive scan of one small count per thread; returns the
+// thread's exclusive offset and writes the block total to *total.
+__device__ __forceinline__ int block_scan(int v, int *s_warp, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kWarps ? s_warp[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < kWarps; d <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < kWarps) s_warp[lane] = w;
+    }
+    __syncthreads();
+    *total = s_warp[kWarps - 1];
+    return inc - v + (warp ? s_warp[warp - 1] : 0);
+}
+
+// Exact widening of a stashed value (FP32 values by integer instructions).
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return f_to_d(v); }
+
+// Counters kept in shared memory per block and species, flushed with one
+// atomic per counter when the block leaves.
+struct BlockStats {
+    unsigned long long c[3][9];
+    double e[3][2];
+};
+enum { cEmit, cPhoton, cPhotonDrop, cSub, cPair, cPairDrop, cSat, cClamp, cCont };
+
+__device__ __forceinline__ void warp_count(unsigned long long *ctr, bool pred)
+{
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+__device__ __forceinline__ void clear_stats(BlockStats &bs)
+{
+    const int t = threadIdx.x;
+    if (t < 27) (&bs.c[0][0])[t] = 0ull;
+    if (t < 6) (&bs.e[0][0])[t] = 0.0;
+}
+
+__device__ void flush_stats(const BlockStats &bs, const StepArgs &a, const Problem &P)
+{
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < 27) {
+        const int s = t / 9, k = t % 9;
+        if (bs.c[s][k] && P.sp[s].present)
+            atomicAdd(&a.stats[P.sp[s].slot_stats].n_emit + k, bs.c[s][k]);
+    } else if (t >= 32 && t < 38) {
+        const int s = (t - 32) / 2, k = (t - 32) % 2;
+        if (bs.e[s][k] != 0.0 && P.sp[s].present)
+            atomicAdd(&a.stats[P.sp[s].slot_stats].e_subthreshold + k, bs.e[s][k]);
+    }
+    if (t == 0 && (bs.c[0][cClamp] | bs.c[1][cClamp] | bs.c[2][cClamp]))
+        raise_status(a.status, QP_WARN_TABLE_CLAMPED);
+}
+
+// Shared-memory layout of k_step (dynamic part).
+template <typename R>
+struct Smem {
+    R H[kNRatePad];                          // rate tables (TMA-staged)
+    R G[kNRatePad];
+    R T[kNRatePad];
+    R gg[QP_MAX_EMISSIONS][kTile];           // stashed photon energies
+    R tg[QP_MAX_EMISSIONS][kTile];           // and their optical depths
+};
+
+__device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepArgs &a)
+{
+    if (!mbar_wait_bounded(bar, 0, a.spin_limit)) {
+        raise_status(a.status, QP_ERR_TIMEOUT);
+        (void)mbar_wait_bounded(bar, 0, a.spin_limit);  // never leave with a copy in flight
+    }
+}
+
+// -------------------------------------------------------------------- lepton tile
+
+template <int PREC, int FK, typename R>
+__device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
+                            unsigned long long *bar,
+                            bool &loaded, unsigned chain_tile, int sp, int64_t first, int64_t n,
+                            int64_t ph_base, unsigned epoch, int *s_warp, long long *s_excl,
+                            BlockStats &bs)
+{
+    const int tid = threadIdx.x;
+    if (!loaded && tid == 0) {
+        // stage the rate tables with one TMA bulk copy each; the copy
+        // overlaps the particle loads, gather and push below
+        const unsigned bytes = kNRatePad * sizeof(R);
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, 2 * bytes);
+        if constexpr (PREC == kFP64) {
+            bulk_g2s(sm.H, a.tab.H, bytes, bar);
+            bulk_g2s(sm.G, a.tab.Gs, bytes, bar);
+        } else {
+            bulk_g2s(sm.H, a.tab.Hf, bytes, bar);
+            bulk_g2s(sm.G, a.tab.Gsf, bytes, bar);
+        }
+    }
+    if (!loaded) __syncthreads();
+    const SpeciesDev &S = P.sp[sp];
+    const SpeciesDev &Ph = P.sp[2];
+    const bool photons = Ph.present != 0;
+    const int64_t i = first + tid;
+    const bool active = i < n;
+
+    int nph = 0;
+    double x0 = 0, y0 = 0, z0 = 0, kx = 0, ky = 0, kz = 0, wgt = 0;
+    bool cont = false, sat = false, clamped = false;
+    int n_emit = 0, n_sub = 0;
+    double e_sub = 0.0;
+
+    if constexpr (PREC == kFP64) {
+    if (active) {
+        const double q = sp == 0 ? -1.0 : 1.0;
+        const double dt = P.dt;
+        x0 = S.x[i];
+        y0 = S.y[i];
+        z0 = S.z ? S.z[i] : 0.0;
+        double ux = S.ux[i], uy = S.uy[i], uz = S.uz[i];
+        double tau = S.tau[i];
+        Vec3<R> E, B;
+        eval_field<FK, R>(P.f, x0, y0, z0, P.t, E, B);
+
+        // ---- Boris push of the Lorentz force (f_l of Eq. 4)
+        if constexpr (PREC == kFP64) {
+            const double h = 0.5 * q * dt;
+            const double mx = ux + h * E.x, my = uy + h * E.y, mz = uz + h * E.z;
+            const double g = sqrt(1.0 + mx * mx + my * my + mz * mz);
+            const double tx = h * B.x / g, ty = h * B.y / g, tz = h * B.z / g;
+            const double t2 = tx * tx + ty * ty + tz * tz;
+            const double sx = 2.0 * tx / (1.0 + t2), sy = 2.0 * ty / (1.0 + t2),
+                         sz = 2.0 * tz / (1.0 + t2);
+            const double px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+                         pz = mz + (mx * ty - my * tx);
+            ux = mx + (py * sz - pz * sy) + h * E.x;
+            uy = my + (pz * sx - px * sz) + h * E.y;
+            uz = mz + (px * sy - py * sx) + h * E.z;
+        } else {
+            // FP32 rotation, FP64 accumulation of the momentum
+            const float h = (float)(0.5 * q * dt);
+            const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
+            const double mx = ux + hx, my = uy + hy, mz = uz + hz;
+            const float fx = (float)mx, fy = (float)my, fz = (float)mz;
+            const float ig = rsqrtf(1.0f + fx * fx + fy * fy + fz * fz);
+            const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
+            const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+            const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
+            const float px = fx + (fy * tz - fz * ty), py = fy + (fz * tx - fx * tz),
+                        pz = fz + (fx * ty - fy * tx);
+            ux = mx + (double)((py * sz - pz * sy) + hx);
+            uy = my + (double)((pz * sx - px * sz) + hy);
+            uz = mz + (double)((px * sy - py * sx) + hz);
+        }
+        double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+        const double Ex = E.x, Ey = E.y, Ez = E.z, Bx = B.x, By = B.y, Bz = B.z;
+        if (!loaded) wait_tables(bar, a);  // tables are needed from here on
+        double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
+        if (S.chi) S.chi[i] = chi;
+        double dvx = 0.0, dvy = 0.0, dvz = 0.0;
+
+        if (chi < P.chi_th) {
+            // ---- Sokolov continuous regime (Eq. 4, P_rad of Eq. 5)
+            cont = true;
+            if constexpr (PREC == kFP64) {
+                const double vx = ux / gam, vy = uy / gam, vz = uz / gam;
+                const double fx = q * (Ex + (vy * Bz - vz * By));
+                const double fy = q * (Ey + (vz * Bx - vx * Bz));
+                const double fz = q * (Ez + (vx * By - vy * Bx));
+                const double vf = vx * fx + vy * fy + vz * fz;
+                const double den = 1.0 + a.tau0w * vf;
+                dvx = a.tau0w * (fx - vx * vf) / den;
+                dvy = a.tau0w * (fy - vy * vf) / den;
+                dvz = a.tau0w * (fz - vz * vf) / den;
+                const double prad = a.C_rate * rate64<1>(sm.G, chi, clamped);
+                ux = ux + dt * (q * (dvy * Bz - dvz * By) - prad * vx);
+                uy = uy + dt * (q * (dvz * Bx - dvx * Bz) - prad * vy);
+                uz = uz + dt * (q * (dvx * By - dvy * Bx) - prad * vz);
+            } else {
+                const float ig = (float)(1.0 / gam), qf = (float)q;
+                const float vx = (float)ux * ig, vy = (float)uy * ig, vz = (float)uz * ig;
+                const float fx = qf * (E.x + (vy * B.z - vz * B.y));
+                const float fy = qf * (E.y + (vz * B.x - vx * B.z));
+                const float fz = qf * (E.z + (vx * B.y - vy * B.x));
+                const float vf = vx * fx + vy * fy + vz * fz;
+                const double den = 1.0 + a.tau0w * (double)vf;  // FP64 denominator
+                const float c = (float)(a.tau0w / den);
+                const float dx_ = c * (fx - vx * vf), dy_ = c * (fy - vy * vf),
+                            dz_ = c * (fz - vz * vf);
+                dvx = dx_;
+                dvy = dy_;
+                dvz = dz_;
+                const float prad = (float)a.C_rate * rate32<1>(sm.G, (float)chi, clamped);
+                const float dtf = (float)dt;
+                ux += (double)(dtf * (qf * (dy_ * B.z - dz_ * B.y) - prad * vx));
+                uy += (double)(dtf * (qf * (dz_ * B.x - dx_ * B.z) - prad * vy));
+                uz += (double)(dtf * (qf * (dx_ * B.y - dy_ * B.x) - prad * vz));
+            }
+            gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+        } else {
+            // ---- optical depth (Eq. 6) with the residual-time sub-loop
+            double r = 1.0;
+            for (int k = 0;; ++k) {
+                double wdt, dtau;
+                if constexpr (PREC == kFP64) {
+                    const double H = rate64<0>(sm.H, chi, clamped);
+                    wdt = a.C_rate * H / gam * dt;
+                    dtau = wdt * r;
+                } else {
+                    const float H = rate32<0>(sm.H, (float)chi, clamped);
+                    const float wf = (float)a.C_rate * H / (float)gam * (float)dt;
+                    wdt = wf;
+                    dtau = (double)(wf * (float)r);
+                }
+                if (!(dtau > 0.0) || tau > dtau) {
+                    tau = tau - dtau;
+                    break;
+                }
+                if (k == P.max_emit) {
+                    tau = tau - dtau;
+                    sat = true;
+                    break;
+                }
+                r = r - tau / wdt;
+                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
+                const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
+                const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
+                double ufrac;
+                ufrac = sample_cdf<double>(a.tab.Cg, chi, xi_p, kSgMin, kSgSpan, true, clamped);
+                const double pmag = sqrt(ux * ux + uy * uy + uz * uz);
+                double gg = ufrac * gam;
+                if (gg > pmag) gg = pmag;
+                if (n_emit == 0 && pmag > 0.0) {
+                    kx = ux / pmag;
+                    ky = uy / pmag;
+                    kz = uz / pmag;
+                }
+                ++n_emit;
+                if (gg > P.gmin) {
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
+                    sm.gg[nph][tid] = gg;
+                    sm.tg[nph][tid] = -log(u53(rp.x, rp.y));
+                    ++nph;
+                } else {
+                    ++n_sub;
+                    e_sub += gg;
+                }
+                if (pmag > 0.0) {
+                    const double scale = (pmag - gg) / pmag;
+                    ux *= scale;
+                    uy *= scale;
+                    uz *= scale;
+                }
+                tau = -log(xi);
+                gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+                chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
+            }
+        }
+
+        // ---- position (Eq. 4: dx/dt = v + delta v)
+        if constexpr (PREC == kFP64) {
+            S.x[i] = x0 + dt * (ux / gam + dvx);
+            S.y[i] = y0 + dt * (uy / gam + dvy);
+            if (S.z) S.z[i] = z0 + dt * (uz / gam + dvz);
+        } else {
+            const float ig = (float)(1.0 / gam), dtf = (float)dt;
+            S.x[i] = x0 + (double)(dtf * ((float)ux * ig + (float)dvx));
+            S.y[i] = y0 + (double)(dtf * ((float)uy * ig + (float)dvy));
+            if (S.z) S.z[i] = z0 + (double)(dtf * ((float)uz * ig + (float)dvz));
+        }
+        S.ux[i] = ux;
+        S.uy[i] = uy;
+        S.uz[i] = uz;
+        S.tau[i] = tau;
+        if (nph || n_sub) wgt = S.w[i];
+    }
+    } else {
+    if (active) {
+        // ---- mixed precision: FP32 physics; the FP64 state is read once,
+        // increments are formed in FP32 and added back by integer
+        // instructions; chi_e falls back to double-float where FP32 cancels
+        const MixedConsts &m = P.mc;
+        const double xd = S.x[i], yd = S.y[i], zd = S.z ? S.z[i] : 0.0;
+        x0 = xd;
+        y0 = yd;
+        z0 = zd;
+        const double uxd = S.ux[i], uyd = S.uy[i], uzd = S.uz[i];
+        const double taud = S.tau[i];
+        Vec3<float> E, B;
+        eval_field_mixed<FK>(P.f, m, split_d(xd), split_d(yd), split_d(zd), E, B);
+
+        // Boris on the leading FP32 parts; the increment is kept in FP32
+        const float u0x = hi_d(uxd), u0y = hi_d(uyd), u0z = hi_d(uzd);
+        const float h = m.h[sp];
+        const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
+        const float mx = u0x + hx, my = u0y + hy, mz = u0z + hz;
+        const float ig = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+        const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
+        const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+        const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
+        const float px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+                    pz = mz + (mx * ty - my * tx);
+        float dux = (py * sz - pz * sy) + 2.0f * hx, duy = (pz * sx - px * sz) + 2.0f * hy,
+              duz = (px * sy - py * sx) + 2.0f * hz;
+        float ux = u0x + dux, uy = u0y + duy, uz = u0z + duz;
+        float gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        if (!loaded) wait_tables(bar, a);  // tables are needed from here on
+        float chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B, m.inv_aS,
+                                   m.inv_aS_lo);
+        if (S.chi) S.chi[i] = f_to_d(chi);
+        float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
+        float dtau_once = 0.0f;
+        bool events = false;
+        df2 TAU = {0.0f, 0.0f};
+
+        if (chi < m.chi_th) {
+            // ---- Sokolov (Eq. 4, 5); denominator 1 + tau0 v.f_l in double-float
+            cont = true;
+            const float q = sp == 0 ? -1.0f : 1.0f;
+            const float gi = 1.0f / gam;
+            const float vx = ux * gi, vy = uy * gi, vz = uz * gi;
+            const float fx = q * (E.x + (vy * B.z - vz * B.y));
+            const float fy = q * (E.y + (vz * B.x - vx * B.z));
+            const float fz = q * (E.z + (vx * B.y - vy * B.x));
+            const float vf = vx * fx + vy * fy + vz * fz;
+            const df2 den = two_sum(1.0f, m.tau0w * vf);
+            const float c = m.tau0w / den.hi * (1.0f - den.lo / den.hi);
+            dvx = c * (fx - vx * vf);
+            dvy = c * (fy - vy * vf);
+            dvz = c * (fz - vz * vf);
+            const float prad = m.C_rate * rate32<1>(sm.G, chi, clamped);
+            const float sx_ = m.dt * (q * (dvy * B.z - dvz * B.y) - prad * vx);
+            const float sy_ = m.dt * (q * (dvz * B.x - dvx * B.z) - prad * vy);
+            const float sz_ = m.dt * (q * (dvx * B.y - dvy * B.x) - prad * vz);
+            dux += sx_;
+            duy += sy_;
+            duz += sz_;
+            ux += sx_;
+            uy += sy_;
+            uz += sz_;
+            gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        } else {
+            // ---- optical depth (Eq. 6) with the residual-time sub-loop
+            TAU = split_d(taud);
+            float r = 1.0f;
+            for (int k = 0;; ++k) {
+                const float H = rate32<0>(sm.H, chi, clamped);
+                const float wdt = m.C_rate * H / gam * m.dt;
+                const float dtau = wdt * r;
+                // tau > dtau decided on the double-float optical depth
+                if (!(dtau > 0.0f) || TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f)) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    break;
+                }
+                if (k == P.max_emit) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    sat = true;
+                    break;
+                }
+                events = true;
+                r = r - df_to_f(TAU) / wdt;
+                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
+                const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
+                const float xi = u53f(rr.z, rr.w);
+                const FracPair uf = sample_cdf_f(
+                    a.tab.Cg2, a.tab.Qg2, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
+                    u53_pair_complement(rr.x, rr.y), (float)(kSgSpan / (kNNode - 1)), true,
+                    clamped);
+                const float pmag = sqrtf(ux * ux + uy * uy + uz * uz);
+                float gg = uf.x * gam;
+                // what the electron keeps, |p| - u gamma = (1-u) gamma - 1/(gamma + |p|),
+                // formed without cancellation
+                float keep = uf.omx * gam - 1.0f / (gam + pmag);
+                if (gg > pmag || keep < 0.0f) {
+                    gg = pmag;
+                    keep = 0.0f;
+                }
+                if (n_emit == 0 && pmag > 0.0f) {
+                    const float ip = 1.0f / pmag;
+                    kx = f_to_d(ux * ip);
+                    ky = f_to_d(uy * ip);
+                    kz = f_to_d(uz * ip);
+                }
+                ++n_emit;
+                if (gg > m.gmin) {
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
+                    sm.gg[nph][tid] = gg;
+                    sm.tg[nph][tid] = -logf(u53f(rp.x, rp.y));
+                    ++nph;
+                } else {
+                    ++n_sub;
+                    e_sub += f_to_d(gg);
+                }
+                if (pmag > 0.0f) {
+                    const float s1 = keep / pmag;
+                    const float s1m = s1 - 1.0f;  // exact (Sterbenz) for s1 in [1/2, 1]
+                    dux = fmaf(ux, s1m, dux);
+                    duy = fmaf(uy, s1m, duy);
+                    duz = fmaf(uz, s1m, duz);
+                    ux *= s1;
+                    uy *= s1;
+                    uz *= s1;
+                }
+                TAU = {-logf(xi), 0.0f};
+                gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B,
+                                     m.inv_aS, m.inv_aS_lo);
+            }
+        }
+
+        // ---- position and write-back: FP64 accumulation of FP32 increments
+        const float gi = 1.0f / gam;
+        S.x[i] = add_fd(xd, m.dt * (ux * gi + dvx));
+        S.y[i] = add_fd(yd, m.dt * (uy * gi + dvy));
+        if (S.z) S.z[i] = add_fd(zd, m.dt * (uz * gi + dvz));
+        S.ux[i] = add_fd(uxd, dux);
+        S.uy[i] = add_fd(uyd, duy);
+        S.uz[i] = add_fd(uzd, duz);
+        if (events)
+            S.tau[i] = merge_df(TAU);
+        else if (dtau_once != 0.0f)
+            S.tau[i] = add_fd(taud, -dtau_once);
+        if (nph || n_sub) wgt = S.w[i];
+    }
+    }
+    if (active && n_emit && S.nemit) S.nemit[i] += n_emit;
+    if (!loaded) {
+        // threads without a particle also wait, so the block never leaves
+        // (or reuses the tables) with the copy in flight
+        if (!active) wait_tables(bar, a);
+        loaded = true;
+    }
+
+    // ---- counters (warp-aggregated into shared memory)
+    warp_count(&bs.c[sp][cCont], cont);
+    warp_count(&bs.c[sp][cSat], sat);
+    warp_count(&bs.c[sp][cClamp], clamped);
+    if (__any_sync(0xFFFFFFFFu, n_emit > 0)) {
+        if (n_emit) atomicAdd(&bs.c[sp][cEmit], (unsigned long long)n_emit);
+        if (n_sub) {
+            atomicAdd(&bs.c[sp][cSub], (unsigned long long)n_sub);
+            atomicAdd(&bs.e[sp][0], wgt * e_sub);
+        }
+    }
+
+    // ---- ordered append of the new photons
+    int tile_total;
+    const int local = block_scan(nph, s_warp, &tile_total);
+    if (tid < 32) {
+        const long long e =
+            chain_prefix(P.lep_words, chain_tile, tile_total, epoch, a.spin_limit, a.status);
+        if (tid == 0) *s_excl = e;
+    }
+    __syncthreads();
+    const long long excl = *s_excl;
+    if (nph) {
+        const int64_t base = ph_base + excl + local;
+        int stored = 0, dropped = 0;
+        double e_drop = 0.0;
+        for (int j = 0; j < nph; ++j) {
+            const int64_t slot = base + j;
+            const double gg = to_double(sm.gg[j][tid]);
+            if (photons && slot < Ph.cap) {
+                Ph.x[slot] = x0;
+                Ph.y[slot] = y0;
+                if (Ph.z) Ph.z[slot] = z0;
+                Ph.ux[slot] = gg * kx;
+                Ph.uy[slot] = gg * ky;
+                Ph.uz[slot] = gg * kz;
+                Ph.tau[slot] = to_double(sm.tg[j][tid]);
+                Ph.w[slot] = wgt;
+                if (Ph.chi) Ph.chi[slot] = 0.0;
+                if (Ph.nemit) Ph.nemit[slot] = 0;
+                ++stored;
+            } else {
+                ++dropped;
+                e_drop += wgt * gg;
+            }
+        }
+        if (stored) atomicAdd(&bs.c[sp][cPhoton], (unsigned long long)stored);
+        if (dropped) {
+            atomicAdd(&bs.c[sp][cPhotonDrop], (unsigned long long)dropped);
+            atomicAdd(&bs.e[sp][1], e_drop);
+        }
+    }
+    // s_excl and s_warp[kWarps - 1] (the tile total) stay valid for the caller
+    // until its next barrier
+}
+
+// -------------------------------------------------------------------- photon tile
+
+template <int PREC, int FK, typename R>
+__device__ void photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
+                            unsigned long long *bar,
+                            bool &loaded, unsigned chain_tile, int64_t n, int64_t be, int64_t bp,
+                            int64_t room, unsigned epoch, int *s_warp, long long *s_excl,
+                            BlockStats &bs, int *tile_total_out)
+{
+    const int tid = threadIdx.x;
+    const SpeciesDev &Ph = P.sp[2], &El = P.sp[0], &Po = P.sp[1];
+    const bool pairs = P.pairs != 0;
+    const bool leptons = El.present && Po.present;
+    if (pairs && !loaded) {
+        if (tid == 0) {
+            const unsigned bytes = kNRatePad * sizeof(R);
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, bytes);
+            if constexpr (PREC == kFP64)
+                bulk_g2s(sm.T, a.tab.Ts, bytes, bar);
+            else
+                bulk_g2s(sm.T, a.tab.Tsf, bytes, bar);
+        }
+        __syncthreads();
+        wait_tables(bar, a);
+        loaded = true;
+    }
+    const int64_t i = (int64_t)chain_tile * kTile + tid;
+    int npair = 0;
+    double px = 0, py = 0, pz = 0, gux = 0, guy = 0, guz = 0, wg = 0, v = 0, omv = 0, tm = 0, tp = 0;
+    bool clamped = false;
+
+    if constexpr (PREC == kFP64) {
+    if (i < n) {
+        double tau = Ph.tau[i];
+        if (tau >= 0.0) {
+            px = Ph.x[i];
+            py = Ph.y[i];
+            pz = Ph.z ? Ph.z[i] : 0.0;
+            gux = Ph.ux[i];
+            guy = Ph.uy[i];
+            guz = Ph.uz[i];
+            const double g = sqrt(gux * gux + guy * guy + guz * guz);
+            const double dt = P.dt;
+            bool decayed = false;
+            if (pairs && g > 2.0) {
+                Vec3<R> E, B;
+                eval_field<FK, R>(P.f, px, py, pz, P.t, E, B);
+                double chi, dtau;
+                if constexpr (PREC == kFP64) {
+                    const double kx = gux / g, ky = guy / g, kz = guz / g;
+                    const double ax = E.x + (ky * B.z - kz * B.y);
+                    const double ay = E.y + (kz * B.x - kx * B.z);
+                    const double az = E.z + (kx * B.y - ky * B.x);
+                    const double ke = kx * E.x + ky * E.y + kz * E.z;
+                    const double s = ax * ax + ay * ay + az * az - ke * ke;
+                    chi = s > 0.0 ? g * sqrt(s) / a.a_S : 0.0;
+                    const double Tr = rate64<2>(sm.T, chi, clamped);
+                    dtau = a.C_rate * Tr / g * dt;
+                } else {
+                    const float ig = (float)(1.0 / g);
+                    const float kx = (float)gux * ig, ky = (float)guy * ig, kz = (float)guz * ig;
+                    const float ax = E.x + (ky * B.z - kz * B.y);
+                    const float ay = E.y + (kz * B.x - kx * B.z);
+                    const float az = E.z + (kx * B.y - ky * B.x);
+                    const float ke = kx * E.x + ky * E.y + kz * E.z;
+                    const float s = ax * ax + ay * ay + az * az - ke * ke;
+                    const float cf = s > 0.0f ? (float)g * sqrtf(s) * (float)(1.0 / a.a_S) : 0.0f;
+                    chi = cf;
+                    const float Tr = rate32<2>(sm.T, cf, clamped);
+                    dtau = (double)((float)a.C_rate * Tr / (float)g * (float)dt);
+                }
+                if (Ph.chi) Ph.chi[i] = chi;
+                if (dtau > 0.0 && !(tau > dtau)) {
+                    // ---- pair creation at the photon position
+                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
+                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
+                    v = sample_cdf<double>(a.tab.Cp, chi, u53(r1.x, r1.y), kSpMin, kSpSpan, false,
+                                           clamped);
+                    omv = 1.0 - v;
+                    tm = -log(u53(r1.z, r1.w));
+                    tp = -log(u53(r2.x, r2.y));
+                    wg = Ph.w[i];
+                    npair = 1;
+                    decayed = true;
+                    Ph.tau[i] = -1.0;
+                } else {
+                    Ph.tau[i] = tau - dtau;
+                }
+            }
+            if (!decayed && g > 0.0) {
+                if constexpr (PREC == kFP64) {
+                    Ph.x[i] = px + dt * (gux / g);
+                    Ph.y[i] = py + dt * (guy / g);
+                    if (Ph.z) Ph.z[i] = pz + dt * (guz / g);
+                } else {
+                    const float c = (float)(dt / g);
+                    Ph.x[i] = px + (double)(c * (float)gux);
+                    Ph.y[i] = py + (double)(c * (float)guy);
+                    if (Ph.z) Ph.z[i] = pz + (double)(c * (float)guz);
+                }
+            }
+        }
+    }
+    } else {
+    if (i < n) {
+        const double taud = Ph.tau[i];
+        if (taud >= 0.0) {
+            // ---- mixed precision: FP32 physics, FP64 accumulation by
+            // integer instructions
+            const MixedConsts &m = P.mc;
+            px = Ph.x[i];
+            py = Ph.y[i];
+            pz = Ph.z ? Ph.z[i] : 0.0;
+            gux = Ph.ux[i];
+            guy = Ph.uy[i];
+            guz = Ph.uz[i];
+            const float fx = hi_d(gux), fy = hi_d(guy), fz = hi_d(guz);
+            const float g = sqrtf(fx * fx + fy * fy + fz * fz);
+            bool decayed = false;
+            if (pairs && g > 2.0f) {
+                Vec3<float> E, B;
+                eval_field_mixed<FK>(P.f, m, split_d(px), split_d(py), split_d(pz), E, B);
+                const float ig = 1.0f / g;
+                const float kx = fx * ig, ky = fy * ig, kz = fz * ig;
+                const float ax = E.x + (ky * B.z - kz * B.y);
+                const float ay = E.y + (kz * B.x - kx * B.z);
+                const float az = E.z + (kx * B.y - ky * B.x);
+                const float ke = kx * E.x + ky * E.y + kz * E.z;
+                const float s2 = ax * ax + ay * ay + az * az - ke * ke;
+                const float chi = s2 > 0.0f ? over_aS(g * sqrtf(s2), m.inv_aS, m.inv_aS_lo) : 0.0f;
+                const float Tr = rate32<2>(sm.T, chi, clamped);
+                const float dtau = m.C_rate * Tr / g * m.dt;
+                if (Ph.chi) Ph.chi[i] = f_to_d(chi);
+                const df2 TAU = split_d(taud);
+                if (dtau > 0.0f && !(TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f))) {
+                    // ---- pair creation at the photon position
+                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
+                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
+                    const FracPair vf = sample_cdf_f(
+                        a.tab.Cp2, a.tab.Qp2, a.tab.Ep, chi, u53_pair(r1.x, r1.y),
+                        u53_pair_complement(r1.x, r1.y), (float)(kSpSpan / (kNNode - 1)), false,
+                        clamped);
+                    v = f_to_d(vf.x);
+                    omv = f_to_d(vf.omx);
+                    tm = f_to_d(-logf(u53f(r1.z, r1.w)));
+                    tp = f_to_d(-logf(u53f(r2.x, r2.y)));
+                    wg = Ph.w[i];
+                    npair = 1;
+                    decayed = true;
+                    Ph.tau[i] = -1.0;
+                } else if (dtau != 0.0f) {
+                    Ph.tau[i] = add_fd(taud, -dtau);
+                }
+            }
+            if (!decayed && g > 0.0f) {
+                const float c = m.dt / g;
+                Ph.x[i] = add_fd(px, c * fx);
+                Ph.y[i] = add_fd(py, c * fy);
+                if (Ph.z) Ph.z[i] = add_fd(pz, c * fz);
+            }
+        }
+    }
+    }
+    if (npair && Ph.nemit) Ph.nemit[i] += 1;
+    warp_count(&bs.c[2][cClamp], clamped);
+    warp_count(&bs.c[2][cPair], npair != 0);
+    *tile_total_out = 0;
+    if (!pairs) return;
+
+    int tile_total;
+    const int local = block_scan(npair, s_warp, &tile_total);
+    if (tid < 32) {
+        const long long e =
+            chain_prefix(P.pho_words, chain_tile, tile_total, epoch, a.spin_limit, a.status);
+        if (tid == 0) *s_excl = e;
+    }
+    __syncthreads();
+    const long long excl = *s_excl;
+    *tile_total_out = tile_total;
+    if (npair) {
+        const int64_t ord = excl + local;
+        if (leptons && ord < room) {
+            const int64_t se = be + ord, spo = bp + ord;
+            const double om = omv;
+            El.x[se] = px;
+            El.y[se] = py;
+            if (El.z) El.z[se] = pz;
+            El.ux[se] = v * gux;
+            El.uy[se] = v * guy;
+            El.uz[se] = v * guz;
+            El.tau[se] = tm;
+            El.w[se] = wg;
+            if (El.chi) El.chi[se] = 0.0;
+            if (El.nemit) El.nemit[se] = 0;
+            Po.x[spo] = px;
+            Po.y[spo] = py;
+            if (Po.z) Po.z[spo] = pz;
+            Po.ux[spo] = om * gux;
+            Po.uy[spo] = om * guy;
+            Po.uz[spo] = om * guz;
+            Po.tau[spo] = tp;
+            Po.w[spo] = wg;
+            if (Po.chi) Po.chi[spo] = 0.0;
+            if (Po.nemit) Po.nemit[spo] = 0;
+        } else {
+            atomicAdd(&bs.c[2][cPairDrop], 1ull);
+            atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
+        }
+    }
+}
+
+// -------------------------------------------------------------------- the step
+
+// Tile counts of one problem for this launch.  Live counts and step counters
+// change only at the end of a launch (last block), so every block sees the
+// same values.  Counts outside [0, capacity] are clamped (and reported).
+struct ProbCounts {
+    long long n[3];
+    long long tiles_e, tiles_l, tiles_g;
+    bool active, bad;
+};
+
+__device__ __forceinline__ ProbCounts problem_counts(const Problem &P)
+{
+    ProbCounts c{};
+    c.active = !P.device_step || *((volatile long long *)P.left_ctr) > 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        long long v = (c.active && P.sp[s].present) ? *((volatile long long *)P.sp[s].n_live) : 0;
+        if (v < 0 || v > P.sp[s].cap) {
+            c.bad = true;
+            v = v < 0 ? 0 : P.sp[s].cap;
+        }
+        c.n[s] = v;
+    }
+    c.tiles_e = (c.n[0] + kTile - 1) / kTile;
+    c.tiles_l = c.tiles_e + (c.n[1] + kTile - 1) / kTile;
+    c.tiles_g = (c.n[2] + kTile - 1) / kTile;
+    return c;
+}
+
+// FP32 / double-float time constants of the mixed path at time t (the same
+// IEEE operations as a host-side split, so both give identical values).
+__device__ __forceinline__ void set_time(Problem &P, long long step)
+{
+    P.step = (uint64_t)step;
+    P.t = (double)step * P.dt;
+    const double tr = P.t - P.f.t_focus;
+    P.mc.t_hi = __double2float_rn(P.t);
+    P.mc.t_lo = __double2float_rn(P.t - (double)P.mc.t_hi);
+    P.mc.tr_hi = __double2float_rn(tr);
+    P.mc.tr_lo = __double2float_rn(tr - (double)P.mc.tr_hi);
+}
+
+// Block-wide inclusive scan of v[0..n) in place (n <= 2 kTile).
+__device__ void scan_offsets(long long *v, int n, long long *s_tmp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long a = 2 * tid < n ? v[2 * tid] : 0, b = 2 * tid + 1 < n ? v[2 * tid + 1] : 0;
+    long long inc = a + b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_tmp[warp] = inc;
+    __syncthreads();
+    long long before = 0;
+    for (int w = 0; w < warp; ++w) before += s_tmp[w];
+    const long long excl = before + inc - (a + b);
+    __syncthreads();
+    if (2 * tid < n) v[2 * tid] = excl + a;
+    if (2 * tid + 1 < n) v[2 * tid + 1] = excl + a + b;
+    __syncthreads();
+}
+
+// One launch = one step of every active problem.  Persistent blocks take
+// 128-particle tiles from an atomic ticket (the next ticket is fetched while
+// the current tile runs when more tiles than blocks remain); tickets enumerate, problem after problem, its
+// electron tiles, positron tiles and photon tiles, so within each problem's
+// chains start order is tile order and the decoupled look-back only ever
+// waits on tiles that are running.  BATCH = false: the single problem of the
+// launch parameters (read in place, from the constant bank); BATCH = true: a
+// device table of problems, each copied to shared memory for its tiles, with
+// time and step counters advanced on the device.
+// FP64: 4 blocks of 128 per SM (128 registers, no spills); mixed: 8 blocks
+// (64 registers; the few spills cost less than the extra resident warps gain)
+template <int PREC, int FK, bool BATCH>
+__global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
+    k_step(const __grid_constant__ StepArgs a)
+{
+    using R = typename std::conditional<PREC == kFP64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
+    __shared__ __align__(8) unsigned long long s_bar[2];   // TMA: lepton, photon tables
+    __shared__ int s_warp[kWarps];
+    __shared__ unsigned s_ticket[2];
+    __shared__ long long s_excl;
+    __shared__ long long s_tmp[kWarps];
+    __shared__ BlockStats bs;
+    __shared__ __align__(16) Problem s_prob;        // batch: the problem of the current tile
+    __shared__ long long s_off[kMaxProblems + 1];   // tickets of problems 0..b
+    __shared__ int s_tl[kMaxProblems], s_tg[kMaxProblems];
+    __shared__ ProbCounts s_pc;
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x;
+    const int np = BATCH ? a.n_problems : 1;
+    const Problem *table = BATCH ? a.problems : &a.single;
+    const unsigned epoch = *((volatile unsigned *)&a.ctl->epoch);
+    clear_stats(bs);
+
+    // tiles of every problem, and the ticket offset of each
+    bool bad = false;
+    for (int b = tid; b < np; b += kTile) {
+        const ProbCounts c = problem_counts(table[b]);
+        s_off[b] = c.tiles_l + c.tiles_g;
+        s_tl[b] = (int)c.tiles_l;
+        s_tg[b] = (int)c.tiles_g;
+        bad |= c.bad;
+        if (!BATCH) s_pc = c;
+    }
+    if (bad && blockIdx.x == 0) raise_status(a.status, QP_ERR_INVALID_ARG);
+    __syncthreads();
+    if (BATCH) scan_offsets(s_off, np, s_tmp);  // s_off[b] = tickets of problems 0..b
+    const long long n_tickets = s_off[np - 1];
+
+    bool lep_loaded = false, ph_loaded = false;
+    int cur = BATCH ? -1 : 0;
+    if ((long long)blockIdx.x < n_tickets) {
+        if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
+        __syncthreads();
+        for (int buf = 0;; buf ^= 1) {
+            const long long t = s_ticket[buf];
+            if (t >= n_tickets) break;
+            // fetch the next ticket while this tile runs, when another tile is
+            // likely left for this block (else the atomic only adds contention)
+            const bool early = t + (long long)gridDim.x < n_tickets;
+            if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+            int b = 0;
+            if (BATCH) {
+                // the problem of ticket t: the first b with s_off[b] > t
+                int lo = 0, hi = np - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[mid] > t)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                b = lo;
+                if (b != cur) {
+                    if (cur >= 0) {
+                        flush_stats(bs, a, s_prob);
+                        __syncthreads();
+                        clear_stats(bs);
+                    }
+                    // copy the problem descriptor to shared memory
+                    const int *src = reinterpret_cast<const int *>(table + b);
+                    int *dst = reinterpret_cast<int *>(&s_prob);
+                    for (int k = tid; k < (int)(sizeof(Problem) / sizeof(int)); k += kTile)
+                        dst[k] = src[k];
+                    __syncthreads();
+                    if (tid == 0) {
+                        s_pc = problem_counts(s_prob);
+                        set_time(s_prob, *((volatile long long *)s_prob.step_ctr));
+                    }
+                    __syncthreads();
+                    cur = b;
+                }
+            }
+            const Problem &P = BATCH ? s_prob : a.single;
+            const ProbCounts pc = s_pc;                         // in registers for the tile
+            const long long lt = t - (b > 0 ? s_off[b - 1] : 0);  // tile within the problem
+            if (lt < pc.tiles_l) {
+                const int sp = lt < pc.tiles_e ? 0 : 1;
+                const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
+                lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp, first,
+                                         pc.n[sp], pc.n[2], epoch, s_warp, &s_excl, bs);
+                if (lt == pc.tiles_l - 1 && tid == 0) {
+                    // last lepton tile: the new photon count, applied at the end
+                    const int64_t tot = pc.n[2] + s_excl + s_warp[kWarps - 1];
+                    if (P.sp[2].present) {
+                        P.pending[2] = tot < P.sp[2].cap ? tot : P.sp[2].cap;
+                        if (tot > P.sp[2].cap) raise_status(a.status, QP_WARN_BUFFER_FULL);
+                    } else if (tot > pc.n[2]) {
+                        raise_status(a.status, QP_WARN_BUFFER_FULL);
+                    }
+                }
+            } else {
+                const unsigned pt = (unsigned)(lt - pc.tiles_l);
+                const long long be = pc.n[0], bp = pc.n[1];
+                long long room = 0;
+                if (P.sp[0].present && P.sp[1].present) {
+                    room = P.sp[0].cap - be;
+                    if (P.sp[1].cap - bp < room) room = P.sp[1].cap - bp;
+                    if (room < 0) room = 0;
+                }
+                int tile_total = 0;
+                photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], be, bp,
+                                         room, epoch, s_warp, &s_excl, bs, &tile_total);
+                if ((long long)pt == pc.tiles_g - 1 && tid == 0 && P.pairs) {
+                    // last photon tile: the new lepton counts, applied at the end
+                    const int64_t tot = s_excl + tile_total;
+                    const int64_t add = tot < room ? tot : room;
+                    P.pending[0] = be + add;
+                    P.pending[1] = bp + add;
+                    if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
+                }
+            }
+            if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+            __syncthreads();
+        }
+    }
+    if (cur >= 0) flush_stats(bs, a, BATCH ? s_prob : a.single);
+
+    // ---- the last block to finish publishes the step of every problem
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.ctl->done, 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int b = tid; b < np; b += kTile) {
+            const Problem &Q = table[b];
+            if (Q.device_step && *((volatile long long *)Q.left_ctr) <= 0) continue;
+            if (Q.device_step) {
+                // slots this launch stepped (before the new counts are applied)
+                const ProbCounts c = problem_counts(Q);
+                *Q.work_ctr += c.n[0] + c.n[1] + c.n[2];
+            }
+            volatile long long *pend = Q.pending;
+            if (s_tl[b] > 0 && Q.sp[2].present) *Q.sp[2].n_live = pend[2];
+            if (s_tg[b] > 0 && Q.pairs && Q.sp[0].present && Q.sp[1].present) {
+                *Q.sp[0].n_live = pend[0];
+                *Q.sp[1].n_live = pend[1];
+            }
+            if (Q.device_step) {
+                *Q.step_ctr += 1;
+                *Q.left_ctr -= 1;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            *((volatile unsigned *)&a.ctl->ticket) = 0u;
+            *((volatile unsigned *)&a.ctl->done) = 0u;
+            *((volatile unsigned *)&a.ctl->epoch) = epoch + 1u;
+            __threadfence();
+        }
+    }
+}
+
+template <int PREC, bool BATCH>
+const void *step_kernel_of(int fk)
+{
+    switch (fk) {
+    case QP_FIELD_NONE: return (const void *)k_step<PREC, QP_FIELD_NONE, BATCH>;
+    case QP_FIELD_PLANE: return (const void *)k_step<PREC, QP_FIELD_PLANE, BATCH>;
+    case QP_FIELD_GAUSSIAN: return (const void *)k_step<PREC, QP_FIELD_GAUSSIAN, BATCH>;
+    case QP_FIELD_YEE2D: return (const void *)k_step<PREC, QP_FIELD_YEE2D, BATCH>;
+    case QP_FIELD_UNIFORM_B: return (const void *)k_step<PREC, QP_FIELD_UNIFORM_B, BATCH>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+}  // namespace qp

@@ -1,0 +1,13 @@
+// Instantiations of the step kernel, FP64 path (see qp_step.cuh).
+#include "qp_step.cuh"
+
+namespace qp {
+
+const void *step_kernel_fp64(int field_kind, bool batch)
+{
+    return batch ? step_kernel_of<kFP64, true>(field_kind) : step_kernel_of<kFP64, false>(field_kind);
+}
+
+size_t step_smem_fp64() { return sizeof(Smem<double>); }
+
+}  // namespace qp

@@ -1,0 +1,13 @@
+// Instantiations of the step kernel, mixed-precision path (see qp_step.cuh).
+#include "qp_step.cuh"
+
+namespace qp {
+
+const void *step_kernel_mixed(int field_kind, bool batch)
+{
+    return batch ? step_kernel_of<kMixed, true>(field_kind) : step_kernel_of<kMixed, false>(field_kind);
+}
+
+size_t step_smem_mixed() { return sizeof(Smem<float>); }
+
+}  // namespace qp

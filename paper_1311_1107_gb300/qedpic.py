@@ -26,6 +26,7 @@ QP_ELECTRON, QP_POSITRON, QP_PHOTON = 0, 1, 2
 QP_FP64, QP_MIXED = 0, 1
 QP_FIELD_NONE, QP_FIELD_PLANE, QP_FIELD_GAUSSIAN, QP_FIELD_YEE2D, QP_FIELD_UNIFORM_B = range(5)
 QP_MAX_EMISSIONS = 8
+QP_MAX_BATCH = 64
 QP_HIST_BINS = 64
 QP_NRATE, QP_NCDF, QP_NNODE = 769, 97, 256
 
@@ -44,7 +45,7 @@ class qp_species_desc(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
                 ("tau", C.c_void_p), ("w", C.c_void_p), ("chi", C.c_void_p),
-                ("nemit", C.c_void_p), ("n_live", C.c_void_p)]
+                ("nemit", C.c_void_p), ("n_live", C.c_void_p), ("id_base", C.c_int64)]
 
 
 class qp_field(C.Structure):
@@ -98,7 +99,9 @@ _lib = None
 EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
            "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
            "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
-           "qp_diagnostics_noalloc", "qp_status_string")
+           "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
+           "qp_batch_create", "qp_batch_destroy", "qp_batch_scratch_words", "qp_batch_set",
+           "qp_batch_clear", "qp_batch_step", "qp_batch_progress")
 
 
 def library_path() -> str:
@@ -131,6 +134,14 @@ def lib(build_if_missing: bool = False):
         L.qp_selftest_wait_timeout.argtypes = [vp, C.c_uint32]
         L.qp_profile_enable.argtypes = [vp, C.c_int]
         L.qp_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.qp_destroy_species.argtypes = [vp, i32]
+        L.qp_batch_create.argtypes = [vp, i32, i32, i32, C.POINTER(vp)]
+        L.qp_batch_destroy.argtypes = [vp]
+        L.qp_batch_scratch_words.argtypes = [vp, C.POINTER(qp_step_params), C.POINTER(i64)]
+        L.qp_batch_set.argtypes = [vp, i32, C.POINTER(qp_step_params), vp, i64, vp]
+        L.qp_batch_clear.argtypes = [vp, i32, vp]
+        L.qp_batch_step.argtypes = [vp, i32, vp]
+        L.qp_batch_progress.argtypes = [vp, vp, vp, vp, vp]
         L.qp_status_string.argtypes = [C.c_int]
         L.qp_status_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -226,3 +237,52 @@ def qp_profile_read(ctx):
 
 def qp_status_string(status: int) -> str:
     return status_name(status)
+
+
+def qp_destroy_species(ctx, handle: int) -> int:
+    return _check("qp_destroy_species", lib().qp_destroy_species(ctx, int(handle)))
+
+
+# ---------------------------------------------------------------- batches
+
+def qp_batch_create(ctx, max_problems: int, precision: int, field_kind: int) -> C.c_void_p:
+    b = C.c_void_p()
+    _check("qp_batch_create", lib().qp_batch_create(ctx, int(max_problems), int(precision),
+                                                    int(field_kind), C.byref(b)))
+    return b
+
+
+def qp_batch_destroy(batch) -> int:
+    return _check("qp_batch_destroy", lib().qp_batch_destroy(batch))
+
+
+def qp_batch_scratch_words(ctx, params: qp_step_params) -> int:
+    w = C.c_int64(0)
+    _check("qp_batch_scratch_words", lib().qp_batch_scratch_words(ctx, C.byref(params),
+                                                                  C.byref(w)))
+    return w.value
+
+
+def qp_batch_set(batch, slot: int, params: qp_step_params, scratch_ptr: int, scratch_words: int,
+                 stream=None) -> int:
+    return _check("qp_batch_set", lib().qp_batch_set(batch, int(slot), C.byref(params),
+                                                     C.c_void_p(scratch_ptr),
+                                                     int(scratch_words), stream))
+
+
+def qp_batch_clear(batch, slot: int, stream=None) -> int:
+    return _check("qp_batch_clear", lib().qp_batch_clear(batch, int(slot), stream))
+
+
+def qp_batch_step(batch, n_launches: int, stream=None) -> int:
+    return _check("qp_batch_step", lib().qp_batch_step(batch, int(n_launches), stream))
+
+
+def qp_batch_progress(batch, steps_left_ptr: int, next_step_ptr: int | None = None,
+                      work_ptr: int | None = None, stream=None) -> int:
+    """Enqueue copies of the slots' remaining launches (and next steps, and
+    live slots stepped) into host memory at the given addresses (pinned,
+    max_problems int64 each)."""
+    opt = lambda p: None if p is None else C.c_void_p(p)
+    return _check("qp_batch_progress", lib().qp_batch_progress(
+        batch, C.c_void_p(steps_left_ptr), opt(next_step_ptr), opt(work_ptr), stream))

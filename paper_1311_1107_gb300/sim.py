@@ -33,7 +33,7 @@ class DeviceSpecies:
     """FP64 SoA buffers of one species on the GPU, registered with a context."""
 
     def __init__(self, ctx, kind: int, capacity: int, dims: int = 3, device="cuda:0",
-                 track_chi: bool = True):
+                 track_chi: bool = True, id_base: int = 0):
         self.kind, self.cap, self.dims = kind, int(capacity), dims
         n = max(self.cap, 1)
         self.t = {nm: torch.zeros(n, dtype=torch.float64, device=device)
@@ -48,6 +48,7 @@ class DeviceSpecies:
         d.chi = _ptr(self.chi)
         d.nemit = _ptr(self.nemit)
         d.n_live = _ptr(self.n_live)
+        d.id_base = int(id_base)
         self._desc = d
         self.handle = Q.qp_create_species(ctx, d)
 
@@ -104,7 +105,10 @@ class Simulation:
     """One run: a context, three species and the step parameters."""
 
     def __init__(self, workload: dict, precision: str = "fp64", device: int = 0, ctx=None,
-                 track_chi: bool = True, init_tau: bool = True, load: bool = True):
+                 track_chi: bool = True, init_tau: bool = True, load: bool = True,
+                 id_base: int = 0):
+        """id_base: particle id of the first electron slot (a shard of a larger
+        population keeps its particles' random streams)."""
         self.dev = f"cuda:{device}"
         self.own_ctx = ctx is None
         self.ctx = ctx if ctx is not None else Q.qp_init_tables(LAMBDA_M, device)
@@ -112,7 +116,8 @@ class Simulation:
         dims = workload["dims"]
         cap = workload["capacity"]
         self.species = {
-            name: DeviceSpecies(self.ctx, KIND[name], cap[name], dims, self.dev, track_chi)
+            name: DeviceSpecies(self.ctx, KIND[name], cap[name], dims, self.dev, track_chi,
+                                id_base if name == "electron" else 0)
             for name in ("electron", "positron", "photon")
         }
         self.field, self._keep = make_field(workload["field"], self.dev)

@@ -93,6 +93,15 @@ def test_arguments_rejected_before_any_device_work(lib):
     assert lib.qp_create_species(None, C.byref(desc), C.byref(h)) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_selftest_wait_timeout(None, 10) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_destroy(None) == Q.QP_OK
+    assert lib.qp_destroy_species(None, 0) == Q.QP_ERR_NOT_INITIALIZED
+    b = C.c_void_p()
+    assert lib.qp_batch_create(None, 4, Q.QP_MIXED, Q.QP_FIELD_GAUSSIAN,
+                               C.byref(b)) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_batch_set(None, 0, C.byref(s), None, 0, None) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_batch_step(None, 1, None) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_batch_clear(None, 0, None) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_batch_progress(None, None, None, None, None) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_batch_destroy(None) == Q.QP_ERR_NOT_INITIALIZED
 
 
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
