@@ -49,6 +49,7 @@ struct qp_ctx {
     // tables: FP64 H Gs Ts Cg Cp, then FP32 copies in the same order
     double *d_tab64 = nullptr;
     float *d_tab32 = nullptr;
+    unsigned char *d_guide = nullptr; // guide tables of the CDF rows (emission, pair)
     qp::DevStats *d_stats = nullptr;  // [kMaxSpecies]
     qp::StepCtl *d_ctl = nullptr;     // ticket, done, epoch of qp_step launches
     long long *d_pending = nullptr;   // [3] new live counts of a qp_step launch
@@ -75,6 +76,31 @@ constexpr size_t kTabWords = kTabRate + kTabCdf;
 // pairs (4 kTabCdf floats), then e^(-s_j) at the 2 x kNNode logit nodes
 constexpr size_t kTab32 = kTabRate + 4 * kTabCdf + 2 * (size_t)qp::kNNode;
 
+constexpr size_t kGuideHalf = (size_t)qp::kNCdf * qp::kGuideBuckets;
+
+// Guide tables of one CDF table (kNCdf rows of kNNode nodes): [half][row][bucket].
+// Lower half, bucket m of xi in (0, 1/2]: the last node j <= 254 with C_j
+// below the bucket's lower edge; upper half, bucket m of eta = 1 - xi: the
+// last node with 1 - C_j above the bucket's upper edge (0 if none).  The
+// margins keep every entry at or before the node a search would find.
+void build_guides(const double *rows, unsigned char *g)
+{
+    for (int r = 0; r < qp::kNCdf; ++r) {
+        const double *C = rows + (size_t)r * qp::kNNode;
+        for (int m = 0; m < qp::kGuideBuckets; ++m) {
+            const int e = -1 - (m >> 2), k = m & 3;
+            const double lo_edge = ldexp(1.0 + k / 4.0, e), hi_edge = ldexp(1.0 + (k + 1) / 4.0, e);
+            int gl = 0, gu = 0;
+            for (int j = 0; j < qp::kNNode - 1; ++j) {
+                if (C[j] < lo_edge * (1.0 - 1e-9)) gl = j;
+                if (1.0 - C[j] > hi_edge * (1.0 + 1e-9)) gu = j;
+            }
+            g[(size_t)r * qp::kGuideBuckets + m] = (unsigned char)gl;
+            g[kGuideHalf + (size_t)r * qp::kGuideBuckets + m] = (unsigned char)gu;
+        }
+    }
+}
+
 int cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return QP_OK;
@@ -91,6 +117,7 @@ void release(qp_ctx *c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->d_tab64);
     cudaFree(c->d_tab32);
+    cudaFree(c->d_guide);
     cudaFree(c->d_stats);
     cudaFree(c->d_ctl);
     cudaFree(c->d_pending);
@@ -270,6 +297,11 @@ int qp_init_tables(const qp_table_params *p, qp_ctx **out_ctx)
             return cuda_status(e);   \
         }                            \
     } while (0)
+    std::vector<unsigned char> guide(4 * kGuideHalf);
+    build_guides(T->Cg, guide.data());
+    build_guides(T->Cp, guide.data() + 2 * kGuideHalf);
+    QP_TRY(cudaMalloc(&c->d_guide, guide.size()));
+    QP_TRY(cudaMemcpy(c->d_guide, guide.data(), guide.size(), cudaMemcpyHostToDevice));
     QP_TRY(cudaMalloc(&c->d_tab64, kTabWords * sizeof(double)));
     QP_TRY(cudaMalloc(&c->d_tab32, kTab32 * sizeof(float)));
     QP_TRY(cudaMemcpy(c->d_tab64, h64.data(), kTabWords * sizeof(double), cudaMemcpyHostToDevice));
@@ -468,6 +500,8 @@ void fill_globals(const qp_ctx *ctx, qp::StepArgs &a)
     a.tab.Qp2 = c2 + 3 * CC;
     a.tab.Eg = ctx->d_tab32 + kTabRate + 4 * kTabCdf;
     a.tab.Ep = a.tab.Eg + qp::kNNode;
+    a.tab.Gg = ctx->d_guide;
+    a.tab.Gp = ctx->d_guide + 2 * kGuideHalf;
     a.stats = ctx->d_stats;
     a.status = ctx->d_status;
     a.a_S = ctx->U.a_S;

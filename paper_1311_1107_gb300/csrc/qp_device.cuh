@@ -48,6 +48,8 @@ struct TablesDev {
     // CDF rows C and their complements Q = 1 - C as hi + lo float pairs
     const float2 *Cg2, *Cp2, *Qg2, *Qp2;
     const float *Eg, *Ep;                      // e^(-s_j) at the logit nodes
+    // guide tables of the CDF rows (see guide_bucket): [half][row][bucket]
+    const unsigned char *Gg, *Gp;
 };
 
 // Step constants of the mixed path as FP32 values or double-float pairs
@@ -265,6 +267,9 @@ __device__ __forceinline__ void yee_gather(const FieldDev &f, const int ix[2], c
                                            const R wx[2], const R wy[2], Vec3<R> &E, Vec3<R> &B)
 {
     const int nx = (int)f.nx, ny = (int)f.ny;
+    // one check for all four stencils (their nodes span min(ix)..max(ix)+1)
+    const bool all_inside = min(ix[0], ix[1]) >= 0 && min(iy[0], iy[1]) >= 0 &&
+                            max(ix[0], ix[1]) + 1 < nx && max(iy[0], iy[1]) + 1 < ny;
     YeeStencil<R> st[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -273,7 +278,8 @@ __device__ __forceinline__ void yee_gather(const FieldDev &f, const int ix[2], c
         st[k].iy = iy[hy];
         st[k].wx = wx[hx];
         st[k].wy = wy[hy];
-        st[k].inside = ix[hx] >= 0 && iy[hy] >= 0 && ix[hx] + 1 < nx && iy[hy] + 1 < ny;
+        st[k].inside = all_inside || (ix[hx] >= 0 && iy[hy] >= 0 && ix[hx] + 1 < nx &&
+                                      iy[hy] + 1 < ny);
         st[k].base = iy[hy] * nx + ix[hx];
     }
     E.x = yee_interp<R>(f.yee[0], st[1], nx, ny);
@@ -449,11 +455,39 @@ __device__ __forceinline__ float rate32(const float *V, float chi, bool &clamped
 
 // ------------------------------------------------------------------ inverse CDF (Eq. 7)
 
+// Guide tables: the search of a CDF row for xi starts from a node read from
+// a small table instead of bisecting the row (8 dependent loads on the rare
+// emission branch, which every later tile of the launch waits for through
+// the look-back).  xi <= 1/2 is located in the row by xi itself, xi > 1/2 by
+// eta = 1 - xi; the bucket of a value in (0, 1/2] is four per octave, from
+// its exponent and two leading mantissa bits.  Lower-half entry: the last
+// node with C < the bucket's lower edge; upper-half entry: the last node
+// with 1 - C > the bucket's upper edge.  A forward scan then finds the same
+// interval as a bisection would (the last node below xi).
+constexpr int kGuideBuckets = 224;
+
+__device__ __forceinline__ int guide_bucket(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    const int m = ((-1 - e) << 2) | (int)((b >> 50) & 3u);
+    return min(max(m, 0), kGuideBuckets - 1);
+}
+
+__device__ __forceinline__ int guide_bucket(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFF) - 127;
+    const int m = ((-1 - e) << 2) | (int)((b >> 21) & 3u);
+    return min(max(m, 0), kGuideBuckets - 1);
+}
+
 // Invert one CDF row C (kNNode logit nodes s_i = smin + span i / 255) at xi.
 // Emission rows follow u^(1/3) below the first node; pair rows clamp.
 template <typename R>
-__device__ __forceinline__ R row_invert(const R *__restrict__ C, R xi, double smin, double span,
-                                        bool power_tail)
+__device__ __forceinline__ R row_invert(const R *__restrict__ C,
+                                        const unsigned char *__restrict__ guide, R xi,
+                                        double smin, double span, bool power_tail)
 {
     const R c0 = __ldg(C);
     if (xi <= c0) {
@@ -466,15 +500,11 @@ __device__ __forceinline__ R row_invert(const R *__restrict__ C, R xi, double sm
     }
     const R clast = __ldg(C + kNNode - 1);
     if (xi >= clast) return R(1) / (R(1) + (R)exp(-(smin + span)));
-    int lo = 0, hi = kNNode - 1;
+    // the last node below xi: guide entry, then a forward scan
+    int lo = xi <= R(0.5) ? (int)__ldg(guide + guide_bucket(xi))
+                          : (int)__ldg(guide + kNCdf * kGuideBuckets + guide_bucket(R(1) - xi));
 #pragma unroll 1
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(C + mid) < xi)
-            lo = mid;
-        else
-            hi = mid;
-    }
+    while (lo < kNNode - 2 && __ldg(C + lo + 1) < xi) ++lo;
     const R clo = __ldg(C + lo), chi_ = __ldg(C + lo + 1);
     const double s_lo = smin + span * lo / (kNNode - 1);
     const double s_hi = smin + span * (lo + 1) / (kNNode - 1);
@@ -492,16 +522,18 @@ __device__ __forceinline__ R row_invert(const R *__restrict__ C, R xi, double sm
 // Photon fraction u = chi_gamma / chi_e for chi_e (rows j, j+1 interpolated
 // linearly in chi; below the grid the classical scaling u ~ chi).
 template <typename R>
-__device__ __forceinline__ R sample_cdf(const R *__restrict__ rows, R chi, R xi, double smin,
-                                        double span, bool emission, bool &clamped)
+__device__ __forceinline__ R sample_cdf(const R *__restrict__ rows,
+                                        const unsigned char *__restrict__ guide, R chi, R xi,
+                                        double smin, double span, bool emission, bool &clamped)
 {
     if (!(chi >= (R)kChiLo)) {
-        const R r0 = row_invert<R>(rows, xi, smin, span, emission);
+        const R r0 = row_invert<R>(rows, guide, xi, smin, span, emission);
         return emission ? (chi / (R)kChiLo) * r0 : r0;
     }
     if (chi >= (R)kChiHi) {
         clamped = true;
-        return row_invert<R>(rows + (kNCdf - 1) * kNNode, xi, smin, span, emission);
+        return row_invert<R>(rows + (kNCdf - 1) * kNNode, guide + (kNCdf - 1) * kGuideBuckets,
+                             xi, smin, span, emission);
     }
     R f;
     int j;
@@ -509,8 +541,10 @@ __device__ __forceinline__ R sample_cdf(const R *__restrict__ rows, R chi, R xi,
         j = grid_index64<2>(chi, f);
     else
         j = grid_index32<2>(chi, f);
-    const R ra = row_invert<R>(rows + j * kNNode, xi, smin, span, emission);
-    const R rb = row_invert<R>(rows + (j + 1) * kNNode, xi, smin, span, emission);
+    const R ra = row_invert<R>(rows + j * kNNode, guide + j * kGuideBuckets, xi, smin, span,
+                               emission);
+    const R rb = row_invert<R>(rows + (j + 1) * kNNode, guide + (j + 1) * kGuideBuckets, xi,
+                               smin, span, emission);
     return ra + f * (rb - ra);
 }
 

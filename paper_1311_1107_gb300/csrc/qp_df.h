@@ -295,7 +295,9 @@ QP_HD double merge_df(df2 a)
 // and large cancellations take an FP64 path.
 QP_HD double add_fd_wide(double d, float f);
 
-QP_HD double add_fd(double d, float f)
+// The general integer sum (the result may leave d's binade: renormalised,
+// rounded once); large cancellations take the double-float route.
+QP_HD double add_fd_renorm(double d, float f)
 {
     const uint32_t fb = f2u(f);
     if ((fb & 0x7FFFFFFFu) == 0u) return d;
@@ -323,6 +325,26 @@ QP_HD double add_fd(double d, float f)
         e -= 1;
     }
     return u2d((db & 0x8000000000000000ull) | (e << 52) | ((uint64_t)S & ((1ull << 52) - 1)));
+}
+
+QP_HD double add_fd(double d, float f)
+{
+    const uint32_t fb = f2u(f);
+    if ((fb & 0x7FFFFFFFu) == 0u) return d;
+    const uint64_t db = d2u(d);
+    const uint32_t ed = (uint32_t)(db >> 52) & 0x7FFu, ef = (fb >> 23) & 0xFFu;
+    // f in units of d's last place: mf * 2^k, k = ef - ed + 925
+    const int k = (int)ef - (int)ed + 925;
+    if (k < -25 && ed != 0u && ed != 0x7FFu && ef != 0xFFu) return d;  // below half a unit
+    if (ed == 0u || ed == 0x7FFu || ef == 0u || ef == 0xFFu || k > 27) return add_fd_wide(d, f);
+    const uint32_t mf = (1u << 23) | (fb & 0x7FFFFFu);
+    // the increment rounded to d's last place (half-way cases away from zero)
+    const uint64_t L = k >= 0 ? ((uint64_t)mf << k) : (uint64_t)((mf + (1u << (-k - 1))) >> (-k));
+    // added to (or taken from) the magnitude bits directly: exact while the
+    // exponent field stays the same, which the check below confirms
+    const uint64_t r = ((uint32_t)(db >> 63) == (fb >> 31)) ? db + L : db - L;
+    if (((uint32_t)(r >> 52) & 0x7FFu) != ed) return add_fd_renorm(d, f);  // binade crossed
+    return u2d(r);
 }
 
 // The cases add_fd does not handle in integers (zero or tiny d, increments

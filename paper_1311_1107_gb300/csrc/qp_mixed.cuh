@@ -182,6 +182,7 @@ __device__ __forceinline__ float2 ldg2(const float2 *p) { return __ldg(p); }
 // even where neighbouring nodes differ by 1e-3 or less.
 __device__ __forceinline__ FracPair row_invert_f(const float2 *__restrict__ C,
                                                  const float2 *__restrict__ Q,
+                                                 const unsigned char *__restrict__ guide,
                                                  const float *__restrict__ En, df2 xi, df2 eta,
                                                  float ds, bool power_tail)
 {
@@ -197,31 +198,20 @@ __device__ __forceinline__ FracPair row_invert_f(const float2 *__restrict__ C,
             }
             return p0;
         }
-        int lo = 0, hi = kNNode - 1;
+        // the last node below xi: guide entry, then a forward scan
+        int lo = (int)__ldg(guide + guide_bucket(xi.hi));
 #pragma unroll 1
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (pair_diff(xi, ldg2(C + mid)) > 0.0f)
-                lo = mid;
-            else
-                hi = mid;
-        }
+        while (lo < kNNode - 2 && pair_diff(xi, ldg2(C + lo + 1)) > 0.0f) ++lo;
         const float2 c_lo = ldg2(C + lo), c_hi = ldg2(C + lo + 1);
         const float den = (c_hi.x - c_lo.x) + (c_hi.y - c_lo.y);
         const float t = den > 0.0f ? fminf(pair_diff(xi, c_lo) / den, 1.0f) : 0.0f;
         return logit_node(En, lo, ds, t);
     }
     if (pair_diff(eta, ldg2(Q + kNNode - 1)) <= 0.0f) return logit_node(En, kNNode - 1, ds, 0.0f);
-    // Q decreases along the row: find Q[lo] > eta >= Q[lo + 1]
-    int lo = 0, hi = kNNode - 1;
+    // Q decreases along the row: the last node with Q > eta (guide, then scan)
+    int lo = (int)__ldg(guide + kNCdf * kGuideBuckets + guide_bucket(eta.hi));
 #pragma unroll 1
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (pair_diff(eta, ldg2(Q + mid)) < 0.0f)
-            lo = mid;
-        else
-            hi = mid;
-    }
+    while (lo < kNNode - 2 && pair_diff(eta, ldg2(Q + lo + 1)) < 0.0f) ++lo;
     const float2 q_lo = ldg2(Q + lo), q_hi = ldg2(Q + lo + 1);
     const float den = (q_lo.x - q_hi.x) + (q_lo.y - q_hi.y);
     const float t = den > 0.0f ? fminf(-pair_diff(eta, q_lo) / den, 1.0f) : 0.0f;
@@ -232,11 +222,12 @@ __device__ __forceinline__ FracPair row_invert_f(const float2 *__restrict__ C,
 // between the two chi rows around chi (same rule as the FP64 path).
 __device__ __forceinline__ FracPair sample_cdf_f(const float2 *__restrict__ rows,
                                                  const float2 *__restrict__ qrows,
+                                                 const unsigned char *__restrict__ guide,
                                                  const float *__restrict__ En, float chi, df2 xi,
                                                  df2 eta, float ds, bool emission, bool &clamped)
 {
     if (!(chi >= (float)kChiLo)) {
-        const FracPair r0 = row_invert_f(rows, qrows, En, xi, eta, ds, emission);
+        const FracPair r0 = row_invert_f(rows, qrows, guide, En, xi, eta, ds, emission);
         if (!emission) return r0;
         const float x = (chi / (float)kChiLo) * r0.x;
         return {x, 1.0f - x};
@@ -244,14 +235,15 @@ __device__ __forceinline__ FracPair sample_cdf_f(const float2 *__restrict__ rows
     if (chi >= (float)kChiHi) {
         clamped = true;
         const int o = (kNCdf - 1) * kNNode;
-        return row_invert_f(rows + o, qrows + o, En, xi, eta, ds, emission);
+        return row_invert_f(rows + o, qrows + o, guide + (kNCdf - 1) * kGuideBuckets, En, xi,
+                            eta, ds, emission);
     }
     float f;
     const int j = grid_index32<2>(chi, f);
-    const FracPair a = row_invert_f(rows + j * kNNode, qrows + j * kNNode, En, xi, eta, ds,
-                                    emission);
-    const FracPair b = row_invert_f(rows + (j + 1) * kNNode, qrows + (j + 1) * kNNode, En, xi,
-                                    eta, ds, emission);
+    const FracPair a = row_invert_f(rows + j * kNNode, qrows + j * kNNode,
+                                    guide + j * kGuideBuckets, En, xi, eta, ds, emission);
+    const FracPair b = row_invert_f(rows + (j + 1) * kNNode, qrows + (j + 1) * kNNode,
+                                    guide + (j + 1) * kGuideBuckets, En, xi, eta, ds, emission);
     return {a.x + f * (b.x - a.x), a.omx + f * (b.omx - a.omx)};
 }
 

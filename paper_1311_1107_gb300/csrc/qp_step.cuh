@@ -68,7 +68,7 @@ __device__ long long chain_prefix(unsigned long long *words, unsigned tile, long
     if (lane == 0) atomicExch(words + tile, make_word(epoch, kFlagAgg, aggregate));
     long long excl = 0;
     long long base = (long long)tile - 1;
-    unsigned spins = 0;
+    unsigned spins = 0, nap = 32;
     for (;;) {
         const long long idx = base - lane;
         // before tile 0 the chain is complete: read as "prefix 0"
@@ -85,7 +85,10 @@ __device__ long long chain_prefix(unsigned long long *words, unsigned tile, long
                 if (lane == 0) raise_status(status, QP_ERR_TIMEOUT);
                 break;
             }
-            __nanosleep(32);
+            // back off (32 ns doubling to 1 us): a waiting warp takes few
+            // issue slots from the warps still computing their tiles
+            __nanosleep(nap);
+            if (nap < 1024) nap <<= 1;
             continue;
         }
         long long v = lane <= first ? (long long)(w & kValMask) : 0;
@@ -339,7 +342,8 @@ __device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
                 const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
                 double ufrac;
-                ufrac = sample_cdf<double>(a.tab.Cg, chi, xi_p, kSgMin, kSgSpan, true, clamped);
+                ufrac = sample_cdf<double>(a.tab.Cg, a.tab.Gg, chi, xi_p, kSgMin, kSgSpan, true,
+                                           clamped);
                 const double pmag = sqrt(ux * ux + uy * uy + uz * uz);
                 double gg = ufrac * gam;
                 if (gg > pmag) gg = pmag;
@@ -478,7 +482,7 @@ __device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
                 const float xi = u53f(rr.z, rr.w);
                 const FracPair uf = sample_cdf_f(
-                    a.tab.Cg2, a.tab.Qg2, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
+                    a.tab.Cg2, a.tab.Qg2, a.tab.Gg, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
                     u53_pair_complement(rr.x, rr.y), (float)(kSgSpan / (kNNode - 1)), true,
                     clamped);
                 const float pmag = sqrtf(ux * ux + uy * uy + uz * uz);
@@ -679,8 +683,8 @@ __device__ void photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                     // ---- pair creation at the photon position
                     const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
                     const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
-                    v = sample_cdf<double>(a.tab.Cp, chi, u53(r1.x, r1.y), kSpMin, kSpSpan, false,
-                                           clamped);
+                    v = sample_cdf<double>(a.tab.Cp, a.tab.Gp, chi, u53(r1.x, r1.y), kSpMin,
+                                           kSpSpan, false, clamped);
                     omv = 1.0 - v;
                     tm = -log(u53(r1.z, r1.w));
                     tp = -log(u53(r2.x, r2.y));
@@ -742,7 +746,7 @@ __device__ void photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                     const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
                     const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
                     const FracPair vf = sample_cdf_f(
-                        a.tab.Cp2, a.tab.Qp2, a.tab.Ep, chi, u53_pair(r1.x, r1.y),
+                        a.tab.Cp2, a.tab.Qp2, a.tab.Gp, a.tab.Ep, chi, u53_pair(r1.x, r1.y),
                         u53_pair_complement(r1.x, r1.y), (float)(kSpSpan / (kNNode - 1)), false,
                         clamped);
                     v = f_to_d(vf.x);
@@ -828,15 +832,21 @@ struct ProbCounts {
 __device__ __forceinline__ ProbCounts problem_counts(const Problem &P)
 {
     ProbCounts c{};
-    c.active = !P.device_step || *((volatile long long *)P.left_ctr) > 0;
+    // every counter is loaded before any is tested, so the (uncached) reads
+    // overlap instead of following each other
+    long long v[3], left = 1;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) v[s] = P.sp[s].present ? __ldcg(P.sp[s].n_live) : 0;
+    if (P.device_step) left = __ldcg(P.left_ctr);
+    c.active = left > 0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        long long v = (c.active && P.sp[s].present) ? *((volatile long long *)P.sp[s].n_live) : 0;
-        if (v < 0 || v > P.sp[s].cap) {
+        long long x = c.active ? v[s] : 0;
+        if (x < 0 || x > P.sp[s].cap) {
             c.bad = true;
-            v = v < 0 ? 0 : P.sp[s].cap;
+            x = x < 0 ? 0 : P.sp[s].cap;
         }
-        c.n[s] = v;
+        c.n[s] = x;
     }
     c.tiles_e = (c.n[0] + kTile - 1) / kTile;
     c.tiles_l = c.tiles_e + (c.n[1] + kTile - 1) / kTile;
@@ -910,9 +920,13 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     __shared__ int s_last;
 
     const int tid = threadIdx.x;
+    // the first ticket is taken at entry: its atomic overlaps the reads of
+    // the live counts below (a block whose ticket is past the last tile
+    // leaves without work)
+    if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
     const int np = BATCH ? a.n_problems : 1;
     const Problem *table = BATCH ? a.problems : &a.single;
-    const unsigned epoch = *((volatile unsigned *)&a.ctl->epoch);
+    const unsigned epoch = __ldcg(&a.ctl->epoch);
     clear_stats(bs);
 
     // tiles of every problem, and the ticket offset of each
@@ -932,9 +946,7 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
 
     bool lep_loaded = false, ph_loaded = false;
     int cur = BATCH ? -1 : 0;
-    if ((long long)blockIdx.x < n_tickets) {
-        if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
-        __syncthreads();
+    {
         for (int buf = 0;; buf ^= 1) {
             const long long t = s_ticket[buf];
             if (t >= n_tickets) break;
