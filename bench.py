@@ -62,18 +62,32 @@ def parse():
                    help="serving: largest electron count of a request (default 1e6; 1e5 "
                         "inside the default line)")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--collision-n", type=float, default=None,
+                   help="collision: electrons (default 1e7; buffers 10x)")
+    p.add_argument("--start-step", type=int, default=None,
+                   help="collision: first step of the timed window (the beam is placed where "
+                        "it is then; default 980, the steps around the pulse peak)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=100)
     return p.parse_args()
 
 
-def workload(name: str, seed: int):
+def workload(name: str, seed: int, start_step: int | None = None, collision_n=None):
     from paper_1311_1107_gb300 import workloads as W
     if name == "foil":
         return W.laser_on_foil(seed=seed)
     if name == "collision":
-        return W.beam_collision(seed=seed)
+        # the 1e7-electron collision, timed from `start` (default 980: the
+        # window around the pulse peak at step 1000), the beam placed where
+        # it is then (it moves at ~c along -x before meeting the pulse)
+        n = int(collision_n or 10_000_000)
+        w = W.beam_collision(n=n, buffer=10 * n, seed=seed)
+        start = 980 if start_step is None else start_step
+        w["electrons"]["x"] = w["electrons"]["x"] - start * w["params"]["dt"]
+        w["params"]["step"] = start
+        w["name"] += f", timed from step {start}"
+        return w
     if name == "serving":
         return W.serving_request_workload(W.serving_requests(n_requests=1, seed=seed)[0])
     return W.plane_wave_collision(seed=seed)
@@ -444,7 +458,7 @@ def ours_arm(args):
     # every rank steps its own shard of one population of `world` copies of
     # the workload: the same initial state, particle ids offset by the rank
     # (independent random streams), no exchange between ranks
-    w = workload(args.workload, 0)
+    w = workload(args.workload, 0, args.start_step, args.collision_n)
     id_base = rank * len(w["electrons"]["x"])
     dims = w["dims"]
     pairs = bool(w["params"].get("pairs", False))
