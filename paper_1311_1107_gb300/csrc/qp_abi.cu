@@ -57,6 +57,8 @@ struct qp_ctx {
     unsigned long long *d_chain = nullptr;  // lepton chain then photon chain
     size_t chain_words = 0;           // words per chain
     double *d_diag = nullptr;         // partials + final
+    double *d_stash = nullptr;        // append records of qp_step launches
+    size_t stash_blocks = 0;          // blocks the stash is sized for
     std::vector<SpeciesRec> species;
     int grid_cache[2][2][5];          // [batch][precision][field] blocks per SM, 0 = unknown
     // kernel timing (qp_profile_*): event pool and (kernel, start event) records
@@ -124,6 +126,7 @@ void release(qp_ctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_chain);
     cudaFree(c->d_diag);
+    cudaFree(c->d_stash);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -167,6 +170,13 @@ int ensure_chain(qp_ctx *c, size_t words)
 }
 
 size_t tiles_of(int64_t cap) { return (size_t)((cap + qp::kTile - 1) / qp::kTile); }
+
+// Bytes of the append-record stash of `blocks` resident blocks (two buffers
+// of kStashFields x kTile doubles each).
+size_t stash_bytes(size_t blocks)
+{
+    return blocks * 2 * (size_t)qp::kStashFieldsHost * qp::kTile * sizeof(double);
+}
 
 // Next free event of the profiling pool (grown on demand).
 cudaError_t next_event(qp_ctx *c, cudaEvent_t *ev)
@@ -574,6 +584,16 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
         if (hs[k] != -1) cap_tiles += (int64_t)tiles_of(ctx->species[hs[k]].d.capacity);
     const int64_t resident = (int64_t)bpsm * ctx->num_sms;
     const int grid = (int)(cap_tiles < resident ? (cap_tiles > 0 ? cap_tiles : 1) : resident);
+    if ((size_t)grid > ctx->stash_blocks) {
+        // grows once, to the resident grid (an allocation, synchronous)
+        double *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, stash_bytes((size_t)resident));
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(ctx->d_stash);
+        ctx->d_stash = p;
+        ctx->stash_blocks = (size_t)resident;
+    }
+    a.stash = ctx->d_stash;
     cudaStream_t cs = (cudaStream_t)stream;
     for (int32_t k = 0; k < s->n_steps; ++k) {
         set_time_host(P, s->step + k);
@@ -595,6 +615,7 @@ struct qp_batch {
     long long *d_left = nullptr;      // [max] launches still to run (0 = idle slot)
     long long *d_pending = nullptr;   // [max][3]
     long long *d_work = nullptr;      // [max] live slots stepped so far
+    double *d_stash = nullptr;        // append records of the batch's launches
     qp::StepCtl *d_ctl = nullptr;
     // pinned staging of the descriptors copied by qp_batch_set; entry k is
     // reused only after the copy that read it has completed (its event)
@@ -617,6 +638,7 @@ void batch_release(qp_batch *b)
     cudaFree(b->d_left);
     cudaFree(b->d_pending);
     cudaFree(b->d_work);
+    cudaFree(b->d_stash);
     cudaFree(b->d_ctl);
     cudaFreeHost(b->h_stage);
     cudaFreeHost(b->h_stage_ctl);
@@ -659,6 +681,7 @@ int qp_batch_create(qp_ctx *ctx, int32_t max_problems, int32_t precision, int32_
     QP_TRY(cudaMemset(b->d_left, 0, n * sizeof(long long)));
     QP_TRY(cudaMalloc(&b->d_pending, 3 * n * sizeof(long long)));
     QP_TRY(cudaMemset(b->d_pending, 0, 3 * n * sizeof(long long)));
+    QP_TRY(cudaMalloc(&b->d_stash, stash_bytes((size_t)b->grid)));
     QP_TRY(cudaMalloc(&b->d_work, n * sizeof(long long)));
     QP_TRY(cudaMemset(b->d_work, 0, n * sizeof(long long)));
     QP_TRY(cudaMalloc(&b->d_ctl, sizeof(qp::StepCtl)));
@@ -779,6 +802,7 @@ int qp_batch_step(qp_batch *b, int32_t n_launches, void *stream)
     a.ctl = b->d_ctl;
     a.n_problems = b->max;
     a.problems = b->d_table;
+    a.stash = b->d_stash;
     cudaStream_t cs = (cudaStream_t)stream;
     for (int32_t k = 0; k < n_launches; ++k) {
         cudaError_t e = timed(b->ctx, 0, cs, [&] {

@@ -75,6 +75,8 @@ struct StepCtl {
 };
 
 constexpr int kMaxProblems = 64;  // problems (independent runs) per launch
+// doubles per thread of one append record (see the stash of qp_step.cuh)
+constexpr int kStashFieldsHost = 7 + 2 * QP_MAX_EMISSIONS;
 
 // One independent run stepped by a launch: its species, field, step
 // constants, look-back scratch and control words.  A launch steps either a
@@ -107,6 +109,7 @@ struct StepArgs {
     unsigned int spin_limit;          // bound of every device-side wait
     int32_t n_problems;               // 0: the single problem below
     const Problem *problems;          // device table of n_problems entries
+    double *stash;                    // append records: [block][2][fields][kTile]
     Problem single;
 };
 

@@ -49,23 +49,30 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *((const volatile unsigned long long *)p);
 }
 
-// Exclusive prefix of this tile in its chain, computed by one full warp
-// (decoupled look-back with a 32-tile window): lane l inspects tile
+// Decoupled look-back over a chain of tiles.  A tile first publishes its
+// aggregate (the number of particles it appends); the exclusive prefix is
+// then computed by one full warp with a 32-tile window: lane l inspects tile
 // base - l; a word counts only if it carries this launch's epoch.  The
 // window is consumed up to the nearest tile that published its inclusive
 // prefix, summing the aggregates in between.  Waits are bounded by
 // spin_limit; on time-out the status is raised and the prefix is what was
 // summed so far (the output is then wrong, the status says so, and the
 // kernel still terminates).  Returns the prefix in every lane.
-__device__ long long chain_prefix(unsigned long long *words, unsigned tile, long long aggregate,
-                                  unsigned epoch, unsigned spin_limit, int *status)
+
+// Publish a tile's aggregate (tile 0: its inclusive prefix); one thread.
+__device__ __forceinline__ void publish_aggregate(unsigned long long *words, unsigned tile,
+                                                  long long aggregate, unsigned epoch)
+{
+    atomicExch(words + tile, make_word(epoch, tile == 0 ? kFlagPre : kFlagAgg, aggregate));
+}
+
+// The exclusive prefix of a tile whose aggregate is published: one full
+// warp; publishes the tile's inclusive prefix.
+__device__ long long resolve_prefix(unsigned long long *words, unsigned tile, long long aggregate,
+                                    unsigned epoch, unsigned spin_limit, int *status)
 {
     const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) atomicExch(words, make_word(epoch, kFlagPre, aggregate));
-        return 0;
-    }
-    if (lane == 0) atomicExch(words + tile, make_word(epoch, kFlagAgg, aggregate));
+    if (tile == 0) return 0;
     long long excl = 0;
     long long base = (long long)tile - 1;
     unsigned spins = 0, nap = 32;
@@ -100,6 +107,14 @@ __device__ long long chain_prefix(unsigned long long *words, unsigned tile, long
     }
     if (lane == 0) atomicExch(words + tile, make_word(epoch, kFlagPre, excl + aggregate));
     return excl;
+}
+
+__device__ long long chain_prefix(unsigned long long *words, unsigned tile, long long aggregate,
+                                  unsigned epoch, unsigned spin_limit, int *status)
+{
+    if ((threadIdx.x & 31) == 0) publish_aggregate(words, tile, aggregate, epoch);
+    __syncwarp();
+    return resolve_prefix(words, tile, aggregate, epoch, spin_limit, status);
 }
 
 // Block-wide exclusive scan of one small count per thread; returns the
@@ -171,14 +186,23 @@ __device__ void flush_stats(const BlockStats &bs, const StepArgs &a, const Probl
         raise_status(a.status, QP_WARN_TABLE_CLAMPED);
 }
 
+// Append records of a tile, written during its physics to a per-block,
+// double-buffered scratch in device memory ([field][thread] per buffer) and
+// read when the tile's slots are known, after the next tile's physics.
+// Lepton tiles: emitter x, y, z, direction kx, ky, kz, weight, then the
+// energies and the optical depths of up to QP_MAX_EMISSIONS photons.  Photon
+// tiles: x, y, z, photon momentum, weight, v, 1 - v, electron and positron
+// optical depths.
+constexpr int kStashGg = 7, kStashTg = kStashGg + QP_MAX_EMISSIONS;
+constexpr int kStashFields = kStashTg + QP_MAX_EMISSIONS;
+static_assert(kStashFields == kStashFieldsHost, "stash layout");
+
 // Shared-memory layout of k_step (dynamic part).
 template <typename R>
 struct Smem {
     R H[kNRatePad];                          // rate tables (TMA-staged)
     R G[kNRatePad];
     R T[kNRatePad];
-    R gg[QP_MAX_EMISSIONS][kTile];           // stashed photon energies
-    R tg[QP_MAX_EMISSIONS][kTile];           // and their optical depths
 };
 
 __device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepArgs &a)
@@ -192,11 +216,10 @@ __device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepA
 // -------------------------------------------------------------------- lepton tile
 
 template <int PREC, int FK, typename R>
-__device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
-                            unsigned long long *bar,
-                            bool &loaded, unsigned chain_tile, int sp, int64_t first, int64_t n,
-                            int64_t ph_base, unsigned epoch, int *s_warp, long long *s_excl,
-                            BlockStats &bs)
+__device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
+                           unsigned long long *bar, bool &loaded, unsigned chain_tile, int sp,
+                           int64_t first, int64_t n, unsigned epoch, int *s_warp, BlockStats &bs,
+                           double *st, unsigned char *s_cnt, int *s_loc)
 {
     const int tid = threadIdx.x;
     if (!loaded && tid == 0) {
@@ -355,8 +378,8 @@ __device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 ++n_emit;
                 if (gg > P.gmin) {
                     const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
-                    sm.gg[nph][tid] = gg;
-                    sm.tg[nph][tid] = -log(u53(rp.x, rp.y));
+                    st[(kStashGg + nph) * kTile + tid] = gg;
+                    st[(kStashTg + nph) * kTile + tid] = -log(u53(rp.x, rp.y));
                     ++nph;
                 } else {
                     ++n_sub;
@@ -503,8 +526,8 @@ __device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 ++n_emit;
                 if (gg > m.gmin) {
                     const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
-                    sm.gg[nph][tid] = gg;
-                    sm.tg[nph][tid] = -logf(u53f(rp.x, rp.y));
+                    st[(kStashGg + nph) * kTile + tid] = f_to_d(gg);
+                    st[(kStashTg + nph) * kTile + tid] = f_to_d(-logf(u53f(rp.x, rp.y)));
                     ++nph;
                 } else {
                     ++n_sub;
@@ -562,58 +585,77 @@ __device__ void lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         }
     }
 
-    // ---- ordered append of the new photons
+    // ---- this tile's appends: the aggregate is published now, the records
+    // stashed; their slots are written after the next tile (write_photons)
     int tile_total;
     const int local = block_scan(nph, s_warp, &tile_total);
-    if (tid < 32) {
-        const long long e =
-            chain_prefix(P.lep_words, chain_tile, tile_total, epoch, a.spin_limit, a.status);
-        if (tid == 0) *s_excl = e;
-    }
-    __syncthreads();
-    const long long excl = *s_excl;
+    if (tid == 0) publish_aggregate(P.lep_words, chain_tile, tile_total, epoch);
     if (nph) {
-        const int64_t base = ph_base + excl + local;
-        int stored = 0, dropped = 0;
-        double e_drop = 0.0;
-        for (int j = 0; j < nph; ++j) {
-            const int64_t slot = base + j;
-            const double gg = to_double(sm.gg[j][tid]);
-            if (photons && slot < Ph.cap) {
-                Ph.x[slot] = x0;
-                Ph.y[slot] = y0;
-                if (Ph.z) Ph.z[slot] = z0;
-                Ph.ux[slot] = gg * kx;
-                Ph.uy[slot] = gg * ky;
-                Ph.uz[slot] = gg * kz;
-                Ph.tau[slot] = to_double(sm.tg[j][tid]);
-                Ph.w[slot] = wgt;
-                if (Ph.chi) Ph.chi[slot] = 0.0;
-                if (Ph.nemit) Ph.nemit[slot] = 0;
-                ++stored;
-            } else {
-                ++dropped;
-                e_drop += wgt * gg;
-            }
-        }
-        if (stored) atomicAdd(&bs.c[sp][cPhoton], (unsigned long long)stored);
-        if (dropped) {
-            atomicAdd(&bs.c[sp][cPhotonDrop], (unsigned long long)dropped);
-            atomicAdd(&bs.e[sp][1], e_drop);
+        st[0 * kTile + tid] = x0;
+        st[1 * kTile + tid] = y0;
+        st[2 * kTile + tid] = z0;
+        st[3 * kTile + tid] = kx;
+        st[4 * kTile + tid] = ky;
+        st[5 * kTile + tid] = kz;
+        st[6 * kTile + tid] = wgt;
+    }
+    s_cnt[tid] = (unsigned char)nph;
+    s_loc[tid] = local;
+    return tile_total;
+}
+
+// Photons of a stashed lepton tile into slots base + (the emitter's offset)
+// onward, in the emitter's order; those beyond the capacity are counted as
+// dropped with their energy.
+__device__ void write_photons(const StepArgs &a, const Problem &P, const double *st,
+                              const unsigned char *s_cnt, const int *s_loc, long long base,
+                              int sp, BlockStats &bs)
+{
+    const int tid = threadIdx.x;
+    const int c = s_cnt[tid];
+    if (!c) return;
+    const SpeciesDev &Ph = P.sp[2];
+    const bool photons = Ph.present != 0;
+    const double x0 = st[0 * kTile + tid], y0 = st[1 * kTile + tid], z0 = st[2 * kTile + tid];
+    const double kx = st[3 * kTile + tid], ky = st[4 * kTile + tid], kz = st[5 * kTile + tid];
+    const double wgt = st[6 * kTile + tid];
+    const int64_t b0 = base + s_loc[tid];
+    int stored = 0, dropped = 0;
+    double e_drop = 0.0;
+    for (int j = 0; j < c; ++j) {
+        const int64_t slot = b0 + j;
+        const double gg = st[(kStashGg + j) * kTile + tid];
+        if (photons && slot < Ph.cap) {
+            Ph.x[slot] = x0;
+            Ph.y[slot] = y0;
+            if (Ph.z) Ph.z[slot] = z0;
+            Ph.ux[slot] = gg * kx;
+            Ph.uy[slot] = gg * ky;
+            Ph.uz[slot] = gg * kz;
+            Ph.tau[slot] = st[(kStashTg + j) * kTile + tid];
+            Ph.w[slot] = wgt;
+            if (Ph.chi) Ph.chi[slot] = 0.0;
+            if (Ph.nemit) Ph.nemit[slot] = 0;
+            ++stored;
+        } else {
+            ++dropped;
+            e_drop += wgt * gg;
         }
     }
-    // s_excl and s_warp[kWarps - 1] (the tile total) stay valid for the caller
-    // until its next barrier
+    if (stored) atomicAdd(&bs.c[sp][cPhoton], (unsigned long long)stored);
+    if (dropped) {
+        atomicAdd(&bs.c[sp][cPhotonDrop], (unsigned long long)dropped);
+        atomicAdd(&bs.e[sp][1], e_drop);
+    }
 }
 
 // -------------------------------------------------------------------- photon tile
 
 template <int PREC, int FK, typename R>
-__device__ void photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
-                            unsigned long long *bar,
-                            bool &loaded, unsigned chain_tile, int64_t n, int64_t be, int64_t bp,
-                            int64_t room, unsigned epoch, int *s_warp, long long *s_excl,
-                            BlockStats &bs, int *tile_total_out)
+__device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
+                           unsigned long long *bar, bool &loaded, unsigned chain_tile, int64_t n,
+                           unsigned epoch, int *s_warp, BlockStats &bs, double *st,
+                           unsigned char *s_cnt, int *s_loc)
 {
     const int tid = threadIdx.x;
     const SpeciesDev &Ph = P.sp[2], &El = P.sp[0], &Po = P.sp[1];
@@ -773,48 +815,71 @@ __device__ void photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     if (npair && Ph.nemit) Ph.nemit[i] += 1;
     warp_count(&bs.c[2][cClamp], clamped);
     warp_count(&bs.c[2][cPair], npair != 0);
-    *tile_total_out = 0;
-    if (!pairs) return;
+    if (!pairs) return 0;
 
+    // ---- this tile's pairs: aggregate published now, records stashed
     int tile_total;
     const int local = block_scan(npair, s_warp, &tile_total);
-    if (tid < 32) {
-        const long long e =
-            chain_prefix(P.pho_words, chain_tile, tile_total, epoch, a.spin_limit, a.status);
-        if (tid == 0) *s_excl = e;
-    }
-    __syncthreads();
-    const long long excl = *s_excl;
-    *tile_total_out = tile_total;
+    if (tid == 0) publish_aggregate(P.pho_words, chain_tile, tile_total, epoch);
     if (npair) {
-        const int64_t ord = excl + local;
-        if (leptons && ord < room) {
-            const int64_t se = be + ord, spo = bp + ord;
-            const double om = omv;
-            El.x[se] = px;
-            El.y[se] = py;
-            if (El.z) El.z[se] = pz;
-            El.ux[se] = v * gux;
-            El.uy[se] = v * guy;
-            El.uz[se] = v * guz;
-            El.tau[se] = tm;
-            El.w[se] = wg;
-            if (El.chi) El.chi[se] = 0.0;
-            if (El.nemit) El.nemit[se] = 0;
-            Po.x[spo] = px;
-            Po.y[spo] = py;
-            if (Po.z) Po.z[spo] = pz;
-            Po.ux[spo] = om * gux;
-            Po.uy[spo] = om * guy;
-            Po.uz[spo] = om * guz;
-            Po.tau[spo] = tp;
-            Po.w[spo] = wg;
-            if (Po.chi) Po.chi[spo] = 0.0;
-            if (Po.nemit) Po.nemit[spo] = 0;
-        } else {
-            atomicAdd(&bs.c[2][cPairDrop], 1ull);
-            atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
-        }
+        st[0 * kTile + tid] = px;
+        st[1 * kTile + tid] = py;
+        st[2 * kTile + tid] = pz;
+        st[3 * kTile + tid] = gux;
+        st[4 * kTile + tid] = guy;
+        st[5 * kTile + tid] = guz;
+        st[6 * kTile + tid] = wg;
+        st[7 * kTile + tid] = v;
+        st[8 * kTile + tid] = omv;
+        st[9 * kTile + tid] = tm;
+        st[10 * kTile + tid] = tp;
+    }
+    s_cnt[tid] = (unsigned char)npair;
+    s_loc[tid] = local;
+    return tile_total;
+}
+
+// The e-/e+ pairs of a stashed photon tile: pair number excl + (offset) goes
+// to slots be + that and bp + that while it is below `room`; beyond it the
+// pair is dropped and its energy counted.
+__device__ void write_pairs(const Problem &P, const double *st, const unsigned char *s_cnt,
+                            const int *s_loc, long long excl, long long be, long long bp,
+                            long long room, BlockStats &bs)
+{
+    const int tid = threadIdx.x;
+    if (!s_cnt[tid]) return;
+    const SpeciesDev &El = P.sp[0], &Po = P.sp[1];
+    const bool leptons = El.present && Po.present;
+    const double px = st[0 * kTile + tid], py = st[1 * kTile + tid], pz = st[2 * kTile + tid];
+    const double gux = st[3 * kTile + tid], guy = st[4 * kTile + tid], guz = st[5 * kTile + tid];
+    const double wg = st[6 * kTile + tid];
+    const int64_t ord = excl + s_loc[tid];
+    if (leptons && ord < room) {
+        const double v = st[7 * kTile + tid], om = st[8 * kTile + tid];
+        const int64_t se = be + ord, spo = bp + ord;
+        El.x[se] = px;
+        El.y[se] = py;
+        if (El.z) El.z[se] = pz;
+        El.ux[se] = v * gux;
+        El.uy[se] = v * guy;
+        El.uz[se] = v * guz;
+        El.tau[se] = st[9 * kTile + tid];
+        El.w[se] = wg;
+        if (El.chi) El.chi[se] = 0.0;
+        if (El.nemit) El.nemit[se] = 0;
+        Po.x[spo] = px;
+        Po.y[spo] = py;
+        if (Po.z) Po.z[spo] = pz;
+        Po.ux[spo] = om * gux;
+        Po.uy[spo] = om * guy;
+        Po.uz[spo] = om * guz;
+        Po.tau[spo] = st[10 * kTile + tid];
+        Po.w[spo] = wg;
+        if (Po.chi) Po.chi[spo] = 0.0;
+        if (Po.nemit) Po.nemit[spo] = 0;
+    } else {
+        atomicAdd(&bs.c[2][cPairDrop], 1ull);
+        atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
     }
 }
 
@@ -889,12 +954,74 @@ __device__ void scan_offsets(long long *v, int n, long long *s_tmp)
     __syncthreads();
 }
 
+// The tile whose appends are stashed and not yet written (one per block).
+struct Pending {
+    int valid, chain, last, sp, buf, total;
+    unsigned tile;
+    long long base, be, bp, room;
+};
+
+// Resolve the pending tile's prefix (its predecessors are, by now, almost
+// always published) and write its photons or pairs; the last tile of a
+// chain also sets the new live count applied at the end of the launch.
+// All threads of the block; uniform on the shared record.
+// (not inlined: its registers stay out of the physics of the tile loop)
+__device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, Pending &pd,
+                                           unsigned epoch, long long *s_excl, BlockStats &bs,
+                                           const double *stash_block,
+                                           unsigned char (*s_cnt)[kTile], int (*s_loc)[kTile])
+{
+    // every thread reads the record before any thread may change it (the
+    // caller's thread 0 records the next pending tile right after the call)
+    const bool valid = pd.valid != 0;
+    __syncthreads();
+    if (!valid) return;
+    if (threadIdx.x < 32) {
+        const long long e = resolve_prefix(pd.chain ? P.pho_words : P.lep_words, pd.tile,
+                                           pd.total, epoch, a.spin_limit, a.status);
+        if (threadIdx.x == 0) *s_excl = e;
+    }
+    __syncthreads();
+    const long long excl = *s_excl;
+    const double *st = stash_block + (size_t)pd.buf * kStashFields * kTile;
+    if (pd.chain == 0) {
+        if (pd.last && threadIdx.x == 0) {
+            const long long tot = pd.base + excl + pd.total;
+            if (P.sp[2].present) {
+                P.pending[2] = tot < P.sp[2].cap ? tot : P.sp[2].cap;
+                if (tot > P.sp[2].cap) raise_status(a.status, QP_WARN_BUFFER_FULL);
+            } else if (tot > pd.base) {
+                raise_status(a.status, QP_WARN_BUFFER_FULL);
+            }
+        }
+        if (pd.total) write_photons(a, P, st, s_cnt[pd.buf], s_loc[pd.buf], pd.base + excl, pd.sp, bs);
+    } else {
+        if (pd.last && threadIdx.x == 0) {
+            const long long tot = excl + pd.total;
+            const long long add = tot < pd.room ? tot : pd.room;
+            P.pending[0] = pd.be + add;
+            P.pending[1] = pd.bp + add;
+            if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
+        }
+        if (pd.total)
+            write_pairs(P, st, s_cnt[pd.buf], s_loc[pd.buf], excl, pd.be, pd.bp, pd.room, bs);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pd.valid = 0;
+    __syncthreads();
+}
+
 // One launch = one step of every active problem.  Persistent blocks take
 // 128-particle tiles from an atomic ticket (the next ticket is fetched while
 // the current tile runs when more tiles than blocks remain); tickets enumerate, problem after problem, its
 // electron tiles, positron tiles and photon tiles, so within each problem's
 // chains start order is tile order and the decoupled look-back only ever
-// waits on tiles that are running.  BATCH = false: the single problem of the
+// waits on tiles that are running.  A tile's appends are written one tile
+// later: its aggregate is published right after its physics, its records go
+// to a stash, and its prefix is resolved after the block's next tile, when
+// the earlier tiles have almost always published, so blocks do not wait on
+// one another tile after tile (the smallest unpublished tile always
+// progresses: every wait is for smaller tiles).  BATCH = false: the single problem of the
 // launch parameters (read in place, from the constant bank); BATCH = true: a
 // device table of problems, each copied to shared memory for its tiles, with
 // time and step counters advanced on the device.
@@ -918,6 +1045,9 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     __shared__ int s_tl[kMaxProblems], s_tg[kMaxProblems];
     __shared__ ProbCounts s_pc;
     __shared__ int s_last;
+    __shared__ Pending s_pend;
+    __shared__ unsigned char s_cnt[2][kTile];
+    __shared__ int s_loc[2][kTile];
 
     const int tid = threadIdx.x;
     // the first ticket is taken at entry: its atomic overlaps the reads of
@@ -928,6 +1058,8 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
     clear_stats(bs);
+    if (tid == 0) s_pend.valid = 0;
+    const double *stash_block = a.stash + (size_t)blockIdx.x * 2 * kStashFields * kTile;
 
     // tiles of every problem, and the ticket offset of each
     bool bad = false;
@@ -968,6 +1100,8 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
                 b = lo;
                 if (b != cur) {
                     if (cur >= 0) {
+                        flush_pending(a, s_prob, s_pend, epoch, &s_excl, bs, stash_block, s_cnt,
+                                      s_loc);
                         flush_stats(bs, a, s_prob);
                         __syncthreads();
                         clear_stats(bs);
@@ -989,20 +1123,25 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
             const Problem &P = BATCH ? s_prob : a.single;
             const ProbCounts pc = s_pc;                         // in registers for the tile
             const long long lt = t - (b > 0 ? s_off[b - 1] : 0);  // tile within the problem
+            const int sb = s_pend.valid ? (s_pend.buf ^ 1) : 0;  // stash buffer of this tile
+            double *st = const_cast<double *>(stash_block) + (size_t)sb * kStashFields * kTile;
             if (lt < pc.tiles_l) {
                 const int sp = lt < pc.tiles_e ? 0 : 1;
                 const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
-                lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp, first,
-                                         pc.n[sp], pc.n[2], epoch, s_warp, &s_excl, bs);
-                if (lt == pc.tiles_l - 1 && tid == 0) {
-                    // last lepton tile: the new photon count, applied at the end
-                    const int64_t tot = pc.n[2] + s_excl + s_warp[kWarps - 1];
-                    if (P.sp[2].present) {
-                        P.pending[2] = tot < P.sp[2].cap ? tot : P.sp[2].cap;
-                        if (tot > P.sp[2].cap) raise_status(a.status, QP_WARN_BUFFER_FULL);
-                    } else if (tot > pc.n[2]) {
-                        raise_status(a.status, QP_WARN_BUFFER_FULL);
-                    }
+                const int total =
+                    lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp,
+                                             first, pc.n[sp], epoch, s_warp, bs, st, s_cnt[sb],
+                                             s_loc[sb]);
+                flush_pending(a, P, s_pend, epoch, &s_excl, bs, stash_block, s_cnt, s_loc);
+                if (tid == 0) {
+                    s_pend.valid = 1;
+                    s_pend.chain = 0;
+                    s_pend.last = lt == pc.tiles_l - 1;
+                    s_pend.sp = sp;
+                    s_pend.buf = sb;
+                    s_pend.total = total;
+                    s_pend.tile = (unsigned)lt;
+                    s_pend.base = pc.n[2];
                 }
             } else {
                 const unsigned pt = (unsigned)(lt - pc.tiles_l);
@@ -1013,23 +1152,32 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
                     if (P.sp[1].cap - bp < room) room = P.sp[1].cap - bp;
                     if (room < 0) room = 0;
                 }
-                int tile_total = 0;
-                photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], be, bp,
-                                         room, epoch, s_warp, &s_excl, bs, &tile_total);
-                if ((long long)pt == pc.tiles_g - 1 && tid == 0 && P.pairs) {
-                    // last photon tile: the new lepton counts, applied at the end
-                    const int64_t tot = s_excl + tile_total;
-                    const int64_t add = tot < room ? tot : room;
-                    P.pending[0] = be + add;
-                    P.pending[1] = bp + add;
-                    if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
+                const int total =
+                    photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], epoch,
+                                             s_warp, bs, st, s_cnt[sb], s_loc[sb]);
+                flush_pending(a, P, s_pend, epoch, &s_excl, bs, stash_block, s_cnt, s_loc);
+                if (tid == 0 && P.pairs) {
+                    s_pend.valid = 1;
+                    s_pend.chain = 1;
+                    s_pend.last = (long long)pt == pc.tiles_g - 1;
+                    s_pend.sp = 2;
+                    s_pend.buf = sb;
+                    s_pend.total = total;
+                    s_pend.tile = pt;
+                    s_pend.be = be;
+                    s_pend.bp = bp;
+                    s_pend.room = room;
                 }
             }
             if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
             __syncthreads();
         }
     }
-    if (cur >= 0) flush_stats(bs, a, BATCH ? s_prob : a.single);
+    if (cur >= 0) {
+        flush_pending(a, BATCH ? s_prob : a.single, s_pend, epoch, &s_excl, bs, stash_block, s_cnt,
+                      s_loc);
+        flush_stats(bs, a, BATCH ? s_prob : a.single);
+    }
 
     // ---- the last block to finish publishes the step of every problem
     if (tid == 0) {

@@ -255,6 +255,30 @@ def test_runs_are_bit_identical(ctx):
             np.testing.assert_array_equal(a[name][k], b[name][k])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pair_cascade_is_bit_identical_with_many_tiles_per_block(ctx, precision):
+    # 20000 electrons in the constant-B cascade: hundreds of thousands of
+    # photons, so every block steps many tiles of both chains and carries
+    # a pending append from one tile to the next; three runs must agree bit
+    # for bit (slot order and counts do not depend on scheduling)
+    w = W.uniform_b_cascade(n=20000, n_steps=40, cap=1 << 21)
+    runs = []
+    for _ in range(3):
+        sim = Simulation(w, precision=precision, ctx=ctx)
+        assert sim.run(40) >= 0
+        torch.cuda.synchronize()
+        runs.append({k: sp.host() for k, sp in sim.species.items()})
+        d = sim.diagnostics("photon")
+        # every pair created is one decay counted by the photon species
+        assert runs[-1]["positron"]["x"].shape[0] == d.n_pair - d.n_pair_drop
+        sim.close()
+    assert runs[0]["photon"]["x"].shape[0] > 500_000
+    for r in runs[1:]:
+        for name in r:
+            for k in r[name]:
+                np.testing.assert_array_equal(r[name][k], runs[0][name][k], err_msg=f"{name}.{k}")
+
+
 def test_diagnostics_match_host_reductions(ctx):
     w = W.beam_collision(n=5000, n_steps=120, buffer=300_000)
     sim, gpu, diag = gpu_run(ctx, w, 120)
