@@ -362,12 +362,13 @@ int qp_diagnostics_noalloc(const qp_species_desc *d, qp_diag *out, void *stream)
 int qp_reset_counters(qp_ctx *ctx, int32_t handle);
 
 /*
- * Kernel timing for benchmarks.  While enabled, qp_step brackets each of its
- * kernel launches with CUDA events recorded on the step's stream (events are
- * owned by the context; enabling clears earlier records).
- * qp_profile_read synchronises on the recorded events and returns, per
- * kernel (0 step-begin, 1 lepton, 2 photon), the summed device time in ms
- * and the number of launches.  No counterpart in the paper.
+ * Kernel timing for benchmarks.  While enabled, qp_step and qp_batch_step
+ * bracket each launch of the fused step kernel (one launch per step) with CUDA
+ * events recorded on the step's stream (events are owned by the context;
+ * enabling clears earlier records).  qp_profile_read synchronises on the
+ * recorded events and returns in ms[0] the summed device time in ms and in
+ * launches[0] the number of launches; entries 1 and 2 are reserved and read
+ * as 0.  No counterpart in the paper.
  */
 int qp_profile_enable(qp_ctx *ctx, int enable);
 int qp_profile_read(qp_ctx *ctx, double ms[3], int64_t launches[3]);

@@ -238,8 +238,6 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     }
     if (!loaded) __syncthreads();
     const SpeciesDev &S = P.sp[sp];
-    const SpeciesDev &Ph = P.sp[2];
-    const bool photons = Ph.present != 0;
     const int64_t i = first + tid;
     const bool active = i < n;
 
@@ -658,9 +656,8 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned char *s_cnt, int *s_loc)
 {
     const int tid = threadIdx.x;
-    const SpeciesDev &Ph = P.sp[2], &El = P.sp[0], &Po = P.sp[1];
+    const SpeciesDev &Ph = P.sp[2];
     const bool pairs = P.pairs != 0;
-    const bool leptons = El.present && Po.present;
     if (pairs && !loaded) {
         if (tid == 0) {
             const unsigned bytes = kNRatePad * sizeof(R);

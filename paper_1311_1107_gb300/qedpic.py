@@ -228,7 +228,7 @@ def qp_profile_enable(ctx, enable: bool = True) -> int:
 
 
 def qp_profile_read(ctx):
-    """(ms[3], launches[3]) per kernel: step-begin, lepton, photon."""
+    """(ms[3], launches[3]): entry 0 is the fused step kernel; 1 and 2 are reserved (0)."""
     ms = (C.c_double * 3)()
     n = (C.c_int64 * 3)()
     _check("qp_profile_read", lib().qp_profile_read(ctx, ms, n))
