@@ -19,8 +19,12 @@
 
 #ifdef __CUDACC__
 #define QP_HD __host__ __device__ __forceinline__
+// rare cases: called, never inlined, so that the common path's code stays
+// short and carries no predicated-off FP64 instructions
+#define QP_HD_COLD __host__ __device__ inline __noinline__
 #else
 #define QP_HD inline
+#define QP_HD_COLD inline
 #include <math.h>
 #include <string.h>
 #endif
@@ -253,17 +257,19 @@ QP_HD double f_to_d(float f)
 // instructions, for a normalised pair (|lo| <= ulp(hi), as every df2
 // operation above returns).  Pairs outside that range, zero hi, and
 // non-finite values take an FP64 path.
+QP_HD_COLD double merge_df_fp64(float hi, float lo) { return (double)hi + (double)lo; }
+
 QP_HD double merge_df(df2 a)
 {
     const uint32_t hb = f2u(a.hi), lb = f2u(a.lo);
     const uint32_t eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
-    if (eh == 0u || eh == 0xFFu || el == 0xFFu) return (double)a.hi + (double)a.lo;
+    if (eh == 0u || eh == 0xFFu || el == 0xFFu) return merge_df_fp64(a.hi, a.lo);
     const uint64_t sign = (uint64_t)(hb & 0x80000000u) << 32;
     int64_t S = (int64_t)((1ull << 52) | ((uint64_t)(hb & 0x7FFFFFu) << 29));
     if (el != 0u) {
         // lo in units of 2^-52 of hi's binade: ml * 2^(el - eh + 29)
         const int k = (int)el - (int)eh + 29;
-        if (k > 8) return (double)a.hi + (double)a.lo;  // not normalised
+        if (k > 8) return merge_df_fp64(a.hi, a.lo);  // not normalised
         const uint64_t ml = (1ull << 23) | (lb & 0x7FFFFFu);
         uint64_t L;
         if (k >= 0)
@@ -290,14 +296,28 @@ QP_HD double merge_df(df2 a)
 
 // d + f rounded to double (within one unit in the last place) by integer
 // instructions: the FP64 accumulation of an FP32 increment.  The stored
-// double keeps all its bits; only the increment carries FP32 error.  Zero,
-// non-finite and subnormal operands, increments not much smaller than d,
-// and large cancellations take an FP64 path.
-QP_HD double add_fd_wide(double d, float f);
+// double keeps all its bits; only the increment carries FP32 error.
+// add_fd handles the common case inline (d and f normal, f from half a unit
+// of d's last place up to 2^27 units, the sum in d's binade) and calls
+// add_fd_slow for the rest.
+
+// The cases add_fd does not handle in integers (zero or tiny d, increments
+// comparable to or larger than d, large cancellations): through a
+// double-float sum, exact to 2^-47 relative, still without FP64
+// instructions; non-finite values go through FP64.
+QP_HD_COLD double add_fd_wide(double d, float f)
+{
+    const uint32_t ed = (uint32_t)(d2u(d) >> 52) & 0x7FFu;
+    const uint32_t ef = (f2u(f) >> 23) & 0xFFu;
+    if (ed == 0x7FFu || ef == 0xFFu || (ed != 0u && ed < 897u) || ed > 1150u)
+        return d + (double)f;
+    return merge_df(df_add_f(split_d(d), f));
+}
 
 // The general integer sum (the result may leave d's binade: renormalised,
-// rounded once); large cancellations take the double-float route.
-QP_HD double add_fd_renorm(double d, float f)
+// rounded once); zero, non-finite and subnormal operands, increments not
+// much smaller than d, and large cancellations take add_fd_wide.
+QP_HD_COLD double add_fd_slow(double d, float f)
 {
     const uint32_t fb = f2u(f);
     if ((fb & 0x7FFFFFFFu) == 0u) return d;
@@ -330,34 +350,24 @@ QP_HD double add_fd_renorm(double d, float f)
 QP_HD double add_fd(double d, float f)
 {
     const uint32_t fb = f2u(f);
-    if ((fb & 0x7FFFFFFFu) == 0u) return d;
+    if ((fb << 1) == 0u) return d;  // f = +-0
     const uint64_t db = d2u(d);
-    const uint32_t ed = (uint32_t)(db >> 52) & 0x7FFu, ef = (fb >> 23) & 0xFFu;
+    const uint32_t dh = (uint32_t)(db >> 32);
+    const uint32_t ed = (dh >> 20) & 0x7FFu, ef = (fb >> 23) & 0xFFu;
     // f in units of d's last place: mf * 2^k, k = ef - ed + 925
     const int k = (int)ef - (int)ed + 925;
-    if (k < -25 && ed != 0u && ed != 0x7FFu && ef != 0xFFu) return d;  // below half a unit
-    if (ed == 0u || ed == 0x7FFu || ef == 0u || ef == 0xFFu || k > 27) return add_fd_wide(d, f);
-    const uint32_t mf = (1u << 23) | (fb & 0x7FFFFFu);
-    // the increment rounded to d's last place (half-way cases away from zero)
-    const uint64_t L = k >= 0 ? ((uint64_t)mf << k) : (uint64_t)((mf + (1u << (-k - 1))) >> (-k));
-    // added to (or taken from) the magnitude bits directly: exact while the
-    // exponent field stays the same, which the check below confirms
-    const uint64_t r = ((uint32_t)(db >> 63) == (fb >> 31)) ? db + L : db - L;
-    if (((uint32_t)(r >> 52) & 0x7FFu) != ed) return add_fd_renorm(d, f);  // binade crossed
-    return u2d(r);
-}
-
-// The cases add_fd does not handle in integers (zero or tiny d, increments
-// comparable to or larger than d, large cancellations): through a
-// double-float sum, exact to 2^-47 relative, still without FP64
-// instructions; non-finite values go through FP64.
-QP_HD double add_fd_wide(double d, float f)
-{
-    const uint32_t ed = (uint32_t)(d2u(d) >> 52) & 0x7FFu;
-    const uint32_t ef = (f2u(f) >> 23) & 0xFFu;
-    if (ed == 0x7FFu || ef == 0xFFu || (ed != 0u && ed < 897u) || ed > 1150u)
-        return d + (double)f;
-    return merge_df(df_add_f(split_d(d), f));
+    if ((ed - 1u) < 0x7FEu && (ef - 1u) < 0xFEu && k <= 27) {
+        if (k < -25) return d;  // below half a unit of d's last place
+        const uint32_t mf = (1u << 23) | (fb & 0x7FFFFFu);
+        // the increment rounded to d's last place (half-way cases away from zero)
+        const uint64_t L =
+            k >= 0 ? ((uint64_t)mf << k) : (uint64_t)((mf + (1u << (-k - 1))) >> (-k));
+        // added to (or taken from) the magnitude bits directly: exact while
+        // the exponent field stays the same, which the test below confirms
+        const uint64_t r = ((dh ^ fb) >> 31) ? db - L : db + L;
+        if (((((uint32_t)(r >> 32)) ^ dh) & 0x7FF00000u) == 0u) return u2d(r);
+    }
+    return add_fd_slow(d, f);
 }
 
 }  // namespace qp

@@ -447,7 +447,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                                    m.inv_aS_lo);
         if (S.chi) S.chi[i] = f_to_d(chi);
         float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
-        float dtau_once = 0.0f;
+        float dtau_once = 0.0f, esub_f = 0.0f;
         bool events = false;
         df2 TAU = {0.0f, 0.0f};
 
@@ -529,7 +529,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                     ++nph;
                 } else {
                     ++n_sub;
-                    e_sub += f_to_d(gg);
+                    esub_f += gg;
                 }
                 if (pmag > 0.0f) {
                     const float s1 = keep / pmag;
@@ -560,6 +560,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             S.tau[i] = merge_df(TAU);
         else if (dtau_once != 0.0f)
             S.tau[i] = add_fd(taud, -dtau_once);
+        if (n_sub) e_sub = f_to_d(esub_f);
         if (nph || n_sub) wgt = S.w[i];
     }
     }

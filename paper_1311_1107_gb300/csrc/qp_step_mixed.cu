@@ -1,4 +1,6 @@
 // Instantiations of the step kernel, mixed-precision path (see qp_step.cuh).
+// This unit is compiled with -prec-div=false: FP32 quotients use the
+// hardware reciprocal (2 ulp), well inside the path's FP32 error budget.
 #include "qp_step.cuh"
 
 namespace qp {
