@@ -171,11 +171,11 @@ int ensure_chain(qp_ctx *c, size_t words)
 
 size_t tiles_of(int64_t cap) { return (size_t)((cap + qp::kTile - 1) / qp::kTile); }
 
-// Bytes of the append-record stash of `blocks` resident blocks (two buffers
-// of kStashFields x kTile doubles each).
+// Bytes of the append-record stash of `blocks` resident blocks (kStashBufs
+// buffers of kStashFields x kTile doubles each).
 size_t stash_bytes(size_t blocks)
 {
-    return blocks * 2 * (size_t)qp::kStashFieldsHost * qp::kTile * sizeof(double);
+    return blocks * qp::kStashBufs * (size_t)qp::kStashFieldsHost * qp::kTile * sizeof(double);
 }
 
 // Next free event of the profiling pool (grown on demand).

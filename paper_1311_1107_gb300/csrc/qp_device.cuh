@@ -75,8 +75,11 @@ struct StepCtl {
 };
 
 constexpr int kMaxProblems = 64;  // problems (independent runs) per launch
-// doubles per thread of one append record (see the stash of qp_step.cuh)
+// doubles per thread of one append record (see the stash of qp_step.cuh),
+// and the append-record buffers per block: a tile's appends are written
+// kStashBufs - 1 tiles after its physics
 constexpr int kStashFieldsHost = 7 + 2 * QP_MAX_EMISSIONS;
+constexpr int kStashBufs = 3;
 
 // One independent run stepped by a launch: its species, field, step
 // constants, look-back scratch and control words.  A launch steps either a

@@ -149,23 +149,40 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(float v) { return f_to_d(v); }
 
 // Counters kept in shared memory per block and species, flushed with one
-// atomic per counter when the block leaves.
+// atomic per counter when the block leaves.  The counts are 32-bit (shared
+// memory adds them natively; a block never counts 2^32 events in a launch),
+// summed over a warp before one lane adds them.
 struct BlockStats {
-    unsigned long long c[3][9];
+    unsigned c[3][9];
     double e[3][2];
 };
 enum { cEmit, cPhoton, cPhotonDrop, cSub, cPair, cPairDrop, cSat, cClamp, cCont };
 
-__device__ __forceinline__ void warp_count(unsigned long long *ctr, bool pred)
+__device__ __forceinline__ void warp_count(unsigned *ctr, bool pred)
 {
     const unsigned m = __ballot_sync(0xFFFFFFFFu, pred);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned long long)__popc(m));
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, (unsigned)__popc(m));
+}
+
+// Sum of v over the (converged) warp, added by one lane.
+__device__ __forceinline__ void warp_add(unsigned *ctr, unsigned v)
+{
+    const unsigned s = __reduce_add_sync(0xFFFFFFFFu, v);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, s);
+}
+
+__device__ __forceinline__ void warp_add(double *ctr, double v)
+{
+    if (!__any_sync(0xFFFFFFFFu, v != 0.0)) return;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(ctr, v);
 }
 
 __device__ __forceinline__ void clear_stats(BlockStats &bs)
 {
     const int t = threadIdx.x;
-    if (t < 27) (&bs.c[0][0])[t] = 0ull;
+    if (t < 27) (&bs.c[0][0])[t] = 0u;
     if (t < 6) (&bs.e[0][0])[t] = 0.0;
 }
 
@@ -176,7 +193,7 @@ __device__ void flush_stats(const BlockStats &bs, const StepArgs &a, const Probl
     if (t < 27) {
         const int s = t / 9, k = t % 9;
         if (bs.c[s][k] && P.sp[s].present)
-            atomicAdd(&a.stats[P.sp[s].slot_stats].n_emit + k, bs.c[s][k]);
+            atomicAdd(&a.stats[P.sp[s].slot_stats].n_emit + k, (unsigned long long)bs.c[s][k]);
     } else if (t >= 32 && t < 38) {
         const int s = (t - 32) / 2, k = (t - 32) % 2;
         if (bs.e[s][k] != 0.0 && P.sp[s].present)
@@ -186,9 +203,9 @@ __device__ void flush_stats(const BlockStats &bs, const StepArgs &a, const Probl
         raise_status(a.status, QP_WARN_TABLE_CLAMPED);
 }
 
-// Append records of a tile, written during its physics to a per-block,
-// double-buffered scratch in device memory ([field][thread] per buffer) and
-// read when the tile's slots are known, after the next tile's physics.
+// Append records of a tile, written during its physics to a per-block ring
+// of kStashBufs buffers in device memory ([field][thread] per buffer) and
+// read when the tile's slots are known, kStashBufs - 1 tiles later.
 // Lepton tiles: emitter x, y, z, direction kx, ky, kz, weight, then the
 // energies and the optical depths of up to QP_MAX_EMISSIONS photons.  Photon
 // tiles: x, y, z, photon momentum, weight, v, 1 - v, electron and positron
@@ -196,6 +213,10 @@ __device__ void flush_stats(const BlockStats &bs, const StepArgs &a, const Probl
 constexpr int kStashGg = 7, kStashTg = kStashGg + QP_MAX_EMISSIONS;
 constexpr int kStashFields = kStashTg + QP_MAX_EMISSIONS;
 static_assert(kStashFields == kStashFieldsHost, "stash layout");
+// Append map of a stashed tile: entry j (the tile's j-th new particle) holds
+// its parent thread (low byte) and the parent's emission index (high byte).
+constexpr int kMapEntries = kTile * QP_MAX_EMISSIONS;
+static_assert(kTile <= 256 && QP_MAX_EMISSIONS <= 256, "append map entries are two bytes");
 
 // Shared-memory layout of k_step (dynamic part).
 template <typename R>
@@ -219,7 +240,7 @@ template <int PREC, int FK, typename R>
 __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned long long *bar, bool &loaded, unsigned chain_tile, int sp,
                            int64_t first, int64_t n, unsigned epoch, int *s_warp, BlockStats &bs,
-                           double *st, unsigned char *s_cnt, int *s_loc)
+                           double *st, unsigned short *s_map)
 {
     const int tid = threadIdx.x;
     if (!loaded && tid == 0) {
@@ -577,15 +598,13 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     warp_count(&bs.c[sp][cSat], sat);
     warp_count(&bs.c[sp][cClamp], clamped);
     if (__any_sync(0xFFFFFFFFu, n_emit > 0)) {
-        if (n_emit) atomicAdd(&bs.c[sp][cEmit], (unsigned long long)n_emit);
-        if (n_sub) {
-            atomicAdd(&bs.c[sp][cSub], (unsigned long long)n_sub);
-            atomicAdd(&bs.e[sp][0], wgt * e_sub);
-        }
+        warp_add(&bs.c[sp][cEmit], (unsigned)n_emit);
+        warp_add(&bs.c[sp][cSub], (unsigned)n_sub);
+        warp_add(&bs.e[sp][0], n_sub ? wgt * e_sub : 0.0);
     }
 
     // ---- this tile's appends: the aggregate is published now, the records
-    // stashed; their slots are written after the next tile (write_photons)
+    // stashed and mapped; their slots are written later (write_photons)
     int tile_total;
     const int local = block_scan(nph, s_warp, &tile_total);
     if (tid == 0) publish_aggregate(P.lep_words, chain_tile, tile_total, epoch);
@@ -598,40 +617,34 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         st[5 * kTile + tid] = kz;
         st[6 * kTile + tid] = wgt;
     }
-    s_cnt[tid] = (unsigned char)nph;
-    s_loc[tid] = local;
+    for (int k = 0; k < nph; ++k) s_map[local + k] = (unsigned short)(tid | (k << 8));
     return tile_total;
 }
 
-// Photons of a stashed lepton tile into slots base + (the emitter's offset)
-// onward, in the emitter's order; those beyond the capacity are counted as
-// dropped with their energy.
-__device__ void write_photons(const StepArgs &a, const Problem &P, const double *st,
-                              const unsigned char *s_cnt, const int *s_loc, long long base,
-                              int sp, BlockStats &bs)
+// Photons of a stashed lepton tile: the tile's photon j (in emitter order)
+// goes to slot base + j, one thread per photon (coalesced stores); those
+// beyond the capacity are counted as dropped with their energy.
+__device__ void write_photons(const Problem &P, const double *st, const unsigned short *s_map,
+                              int total, long long base, int sp, BlockStats &bs)
 {
-    const int tid = threadIdx.x;
-    const int c = s_cnt[tid];
-    if (!c) return;
     const SpeciesDev &Ph = P.sp[2];
     const bool photons = Ph.present != 0;
-    const double x0 = st[0 * kTile + tid], y0 = st[1 * kTile + tid], z0 = st[2 * kTile + tid];
-    const double kx = st[3 * kTile + tid], ky = st[4 * kTile + tid], kz = st[5 * kTile + tid];
-    const double wgt = st[6 * kTile + tid];
-    const int64_t b0 = base + s_loc[tid];
     int stored = 0, dropped = 0;
     double e_drop = 0.0;
-    for (int j = 0; j < c; ++j) {
-        const int64_t slot = b0 + j;
-        const double gg = st[(kStashGg + j) * kTile + tid];
+    for (int j = threadIdx.x; j < total; j += kTile) {
+        const unsigned m = s_map[j];
+        const int e = (int)(m & 0xFFu), k = (int)(m >> 8);
+        const int64_t slot = base + j;
+        const double gg = st[(kStashGg + k) * kTile + e];
+        const double wgt = st[6 * kTile + e];
         if (photons && slot < Ph.cap) {
-            Ph.x[slot] = x0;
-            Ph.y[slot] = y0;
-            if (Ph.z) Ph.z[slot] = z0;
-            Ph.ux[slot] = gg * kx;
-            Ph.uy[slot] = gg * ky;
-            Ph.uz[slot] = gg * kz;
-            Ph.tau[slot] = st[(kStashTg + j) * kTile + tid];
+            Ph.x[slot] = st[0 * kTile + e];
+            Ph.y[slot] = st[1 * kTile + e];
+            if (Ph.z) Ph.z[slot] = st[2 * kTile + e];
+            Ph.ux[slot] = gg * st[3 * kTile + e];
+            Ph.uy[slot] = gg * st[4 * kTile + e];
+            Ph.uz[slot] = gg * st[5 * kTile + e];
+            Ph.tau[slot] = st[(kStashTg + k) * kTile + e];
             Ph.w[slot] = wgt;
             if (Ph.chi) Ph.chi[slot] = 0.0;
             if (Ph.nemit) Ph.nemit[slot] = 0;
@@ -641,10 +654,10 @@ __device__ void write_photons(const StepArgs &a, const Problem &P, const double 
             e_drop += wgt * gg;
         }
     }
-    if (stored) atomicAdd(&bs.c[sp][cPhoton], (unsigned long long)stored);
-    if (dropped) {
-        atomicAdd(&bs.c[sp][cPhotonDrop], (unsigned long long)dropped);
-        atomicAdd(&bs.e[sp][1], e_drop);
+    warp_add(&bs.c[sp][cPhoton], (unsigned)stored);
+    if (__any_sync(0xFFFFFFFFu, dropped != 0)) {
+        warp_add(&bs.c[sp][cPhotonDrop], (unsigned)dropped);
+        warp_add(&bs.e[sp][1], e_drop);
     }
 }
 
@@ -654,7 +667,7 @@ template <int PREC, int FK, typename R>
 __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned long long *bar, bool &loaded, unsigned chain_tile, int64_t n,
                            unsigned epoch, int *s_warp, BlockStats &bs, double *st,
-                           unsigned char *s_cnt, int *s_loc)
+                           unsigned short *s_map)
 {
     const int tid = threadIdx.x;
     const SpeciesDev &Ph = P.sp[2];
@@ -831,53 +844,53 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         st[8 * kTile + tid] = omv;
         st[9 * kTile + tid] = tm;
         st[10 * kTile + tid] = tp;
+        s_map[local] = (unsigned short)tid;
     }
-    s_cnt[tid] = (unsigned char)npair;
-    s_loc[tid] = local;
     return tile_total;
 }
 
-// The e-/e+ pairs of a stashed photon tile: pair number excl + (offset) goes
-// to slots be + that and bp + that while it is below `room`; beyond it the
-// pair is dropped and its energy counted.
-__device__ void write_pairs(const Problem &P, const double *st, const unsigned char *s_cnt,
-                            const int *s_loc, long long excl, long long be, long long bp,
-                            long long room, BlockStats &bs)
+// The e-/e+ pairs of a stashed photon tile, one thread per pair: pair number
+// excl + j goes to slots be + that and bp + that while it is below `room`;
+// beyond it the pair is dropped and its energy counted.
+__device__ void write_pairs(const Problem &P, const double *st, const unsigned short *s_map,
+                            int total, long long excl, long long be, long long bp, long long room,
+                            BlockStats &bs)
 {
-    const int tid = threadIdx.x;
-    if (!s_cnt[tid]) return;
     const SpeciesDev &El = P.sp[0], &Po = P.sp[1];
     const bool leptons = El.present && Po.present;
-    const double px = st[0 * kTile + tid], py = st[1 * kTile + tid], pz = st[2 * kTile + tid];
-    const double gux = st[3 * kTile + tid], guy = st[4 * kTile + tid], guz = st[5 * kTile + tid];
-    const double wg = st[6 * kTile + tid];
-    const int64_t ord = excl + s_loc[tid];
-    if (leptons && ord < room) {
-        const double v = st[7 * kTile + tid], om = st[8 * kTile + tid];
-        const int64_t se = be + ord, spo = bp + ord;
-        El.x[se] = px;
-        El.y[se] = py;
-        if (El.z) El.z[se] = pz;
-        El.ux[se] = v * gux;
-        El.uy[se] = v * guy;
-        El.uz[se] = v * guz;
-        El.tau[se] = st[9 * kTile + tid];
-        El.w[se] = wg;
-        if (El.chi) El.chi[se] = 0.0;
-        if (El.nemit) El.nemit[se] = 0;
-        Po.x[spo] = px;
-        Po.y[spo] = py;
-        if (Po.z) Po.z[spo] = pz;
-        Po.ux[spo] = om * gux;
-        Po.uy[spo] = om * guy;
-        Po.uz[spo] = om * guz;
-        Po.tau[spo] = st[10 * kTile + tid];
-        Po.w[spo] = wg;
-        if (Po.chi) Po.chi[spo] = 0.0;
-        if (Po.nemit) Po.nemit[spo] = 0;
-    } else {
-        atomicAdd(&bs.c[2][cPairDrop], 1ull);
-        atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
+    for (int j = threadIdx.x; j < total; j += kTile) {
+        const int e = (int)(s_map[j] & 0xFFu);
+        const double px = st[0 * kTile + e], py = st[1 * kTile + e], pz = st[2 * kTile + e];
+        const double gux = st[3 * kTile + e], guy = st[4 * kTile + e], guz = st[5 * kTile + e];
+        const double wg = st[6 * kTile + e];
+        const int64_t ord = excl + j;
+        if (leptons && ord < room) {
+            const double v = st[7 * kTile + e], om = st[8 * kTile + e];
+            const int64_t se = be + ord, spo = bp + ord;
+            El.x[se] = px;
+            El.y[se] = py;
+            if (El.z) El.z[se] = pz;
+            El.ux[se] = v * gux;
+            El.uy[se] = v * guy;
+            El.uz[se] = v * guz;
+            El.tau[se] = st[9 * kTile + e];
+            El.w[se] = wg;
+            if (El.chi) El.chi[se] = 0.0;
+            if (El.nemit) El.nemit[se] = 0;
+            Po.x[spo] = px;
+            Po.y[spo] = py;
+            if (Po.z) Po.z[spo] = pz;
+            Po.ux[spo] = om * gux;
+            Po.uy[spo] = om * guy;
+            Po.uz[spo] = om * guz;
+            Po.tau[spo] = st[10 * kTile + e];
+            Po.w[spo] = wg;
+            if (Po.chi) Po.chi[spo] = 0.0;
+            if (Po.nemit) Po.nemit[spo] = 0;
+        } else {
+            atomicAdd(&bs.c[2][cPairDrop], 1u);
+            atomicAdd(&bs.e[2][1], wg * sqrt(gux * gux + guy * guy + guz * guz));
+        }
     }
 }
 
@@ -952,28 +965,24 @@ __device__ void scan_offsets(long long *v, int n, long long *s_tmp)
     __syncthreads();
 }
 
-// The tile whose appends are stashed and not yet written (one per block).
+// A tile whose appends are stashed and not yet written (a ring of
+// kStashBufs per block; the record of tile number q of the block sits at
+// q % kStashBufs, beside its stash buffer and append map).
 struct Pending {
-    int valid, chain, last, sp, buf, total;
+    int chain, last, sp, total;
     unsigned tile;
     long long base, be, bp, room;
 };
 
-// Resolve the pending tile's prefix (its predecessors are, by now, almost
+// Resolve a stashed tile's prefix (its predecessors are, by now, almost
 // always published) and write its photons or pairs; the last tile of a
 // chain also sets the new live count applied at the end of the launch.
-// All threads of the block; uniform on the shared record.
+// All threads of the block; the record was written before a barrier.
 // (not inlined: its registers stay out of the physics of the tile loop)
-__device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, Pending &pd,
+__device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, const Pending &pd,
                                            unsigned epoch, long long *s_excl, BlockStats &bs,
-                                           const double *stash_block,
-                                           unsigned char (*s_cnt)[kTile], int (*s_loc)[kTile])
+                                           const double *st, const unsigned short *s_map)
 {
-    // every thread reads the record before any thread may change it (the
-    // caller's thread 0 records the next pending tile right after the call)
-    const bool valid = pd.valid != 0;
-    __syncthreads();
-    if (!valid) return;
     if (threadIdx.x < 32) {
         const long long e = resolve_prefix(pd.chain ? P.pho_words : P.lep_words, pd.tile,
                                            pd.total, epoch, a.spin_limit, a.status);
@@ -981,7 +990,6 @@ __device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, 
     }
     __syncthreads();
     const long long excl = *s_excl;
-    const double *st = stash_block + (size_t)pd.buf * kStashFields * kTile;
     if (pd.chain == 0) {
         if (pd.last && threadIdx.x == 0) {
             const long long tot = pd.base + excl + pd.total;
@@ -992,7 +1000,7 @@ __device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, 
                 raise_status(a.status, QP_WARN_BUFFER_FULL);
             }
         }
-        if (pd.total) write_photons(a, P, st, s_cnt[pd.buf], s_loc[pd.buf], pd.base + excl, pd.sp, bs);
+        if (pd.total) write_photons(P, st, s_map, pd.total, pd.base + excl, pd.sp, bs);
     } else {
         if (pd.last && threadIdx.x == 0) {
             const long long tot = excl + pd.total;
@@ -1001,11 +1009,9 @@ __device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, 
             P.pending[1] = pd.bp + add;
             if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
         }
-        if (pd.total)
-            write_pairs(P, st, s_cnt[pd.buf], s_loc[pd.buf], excl, pd.be, pd.bp, pd.room, bs);
+        if (pd.total) write_pairs(P, st, s_map, pd.total, excl, pd.be, pd.bp, pd.room, bs);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) pd.valid = 0;
+    // the record, map, stash buffer and s_excl are free for reuse after this
     __syncthreads();
 }
 
@@ -1014,12 +1020,14 @@ __device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, 
 // the current tile runs when more tiles than blocks remain); tickets enumerate, problem after problem, its
 // electron tiles, positron tiles and photon tiles, so within each problem's
 // chains start order is tile order and the decoupled look-back only ever
-// waits on tiles that are running.  A tile's appends are written one tile
-// later: its aggregate is published right after its physics, its records go
-// to a stash, and its prefix is resolved after the block's next tile, when
-// the earlier tiles have almost always published, so blocks do not wait on
-// one another tile after tile (the smallest unpublished tile always
-// progresses: every wait is for smaller tiles).  BATCH = false: the single problem of the
+// waits on tiles that are running.  A tile's appends are written
+// kStashBufs - 1 tiles later: its aggregate is published right after its
+// physics, its records go to a stash, and its prefix is resolved after the
+// block's next two tiles, when the earlier tiles have almost always
+// published, so blocks do not wait on one another tile after tile (the
+// smallest unpublished tile always progresses: every wait is for smaller
+// tiles, and a block holds its next ticket only while it runs physics or
+// flushes tiles older than that ticket).  BATCH = false: the single problem of the
 // launch parameters (read in place, from the constant bank); BATCH = true: a
 // device table of problems, each copied to shared memory for its tiles, with
 // time and step counters advanced on the device.
@@ -1043,9 +1051,8 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     __shared__ int s_tl[kMaxProblems], s_tg[kMaxProblems];
     __shared__ ProbCounts s_pc;
     __shared__ int s_last;
-    __shared__ Pending s_pend;
-    __shared__ unsigned char s_cnt[2][kTile];
-    __shared__ int s_loc[2][kTile];
+    __shared__ Pending s_pq[kStashBufs];
+    __shared__ unsigned short s_map[kStashBufs][kMapEntries];
 
     const int tid = threadIdx.x;
     // the first ticket is taken at entry: its atomic overlaps the reads of
@@ -1056,8 +1063,16 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
     clear_stats(bs);
-    if (tid == 0) s_pend.valid = 0;
-    const double *stash_block = a.stash + (size_t)blockIdx.x * 2 * kStashFields * kTile;
+    double *const stash_block = a.stash + (size_t)blockIdx.x * kStashBufs * kStashFields * kTile;
+    // tiles of this block with stashed appends: numbers q_lo..q-1 are not
+    // yet written (uniform over the block)
+    unsigned q = 0, q_lo = 0;
+    auto flush_oldest = [&](const Problem &P) {
+        const int ob = (int)(q_lo % kStashBufs);
+        flush_pending(a, P, s_pq[ob], epoch, &s_excl, bs,
+                      stash_block + (size_t)ob * kStashFields * kTile, s_map[ob]);
+        ++q_lo;
+    };
 
     // tiles of every problem, and the ticket offset of each
     bool bad = false;
@@ -1098,8 +1113,7 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
                 b = lo;
                 if (b != cur) {
                     if (cur >= 0) {
-                        flush_pending(a, s_prob, s_pend, epoch, &s_excl, bs, stash_block, s_cnt,
-                                      s_loc);
+                        while (q_lo != q) flush_oldest(s_prob);
                         flush_stats(bs, a, s_prob);
                         __syncthreads();
                         clear_stats(bs);
@@ -1121,25 +1135,25 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
             const Problem &P = BATCH ? s_prob : a.single;
             const ProbCounts pc = s_pc;                         // in registers for the tile
             const long long lt = t - (b > 0 ? s_off[b - 1] : 0);  // tile within the problem
-            const int sb = s_pend.valid ? (s_pend.buf ^ 1) : 0;  // stash buffer of this tile
-            double *st = const_cast<double *>(stash_block) + (size_t)sb * kStashFields * kTile;
+            // this tile's stash buffer, append map and record: the oldest
+            // pending tile is at most kStashBufs - 1 numbers back
+            const int sb = (int)(q % kStashBufs);
+            double *st = stash_block + (size_t)sb * kStashFields * kTile;
+            bool stashed = true;
             if (lt < pc.tiles_l) {
                 const int sp = lt < pc.tiles_e ? 0 : 1;
                 const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
                 const int total =
                     lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp,
-                                             first, pc.n[sp], epoch, s_warp, bs, st, s_cnt[sb],
-                                             s_loc[sb]);
-                flush_pending(a, P, s_pend, epoch, &s_excl, bs, stash_block, s_cnt, s_loc);
+                                             first, pc.n[sp], epoch, s_warp, bs, st, s_map[sb]);
                 if (tid == 0) {
-                    s_pend.valid = 1;
-                    s_pend.chain = 0;
-                    s_pend.last = lt == pc.tiles_l - 1;
-                    s_pend.sp = sp;
-                    s_pend.buf = sb;
-                    s_pend.total = total;
-                    s_pend.tile = (unsigned)lt;
-                    s_pend.base = pc.n[2];
+                    Pending &r = s_pq[sb];
+                    r.chain = 0;
+                    r.last = lt == pc.tiles_l - 1;
+                    r.sp = sp;
+                    r.total = total;
+                    r.tile = (unsigned)lt;
+                    r.base = pc.n[2];
                 }
             } else {
                 const unsigned pt = (unsigned)(lt - pc.tiles_l);
@@ -1152,29 +1166,30 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
                 }
                 const int total =
                     photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], epoch,
-                                             s_warp, bs, st, s_cnt[sb], s_loc[sb]);
-                flush_pending(a, P, s_pend, epoch, &s_excl, bs, stash_block, s_cnt, s_loc);
-                if (tid == 0 && P.pairs) {
-                    s_pend.valid = 1;
-                    s_pend.chain = 1;
-                    s_pend.last = (long long)pt == pc.tiles_g - 1;
-                    s_pend.sp = 2;
-                    s_pend.buf = sb;
-                    s_pend.total = total;
-                    s_pend.tile = pt;
-                    s_pend.be = be;
-                    s_pend.bp = bp;
-                    s_pend.room = room;
+                                             s_warp, bs, st, s_map[sb]);
+                stashed = P.pairs != 0;  // without pairs a photon tile appends nothing
+                if (tid == 0 && stashed) {
+                    Pending &r = s_pq[sb];
+                    r.chain = 1;
+                    r.last = (long long)pt == pc.tiles_g - 1;
+                    r.sp = 2;
+                    r.total = total;
+                    r.tile = pt;
+                    r.be = be;
+                    r.bp = bp;
+                    r.room = room;
                 }
             }
             if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
-            __syncthreads();
+            __syncthreads();  // the record and the next ticket are visible
+            if (stashed) ++q;
+            if (q - q_lo == (unsigned)kStashBufs) flush_oldest(P);
         }
     }
     if (cur >= 0) {
-        flush_pending(a, BATCH ? s_prob : a.single, s_pend, epoch, &s_excl, bs, stash_block, s_cnt,
-                      s_loc);
-        flush_stats(bs, a, BATCH ? s_prob : a.single);
+        const Problem &P = BATCH ? s_prob : a.single;
+        while (q_lo != q) flush_oldest(P);
+        flush_stats(bs, a, P);
     }
 
     // ---- the last block to finish publishes the step of every problem
