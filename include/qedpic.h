@@ -71,6 +71,7 @@ enum {
 };
 #define QP_MAX_EMISSIONS 8  /* upper bound of qp_step_params.max_emissions     */
 #define QP_MAX_BATCH 64     /* problems (independent runs) per batch            */
+#define QP_STEP_TILE 128    /* slots per tile of qp_step (one look-back word)   */
 #define QP_HIST_BINS 64     /* diagnostic spectrum bins in log10(gamma)        */
 #define QP_HIST_LOG10_MIN (-1.0)
 #define QP_HIST_LOG10_MAX (5.0)
@@ -233,7 +234,8 @@ int qp_batch_create(qp_ctx *ctx, int32_t max_problems, int32_t precision, int32_
 int qp_batch_destroy(qp_batch *b);
 
 /* Look-back scratch a problem needs: 64-bit words, from the capacities of
- * the species named in s (one word per 128 slots of each chain, plus a few). */
+ * the species named in s (one word per QP_STEP_TILE slots of each chain,
+ * plus a few). */
 int qp_batch_scratch_words(qp_ctx *ctx, const qp_step_params *s, int64_t *words);
 
 /*

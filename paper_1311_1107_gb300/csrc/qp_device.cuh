@@ -10,7 +10,7 @@
 namespace qp {
 
 enum Prec { kFP64 = 0, kMixed = 1 };
-constexpr int kTile = 128;      // particles per step tile = threads per block
+constexpr int kTile = QP_STEP_TILE;  // particles per step tile = threads per block
 constexpr int kWarps = kTile / 32;
 constexpr int kDiagTile = 256;  // slots per block tile of the diagnostics
 
@@ -188,15 +188,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 {
+    // two rounds per iteration: a short loop body keeps the several inlined
+    // draws of the step kernel small in the instruction cache
+#pragma unroll 1
+    for (int r = 0; r < 10; r += 2) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
+        for (int h = 0; h < 2; ++h) {
+            const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+            const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+            c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
             k.x += 0x9E3779B9u;
             k.y += 0xBB67AE85u;
         }
-        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     }
     return c;
 }

@@ -230,32 +230,42 @@ __device__ __forceinline__ FracPair row_invert_f(const float2 *__restrict__ C,
 }
 
 // Inverse CDF of Eq. 7 (emission rows) or of the pair spectrum, linear
-// between the two chi rows around chi (same rule as the FP64 path).
+// between the two chi rows around chi (same rule as the FP64 path).  One
+// copy of the row inversion serves both rows (a loop of one or two).
 __device__ __forceinline__ FracPair sample_cdf_f(const float2 *__restrict__ rows,
                                                  const float2 *__restrict__ qrows,
                                                  const unsigned char *__restrict__ guide,
                                                  const float *__restrict__ En, float chi, df2 xi,
                                                  df2 eta, float ds, bool emission, bool &clamped)
 {
-    if (!(chi >= (float)kChiLo)) {
-        const FracPair r0 = row_invert_f(rows, qrows, guide, En, xi, eta, ds, emission);
-        if (!emission) return r0;
-        const float x = (chi / (float)kChiLo) * r0.x;
+    const bool below = !(chi >= (float)kChiLo);
+    int j = 0, nrow = 1;
+    float f = 0.0f;
+    if (below) {
+        j = 0;
+    } else if (chi >= (float)kChiHi) {
+        clamped = true;
+        j = kNCdf - 1;
+    } else {
+        j = grid_index32<2>(chi, f);
+        nrow = 2;
+    }
+    FracPair a{0.0f, 1.0f}, b{0.0f, 1.0f};
+#pragma unroll 1
+    for (int k = 0; k < nrow; ++k, ++j) {
+        const FracPair r = row_invert_f(rows + j * kNNode, qrows + j * kNNode,
+                                        guide + j * kGuideBuckets, En, xi, eta, ds, emission);
+        if (k == 0)
+            a = r;
+        else
+            b = r;
+    }
+    if (nrow == 2) return {a.x + f * (b.x - a.x), a.omx + f * (b.omx - a.omx)};
+    if (below && emission) {
+        const float x = (chi / (float)kChiLo) * a.x;
         return {x, 1.0f - x};
     }
-    if (chi >= (float)kChiHi) {
-        clamped = true;
-        const int o = (kNCdf - 1) * kNNode;
-        return row_invert_f(rows + o, qrows + o, guide + (kNCdf - 1) * kGuideBuckets, En, xi,
-                            eta, ds, emission);
-    }
-    float f;
-    const int j = grid_index32<2>(chi, f);
-    const FracPair a = row_invert_f(rows + j * kNNode, qrows + j * kNNode,
-                                    guide + j * kGuideBuckets, En, xi, eta, ds, emission);
-    const FracPair b = row_invert_f(rows + (j + 1) * kNNode, qrows + (j + 1) * kNNode,
-                                    guide + (j + 1) * kGuideBuckets, En, xi, eta, ds, emission);
-    return {a.x + f * (b.x - a.x), a.omx + f * (b.omx - a.omx)};
+    return a;
 }
 
 }  // namespace qp

@@ -27,6 +27,7 @@ QP_FP64, QP_MIXED = 0, 1
 QP_FIELD_NONE, QP_FIELD_PLANE, QP_FIELD_GAUSSIAN, QP_FIELD_YEE2D, QP_FIELD_UNIFORM_B = range(5)
 QP_MAX_EMISSIONS = 8
 QP_MAX_BATCH = 64
+QP_STEP_TILE = 128
 QP_HIST_BINS = 64
 QP_NRATE, QP_NCDF, QP_NNODE = 769, 97, 256
 

@@ -78,7 +78,7 @@ class Arena:
 
 
 def _tiles(n: int) -> int:
-    return (n + 127) // 128
+    return (n + Q.QP_STEP_TILE - 1) // Q.QP_STEP_TILE
 
 
 @dataclass

@@ -35,6 +35,13 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_binding_constants_match_the_header():
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(QP_\w+)\s+(-?\d+)\b", text))
+    for name in ("QP_MAX_EMISSIONS", "QP_MAX_BATCH", "QP_STEP_TILE"):
+        assert int(defs[name]) == getattr(Q, name), name
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True,
                          check=True).stdout
