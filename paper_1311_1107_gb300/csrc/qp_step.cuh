@@ -440,9 +440,6 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         // instructions; chi_e falls back to double-float where FP32 cancels
         const MixedConsts &m = P.mc;
         const double xd = S.x[i], yd = S.y[i], zd = S.z ? S.z[i] : 0.0;
-        x0 = xd;
-        y0 = yd;
-        z0 = zd;
         const double uxd = S.ux[i], uyd = S.uy[i], uzd = S.uz[i];
         const double taud = S.tau[i];
         Vec3<float> E, B;
@@ -536,11 +533,13 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                     gg = pmag;
                     keep = 0.0f;
                 }
-                if (n_emit == 0 && pmag > 0.0f) {
-                    const float ip = 1.0f / pmag;
-                    kx = f_to_d(ux * ip);
-                    ky = f_to_d(uy * ip);
-                    kz = f_to_d(uz * ip);
+                if (n_emit == 0) {
+                    // the photons' direction goes to the append record now
+                    // (fewer values live through the loop)
+                    const float ip = pmag > 0.0f ? 1.0f / pmag : 0.0f;
+                    st[3 * kTile + tid] = f_to_d(ux * ip);
+                    st[4 * kTile + tid] = f_to_d(uy * ip);
+                    st[5 * kTile + tid] = f_to_d(uz * ip);
                 }
                 ++n_emit;
                 if (gg > m.gmin) {
@@ -583,6 +582,12 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             S.tau[i] = add_fd(taud, -dtau_once);
         if (n_sub) e_sub = f_to_d(esub_f);
         if (nph || n_sub) wgt = S.w[i];
+        if (nph) {
+            st[0 * kTile + tid] = xd;
+            st[1 * kTile + tid] = yd;
+            st[2 * kTile + tid] = zd;
+            st[6 * kTile + tid] = wgt;
+        }
     }
     }
     if (active && n_emit && S.nemit) S.nemit[i] += n_emit;
@@ -608,7 +613,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     int tile_total;
     const int local = block_scan(nph, s_warp, &tile_total);
     if (tid == 0) publish_aggregate(P.lep_words, chain_tile, tile_total, epoch);
-    if (nph) {
+    if (PREC == kFP64 && nph) {
         st[0 * kTile + tid] = x0;
         st[1 * kTile + tid] = y0;
         st[2 * kTile + tid] = z0;
@@ -977,9 +982,10 @@ struct Pending {
 // Resolve a stashed tile's prefix (its predecessors are, by now, almost
 // always published) and write its photons or pairs; the last tile of a
 // chain also sets the new live count applied at the end of the launch.
-// All threads of the block; the record was written before a barrier.
-// (not inlined: its registers stay out of the physics of the tile loop)
-__device__ __noinline__ void flush_pending(const StepArgs &a, const Problem &P, const Pending &pd,
+// All threads of the block; the record was written before a barrier.  The
+// tile loop has one call site, after the physics of a tile (the registers
+// of the physics are free by then).
+__device__ __forceinline__ void flush_pending(const StepArgs &a, const Problem &P, const Pending &pd,
                                            unsigned epoch, long long *s_excl, BlockStats &bs,
                                            const double *st, const unsigned short *s_map)
 {
@@ -1067,12 +1073,6 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     // tiles of this block with stashed appends: numbers q_lo..q-1 are not
     // yet written (uniform over the block)
     unsigned q = 0, q_lo = 0;
-    auto flush_oldest = [&](const Problem &P) {
-        const int ob = (int)(q_lo % kStashBufs);
-        flush_pending(a, P, s_pq[ob], epoch, &s_excl, bs,
-                      stash_block + (size_t)ob * kStashFields * kTile, s_map[ob]);
-        ++q_lo;
-    };
 
     // tiles of every problem, and the ticket offset of each
     bool bad = false;
@@ -1091,105 +1091,109 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
 
     bool lep_loaded = false, ph_loaded = false;
     int cur = BATCH ? -1 : 0;
-    {
-        for (int buf = 0;; buf ^= 1) {
-            const long long t = s_ticket[buf];
-            if (t >= n_tickets) break;
-            // fetch the next ticket while this tile runs, when another tile is
-            // likely left for this block (else the atomic only adds contention)
-            const bool early = t + (long long)gridDim.x < n_tickets;
-            if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
-            int b = 0;
-            if (BATCH) {
-                // the problem of ticket t: the first b with s_off[b] > t
-                int lo = 0, hi = np - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_off[mid] > t)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
-                }
-                b = lo;
-                if (b != cur) {
-                    if (cur >= 0) {
-                        while (q_lo != q) flush_oldest(s_prob);
-                        flush_stats(bs, a, s_prob);
-                        __syncthreads();
-                        clear_stats(bs);
-                    }
-                    // copy the problem descriptor to shared memory
-                    const int *src = reinterpret_cast<const int *>(table + b);
-                    int *dst = reinterpret_cast<int *>(&s_prob);
-                    for (int k = tid; k < (int)(sizeof(Problem) / sizeof(int)); k += kTile)
-                        dst[k] = src[k];
-                    __syncthreads();
-                    if (tid == 0) {
-                        s_pc = problem_counts(s_prob);
-                        set_time(s_prob, *((volatile long long *)s_prob.step_ctr));
-                    }
-                    __syncthreads();
-                    cur = b;
-                }
+    for (int buf = 0;; buf ^= 1) {
+        const long long t = s_ticket[buf];
+        const bool more = t < n_tickets;
+        // fetch the next ticket while this tile runs, when another tile is
+        // likely left for this block (else the atomic only adds contention)
+        const bool early = t + (long long)gridDim.x < n_tickets;
+        if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        int b = 0;
+        if (BATCH && more) {
+            // the problem of ticket t: the first b with s_off[b] > t
+            int lo = 0, hi = np - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] > t)
+                    hi = mid;
+                else
+                    lo = mid + 1;
             }
-            const Problem &P = BATCH ? s_prob : a.single;
-            const ProbCounts pc = s_pc;                         // in registers for the tile
-            const long long lt = t - (b > 0 ? s_off[b - 1] : 0);  // tile within the problem
-            // this tile's stash buffer, append map and record: the oldest
-            // pending tile is at most kStashBufs - 1 numbers back
-            const int sb = (int)(q % kStashBufs);
-            double *st = stash_block + (size_t)sb * kStashFields * kTile;
-            bool stashed = true;
-            if (lt < pc.tiles_l) {
-                const int sp = lt < pc.tiles_e ? 0 : 1;
-                const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
-                const int total =
-                    lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp,
-                                             first, pc.n[sp], epoch, s_warp, bs, st, s_map[sb]);
-                if (tid == 0) {
-                    Pending &r = s_pq[sb];
-                    r.chain = 0;
-                    r.last = lt == pc.tiles_l - 1;
-                    r.sp = sp;
-                    r.total = total;
-                    r.tile = (unsigned)lt;
-                    r.base = pc.n[2];
-                }
-            } else {
-                const unsigned pt = (unsigned)(lt - pc.tiles_l);
-                const long long be = pc.n[0], bp = pc.n[1];
-                long long room = 0;
-                if (P.sp[0].present && P.sp[1].present) {
-                    room = P.sp[0].cap - be;
-                    if (P.sp[1].cap - bp < room) room = P.sp[1].cap - bp;
-                    if (room < 0) room = 0;
-                }
-                const int total =
-                    photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], epoch,
-                                             s_warp, bs, st, s_map[sb]);
-                stashed = P.pairs != 0;  // without pairs a photon tile appends nothing
-                if (tid == 0 && stashed) {
-                    Pending &r = s_pq[sb];
-                    r.chain = 1;
-                    r.last = (long long)pt == pc.tiles_g - 1;
-                    r.sp = 2;
-                    r.total = total;
-                    r.tile = pt;
-                    r.be = be;
-                    r.bp = bp;
-                    r.room = room;
-                }
-            }
-            if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
-            __syncthreads();  // the record and the next ticket are visible
-            if (stashed) ++q;
-            if (q - q_lo == (unsigned)kStashBufs) flush_oldest(P);
+            b = lo;
         }
-    }
-    if (cur >= 0) {
+        const bool leave = !more || (BATCH && b != cur);  // the current problem's last tile is done
+        // ---- stashed appends: the oldest tile when the ring is full, all of
+        // them when the block leaves its problem (the one flush site)
+        {
+            const Problem &F = BATCH ? s_prob : a.single;
+            while (q_lo != q && (leave || q - q_lo == (unsigned)kStashBufs)) {
+                const int ob = (int)(q_lo % kStashBufs);
+                flush_pending(a, F, s_pq[ob], epoch, &s_excl, bs,
+                              stash_block + (size_t)ob * kStashFields * kTile, s_map[ob]);
+                ++q_lo;
+            }
+            if (leave && cur >= 0) {
+                flush_stats(bs, a, F);
+                __syncthreads();
+                clear_stats(bs);
+            }
+        }
+        if (!more) break;
+        if (BATCH && b != cur) {
+            // copy the problem descriptor to shared memory
+            const int *src = reinterpret_cast<const int *>(table + b);
+            int *dst = reinterpret_cast<int *>(&s_prob);
+            for (int k = tid; k < (int)(sizeof(Problem) / sizeof(int)); k += kTile)
+                dst[k] = src[k];
+            __syncthreads();
+            if (tid == 0) {
+                s_pc = problem_counts(s_prob);
+                set_time(s_prob, *((volatile long long *)s_prob.step_ctr));
+            }
+            __syncthreads();
+            cur = b;
+        }
         const Problem &P = BATCH ? s_prob : a.single;
-        while (q_lo != q) flush_oldest(P);
-        flush_stats(bs, a, P);
+        const ProbCounts pc = s_pc;                         // in registers for the tile
+        const long long lt = t - (b > 0 ? s_off[b - 1] : 0);  // tile within the problem
+        // this tile's stash buffer, append map and record: the oldest
+        // pending tile is at most kStashBufs - 1 numbers back
+        const int sb = (int)(q % kStashBufs);
+        double *st = stash_block + (size_t)sb * kStashFields * kTile;
+        bool stashed = true;
+        if (lt < pc.tiles_l) {
+            const int sp = lt < pc.tiles_e ? 0 : 1;
+            const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
+            const int total =
+                lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp,
+                                         first, pc.n[sp], epoch, s_warp, bs, st, s_map[sb]);
+            if (tid == 0) {
+                Pending &r = s_pq[sb];
+                r.chain = 0;
+                r.last = lt == pc.tiles_l - 1;
+                r.sp = sp;
+                r.total = total;
+                r.tile = (unsigned)lt;
+                r.base = pc.n[2];
+            }
+        } else {
+            const unsigned pt = (unsigned)(lt - pc.tiles_l);
+            const long long be = pc.n[0], bp = pc.n[1];
+            long long room = 0;
+            if (P.sp[0].present && P.sp[1].present) {
+                room = P.sp[0].cap - be;
+                if (P.sp[1].cap - bp < room) room = P.sp[1].cap - bp;
+                if (room < 0) room = 0;
+            }
+            const int total =
+                photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], epoch,
+                                         s_warp, bs, st, s_map[sb]);
+            stashed = P.pairs != 0;  // without pairs a photon tile appends nothing
+            if (tid == 0 && stashed) {
+                Pending &r = s_pq[sb];
+                r.chain = 1;
+                r.last = (long long)pt == pc.tiles_g - 1;
+                r.sp = 2;
+                r.total = total;
+                r.tile = pt;
+                r.be = be;
+                r.bp = bp;
+                r.room = room;
+            }
+        }
+        if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        __syncthreads();  // the record and the next ticket are visible
+        if (stashed) ++q;
     }
 
     // ---- the last block to finish publishes the step of every problem
