@@ -22,9 +22,14 @@
 // rare cases: called, never inlined, so that the common path's code stays
 // short and carries no predicated-off FP64 instructions
 #define QP_HD_COLD __host__ __device__ inline __noinline__
+// frequent but repeated many times per particle: one called copy keeps the
+// step kernel's instruction footprint small (it measured faster than
+// inlining every call site)
+#define QP_HD_SHARED __host__ __device__ inline __noinline__
 #else
 #define QP_HD inline
 #define QP_HD_COLD inline
+#define QP_HD_SHARED inline
 #include <math.h>
 #include <string.h>
 #endif
@@ -347,7 +352,7 @@ QP_HD_COLD double add_fd_slow(double d, float f)
     return u2d((db & 0x8000000000000000ull) | (e << 52) | ((uint64_t)S & ((1ull << 52) - 1)));
 }
 
-QP_HD double add_fd(double d, float f)
+QP_HD_SHARED double add_fd(double d, float f)
 {
     const uint32_t fb = f2u(f);
     if ((fb << 1) == 0u) return d;  // f = +-0
