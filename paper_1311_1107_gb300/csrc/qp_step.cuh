@@ -1061,10 +1061,12 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
     __shared__ unsigned short s_map[kStashBufs][kMapEntries];
 
     const int tid = threadIdx.x;
-    // the first ticket is taken at entry: its atomic overlaps the reads of
-    // the live counts below (a block whose ticket is past the last tile
-    // leaves without work)
-    if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
+    // the first ticket of block b is b (all blocks of the grid are resident
+    // together: the grid is sized by the occupancy of the kernel, and a block
+    // that another stream's kernel delays only delays the tiles after its
+    // own); the later ones come from the atomic counter, offset by the grid.
+    // A block whose ticket is past the last tile leaves without work.
+    if (tid == 0) s_ticket[0] = blockIdx.x;
     const int np = BATCH ? a.n_problems : 1;
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
@@ -1097,7 +1099,7 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
         // fetch the next ticket while this tile runs, when another tile is
         // likely left for this block (else the atomic only adds contention)
         const bool early = t + (long long)gridDim.x < n_tickets;
-        if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        if (early && tid == 0) s_ticket[buf ^ 1] = gridDim.x + atomicAdd(&a.ctl->ticket, 1u);
         int b = 0;
         if (BATCH && more) {
             // the problem of ticket t: the first b with s_off[b] > t
@@ -1191,16 +1193,24 @@ __global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
                 r.room = room;
             }
         }
-        if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        if (!early && tid == 0) s_ticket[buf ^ 1] = gridDim.x + atomicAdd(&a.ctl->ticket, 1u);
         __syncthreads();  // the record and the next ticket are visible
         if (stashed) ++q;
     }
 
-    // ---- the last block to finish publishes the step of every problem
+    // ---- the last block to finish publishes the step of every problem:
+    // the last block of each group counts in `done`, the last of those is it
     if (tid == 0) {
         __threadfence();
-        const unsigned prev = atomicAdd(&a.ctl->done, 1u);
-        s_last = prev == gridDim.x - 1;
+        const unsigned g = blockIdx.x % kDoneGroups;
+        const unsigned in_group = (gridDim.x - 1 - g) / kDoneGroups + 1;
+        const unsigned groups = gridDim.x < kDoneGroups ? gridDim.x : kDoneGroups;
+        s_last = 0;
+        if (atomicAdd(&a.ctl->grp[g][0], 1u) == in_group - 1) {
+            a.ctl->grp[g][0] = 0u;  // every block of the group has counted
+            __threadfence();
+            s_last = atomicAdd(&a.ctl->done, 1u) == groups - 1;
+        }
     }
     __syncthreads();
     if (s_last) {
