@@ -296,6 +296,37 @@ __device__ __forceinline__ void yee_gather(const FieldDev &f, const int ix[2], c
                                       iy[hy] + 1 < ny);
         st[k].base = iy[hy] * nx + ix[hx];
     }
+    if (all_inside) {
+        // the common case: the 24 loads of the six components are issued
+        // together (one round trip to memory), then combined in the order
+        // of yee_interp
+        const int comp_st[6] = {1, 2, 0, 2, 1, 3};  // stencil of Ex Ey Ez Bx By Bz
+        float v[6][4];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float *p = f.yee[c] + st[comp_st[c]].base;
+            v[c][0] = __ldg(p);
+            v[c][1] = __ldg(p + 1);
+            v[c][2] = __ldg(p + nx);
+            v[c][3] = __ldg(p + nx + 1);
+        }
+        R out[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const YeeStencil<R> &q = st[comp_st[c]];
+            const R w00 = (R(1) - q.wx) * (R(1) - q.wy), w10 = q.wx * (R(1) - q.wy);
+            const R w01 = (R(1) - q.wx) * q.wy, w11 = q.wx * q.wy;
+            R acc = R(0);
+            acc += w00 * (R)v[c][0];
+            acc += w10 * (R)v[c][1];
+            acc += w01 * (R)v[c][2];
+            acc += w11 * (R)v[c][3];
+            out[c] = acc;
+        }
+        E = {out[0], out[1], out[2]};
+        B = {out[3], out[4], out[5]};
+        return;
+    }
     E.x = yee_interp<R>(f.yee[0], st[1], nx, ny);
     E.y = yee_interp<R>(f.yee[1], st[2], nx, ny);
     E.z = yee_interp<R>(f.yee[2], st[0], nx, ny);
