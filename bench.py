@@ -368,7 +368,7 @@ def serving_arm(args):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(w, n_sample: int, n_steps: int):
+def oracle_sample(w, n_sample: int, n_steps: int, photons_per_electron: int = 256):
     """Time the CPU oracle (single thread) on a bounded sample of the
     workload: n_sample electrons (evenly spaced slots, each with its own
     random stream) for n_steps steps."""
@@ -385,7 +385,7 @@ def oracle_sample(w, n_sample: int, n_steps: int):
                         n_all)
     el.tau[:len(idx)] = tau[idx]
     po = O.Species(len(idx) * 4 + 64, dims, track=False)
-    ph = O.Species(len(idx) * 256 + 64, dims, track=False)
+    ph = O.Species(len(idx) * photons_per_electron + 64, dims, track=False)
     O.tables()
     sim = O.Sim(oracle_field(w["field"]), w["params"], electrons=el, positrons=po, photons=ph)
     slots = 0
@@ -397,11 +397,25 @@ def oracle_sample(w, n_sample: int, n_steps: int):
     return slots, dt, len(idx)
 
 
+CPU_BASELINE_SECONDS = 18.0
+
+
 def cpu_baseline(w, args):
-    slots, dt, n = oracle_sample(w, 16384 if args.workload != "collision" else 4096,
-                                 min(args.steps, 200))
+    """The oracle on about CPU_BASELINE_SECONDS of the same workload: a short
+    calibration sample sets how many evenly spaced electrons the timed sample
+    steps (at most all of them, for the timed number of steps)."""
+    collision = args.workload == "collision"
+    ppe = 256 if collision else 16
+    steps = min(args.steps, 200)
+    slots_c, dt_c, _ = oracle_sample(w, 2048, min(steps, 20), ppe)
+    target = CPU_BASELINE_SECONDS * slots_c / max(dt_c, 1e-6)  # particle-steps
+    n_all = len(w["electrons"]["x"])
+    n = int(min(n_all, max(1024, target / steps)))
+    if n == n_all:  # every electron: more steps, up to the timed count
+        steps = int(min(args.steps, max(steps, target / n_all)))
+    slots, dt, n = oracle_sample(w, n, steps, ppe)
     return {"value": round(slots / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} electrons (evenly spaced slots) for {min(args.steps, 200)} steps "
+            "sample": f"{n} electrons (evenly spaced slots) for {steps} steps "
                       f"of the same workload, FP64 oracle, {dt:.1f} s"}
 
 
