@@ -247,53 +247,49 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind):
 
 def e2e(w, precision, steps, dev):
     """End to end through the public API with host buffers: every step copies
-    the live particles from pinned host memory to the device, runs qp_step,
-    and reads the new state and live counts back."""
+    the live particles and the live counts from pinned host memory to the
+    device (qp_species_copy: one strided copy per species), runs qp_step,
+    and reads the new counts and then the new state back."""
     import torch
 
     from paper_1311_1107_gb300 import qedpic as Q
-    from paper_1311_1107_gb300.sim import Simulation
+    from paper_1311_1107_gb300.sim import Simulation, stream_handle
     from paper_1311_1107_gb300.workloads import LAMBDA_M
 
     ctx = Q.qp_init_tables(LAMBDA_M, dev)
     sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False)
     names = ("electron", "positron", "photon")
-    host = {}
-    for n in names:
-        sp = sim.species[n]
-        host[n] = {k: torch.empty(max(sp.cap, 1), dtype=torch.float64, pin_memory=True)
-                   for k in sp.t}
+    host = {n: torch.empty(sim.species[n].block.shape, dtype=torch.float64, pin_memory=True)
+            for n in names}
     counts_h = torch.empty(3, dtype=torch.int64, pin_memory=True)
-    live = {n: sim.species[n].count() for n in names}
+    stream = torch.cuda.current_stream()
+    st = stream_handle(stream)
+    counts_h.copy_(sim.counts)
+    live = dict(zip(names, (int(v) for v in counts_h.tolist())))
     for n in names:
-        for k, t in sim.species[n].t.items():
-            host[n][k][:live[n]].copy_(t[:live[n]])
+        sim.species[n].copy_state(host[n], live[n], False, st)
     torch.cuda.synchronize()
     h2d = d2h = 0
     total_slots = 0
     t0 = time.perf_counter()
     for _ in range(steps):
         for n in names:
-            sp = sim.species[n]
-            m = live[n]
-            for k, t in sp.t.items():
-                if m:
-                    t[:m].copy_(host[n][k][:m], non_blocking=True)
-                    h2d += m * 8
-            sp.n_live.fill_(m)
+            if live[n]:
+                sim.species[n].copy_state(host[n], live[n], True, st)
+                h2d += live[n] * 8 * host[n].shape[0]
+        sim.counts.copy_(counts_h, non_blocking=True)
+        h2d += 24
         total_slots += sum(live.values())
-        sim.run(1)
-        counts_h.copy_(torch.cat([sim.species[n].n_live for n in names]))
+        sim.run(1, stream)
+        counts_h.copy_(sim.counts, non_blocking=True)
         d2h += 24
+        stream.synchronize()
         live = dict(zip(names, (int(v) for v in counts_h.tolist())))
         for n in names:
-            sp = sim.species[n]
-            m = live[n]
-            for k, t in sp.t.items():
-                if m:
-                    host[n][k][:m].copy_(t[:m], non_blocking=True)
-                    d2h += m * 8
-        torch.cuda.synchronize()
+            if live[n]:
+                sim.species[n].copy_state(host[n], live[n], False, st)
+                d2h += live[n] * 8 * host[n].shape[0]
+        stream.synchronize()
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     Q.qp_destroy(ctx)

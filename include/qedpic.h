@@ -144,6 +144,20 @@ int qp_create_species(qp_ctx *ctx, const qp_species_desc *d, int32_t *out_handle
 int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t first,
                           int64_t count, void *stream);
 
+/*
+ * Copy slots [0, count) of a species' FP64 state between its device arrays
+ * and a host block: array k of (x, y, [z if dims == 3], ux, uy, uz, tau, w)
+ * starts at byte k * host_pitch of `host` (host_pitch >= 8 count, a
+ * multiple of 8).  to_device != 0 copies host -> device, else device ->
+ * host.  Asynchronous on `stream` (pinned host memory lets it overlap); one
+ * strided copy when the device arrays lie at a constant pitch in that order,
+ * else one copy per array.  The live count is not touched.  Returns
+ * QP_ERR_INVALID_ARG for a null host pointer, a count outside [0, capacity]
+ * or a pitch too small.  No counterpart in the paper: host I/O of the state.
+ */
+int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch, int64_t count,
+                    int32_t to_device, void *stream);
+
 /* ---- qp_step ----------------------------------------------------------- */
 typedef struct {
     int32_t kind;         /* QP_FIELD_*                                         */

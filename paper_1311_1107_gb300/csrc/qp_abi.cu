@@ -390,6 +390,49 @@ int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t fi
                                            (cudaStream_t)stream));
 }
 
+int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch, int64_t count,
+                    int32_t to_device, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &d = ctx->species[handle].d;
+    if (!host || count < 0 || count > d.capacity || host_pitch < 8 * count || host_pitch % 8)
+        return QP_ERR_INVALID_ARG;
+    if (count == 0) return QP_OK;
+    double *arr[8];
+    int na = 0;
+    arr[na++] = d.x;
+    arr[na++] = d.y;
+    if (d.dims == 3) arr[na++] = d.z;
+    arr[na++] = d.ux;
+    arr[na++] = d.uy;
+    arr[na++] = d.uz;
+    arr[na++] = d.tau;
+    arr[na++] = d.w;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t width = (size_t)count * sizeof(double);
+    // device arrays at a constant pitch (one allocation): one strided copy
+    const ptrdiff_t dpitch = (char *)arr[1] - (char *)arr[0];
+    bool strided = dpitch >= (ptrdiff_t)width;
+    for (int k = 2; k < na && strided; ++k) strided = (char *)arr[k] - (char *)arr[k - 1] == dpitch;
+    cudaError_t e = cudaSuccess;
+    if (strided) {
+        e = to_device ? cudaMemcpy2DAsync(arr[0], (size_t)dpitch, host, (size_t)host_pitch, width,
+                                          (size_t)na, cudaMemcpyHostToDevice, st)
+                      : cudaMemcpy2DAsync(host, (size_t)host_pitch, arr[0], (size_t)dpitch, width,
+                                          (size_t)na, cudaMemcpyDeviceToHost, st);
+    } else {
+        for (int k = 0; k < na && e == cudaSuccess; ++k) {
+            char *h = (char *)host + (size_t)k * (size_t)host_pitch;
+            e = to_device ? cudaMemcpyAsync(arr[k], h, width, cudaMemcpyHostToDevice, st)
+                          : cudaMemcpyAsync(h, arr[k], width, cudaMemcpyDeviceToHost, st);
+        }
+    }
+    return cuda_status(e);
+}
+
 namespace {
 
 // Checks of a step description (everything but the species' precision and

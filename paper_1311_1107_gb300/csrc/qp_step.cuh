@@ -1037,10 +1037,20 @@ __device__ __forceinline__ void flush_pending(const StepArgs &a, const Problem &
 // launch parameters (read in place, from the constant bank); BATCH = true: a
 // device table of problems, each copied to shared memory for its tiles, with
 // time and step counters advanced on the device.
-// FP64: 4 blocks of 128 per SM (128 registers, no spills); mixed: 8 blocks
-// (64 registers; the few spills cost less than the extra resident warps gain)
+// Resident blocks of 128 per SM.  FP64: 4 (128 registers, no spills).
+// Mixed: 8 (64 registers; the few spills cost less than the extra resident
+// warps gain), except with the Yee grid: 7 (73 registers), where the 24
+// loads of the gather are in flight together and spill at 64 (measured on
+// the 2D foil: 30.4 us per step at 7, 32.7 at 8; the analytic-field
+// collision: 366 us at 7, 356 at 8).
+template <int PREC, int FK>
+constexpr int step_min_blocks()
+{
+    return PREC == kFP64 ? 4 : (FK == QP_FIELD_YEE2D ? 7 : 8);
+}
+
 template <int PREC, int FK, bool BATCH>
-__global__ void __launch_bounds__(kTile, PREC == kFP64 ? 4 : 8)
+__global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     k_step(const __grid_constant__ StepArgs a)
 {
     using R = typename std::conditional<PREC == kFP64, double, float>::type;

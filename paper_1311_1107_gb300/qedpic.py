@@ -98,6 +98,7 @@ _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
+           "qp_species_copy",
            "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
            "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
@@ -127,6 +128,7 @@ def lib(build_if_missing: bool = False):
         L.qp_destroy.argtypes = [vp]
         L.qp_create_species.argtypes = [vp, C.POINTER(qp_species_desc), C.POINTER(i32)]
         L.qp_init_optical_depth.argtypes = [vp, i32, C.c_uint64, i64, i64, vp]
+        L.qp_species_copy.argtypes = [vp, i32, vp, i64, i64, i32, vp]
         L.qp_step.argtypes = [vp, C.POINTER(qp_step_params), vp]
         L.qp_diagnostics.argtypes = [vp, i32, C.POINTER(qp_diag), vp]
         L.qp_diagnostics_noalloc.argtypes = [C.POINTER(qp_species_desc), C.POINTER(qp_diag), vp]
@@ -184,6 +186,15 @@ def qp_create_species(ctx, desc: qp_species_desc) -> int:
 def qp_init_optical_depth(ctx, handle: int, seed: int, first: int, count: int, stream=None):
     return _check("qp_init_optical_depth",
                   lib().qp_init_optical_depth(ctx, handle, seed, first, count, stream))
+
+
+def qp_species_copy(ctx, handle: int, host_ptr: int, host_pitch: int, count: int,
+                    to_device: bool, stream=None):
+    """Slots [0, count) of the FP64 state between the device arrays and a host
+    block (array k at host_ptr + k * host_pitch bytes)."""
+    return _check("qp_species_copy",
+                  lib().qp_species_copy(ctx, handle, host_ptr, host_pitch, count,
+                                        1 if to_device else 0, stream))
 
 
 def qp_step(ctx, params: qp_step_params, stream=None) -> int:

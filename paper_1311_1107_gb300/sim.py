@@ -33,14 +33,20 @@ class DeviceSpecies:
     """FP64 SoA buffers of one species on the GPU, registered with a context."""
 
     def __init__(self, ctx, kind: int, capacity: int, dims: int = 3, device="cuda:0",
-                 track_chi: bool = True, id_base: int = 0):
+                 track_chi: bool = True, id_base: int = 0, n_live=None):
+        """n_live: a one-element int64 device tensor to hold the live count
+        (a view of a shared tensor lets a caller move all counts at once)."""
         self.kind, self.cap, self.dims = kind, int(capacity), dims
         n = max(self.cap, 1)
-        self.t = {nm: torch.zeros(n, dtype=torch.float64, device=device)
-                  for nm in NAMES if not (nm == "z" and dims == 2)}
+        names = [nm for nm in NAMES if not (nm == "z" and dims == 2)]
+        # one allocation, array k at row k: the host copies of the state
+        # (qp_species_copy) move every array of a species in one strided copy
+        self.block = torch.zeros((len(names), n), dtype=torch.float64, device=device)
+        self.t = {nm: self.block[k] for k, nm in enumerate(names)}
         self.chi = torch.zeros(n, dtype=torch.float64, device=device) if track_chi else None
         self.nemit = torch.zeros(n, dtype=torch.int32, device=device) if track_chi else None
-        self.n_live = torch.zeros(1, dtype=torch.int64, device=device)
+        self.n_live = (n_live if n_live is not None
+                       else torch.zeros(1, dtype=torch.int64, device=device))
         d = Q.qp_species_desc()
         d.kind, d.dims, d.capacity = kind, dims, self.cap
         for nm in NAMES:
@@ -50,6 +56,7 @@ class DeviceSpecies:
         d.n_live = _ptr(self.n_live)
         d.id_base = int(id_base)
         self._desc = d
+        self.ctx = ctx
         self.handle = Q.qp_create_species(ctx, d)
 
     def load(self, arrays: dict, n: int | None = None):
@@ -63,6 +70,12 @@ class DeviceSpecies:
             if nm in arrays and n:
                 t[:n].copy_(torch.as_tensor(np.asarray(arrays[nm][:n], dtype=np.float64)))
         self.n_live.fill_(n)
+
+    def copy_state(self, host: torch.Tensor, count: int, to_device: bool, stream=None):
+        """Slots [0, count) of the FP64 arrays between the device and a host
+        tensor shaped like self.block (pinned for asynchronous copies)."""
+        Q.qp_species_copy(self.ctx, self.handle, host.data_ptr(), host.stride(0) * 8, count,
+                          to_device, stream)
 
     def count(self) -> int:
         return int(self.n_live.item())
@@ -115,10 +128,13 @@ class Simulation:
         self.workload = workload
         dims = workload["dims"]
         cap = workload["capacity"]
+        # live counts of electrons, positrons, photons side by side
+        self.counts = torch.zeros(3, dtype=torch.int64, device=self.dev)
         self.species = {
             name: DeviceSpecies(self.ctx, KIND[name], cap[name], dims, self.dev, track_chi,
-                                id_base if name == "electron" else 0)
-            for name in ("electron", "positron", "photon")
+                                id_base if name == "electron" else 0,
+                                n_live=self.counts[k:k + 1])
+            for k, name in enumerate(("electron", "positron", "photon"))
         }
         self.field, self._keep = make_field(workload["field"], self.dev)
         p = workload["params"]

@@ -109,6 +109,7 @@ def test_arguments_rejected_before_any_device_work(lib):
     assert lib.qp_batch_clear(None, 0, None) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_batch_progress(None, None, None, None, None) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_batch_destroy(None) == Q.QP_ERR_NOT_INITIALIZED
+    assert lib.qp_species_copy(None, 0, None, 8, 1, 1, None) == Q.QP_ERR_NOT_INITIALIZED
 
 
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
