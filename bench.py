@@ -44,6 +44,7 @@ import numpy as np  # noqa: E402
 METRIC = "QED particle-steps/s, mixed vs FP64 on same GPU; p50/p99 request latency"
 UNIT = "particle-steps/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILES = os.path.join(ROOT, "profiles")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -226,10 +227,47 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, id_base=0):
     return res
 
 
-def roofline(res, dims, pairs, hbm_peak, peak_kind):
+def kernel_source_id() -> str:
+    """Hash of the sources and build flags the step kernel is compiled from
+    (the ncu summaries under profiles/ name the one they were taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_1107_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    for extra in (("include", "qedpic.h"), ("paper_1311_1107_gb300", "build.py")):
+        with open(os.path.join(ROOT, *extra), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(profile: str, precision: str):
+    """DRAM bytes (read, write) per k_step launch from the committed ncu
+    summary of the workload, when it was taken on the current kernel
+    sources; None otherwise (the counters no longer describe the kernel)."""
+    import re
+    path = os.path.join(PROFILES, profile)
+    if not os.path.exists(path):
+        return None
+    sid = kernel_source_id()
+    pat = re.compile(r"^traffic, (\w+): read (\d+) B, write (\d+) B per launch, "
+                     r"kernel source ([0-9a-f]{12})")
+    with open(path) as f:
+        for line in f:
+            m = pat.match(line.strip())
+            if m and m.group(1) == precision and m.group(4) == sid:
+                return int(m.group(2)), int(m.group(3))
+    return None
+
+
+def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
     """Roofline of k_step (the only kernel of a step): algorithmic bytes of
     all lepton and photon slot-steps and appended particles in the timed
-    steps, over the summed k_step device time (CUDA events on its stream)."""
+    steps, over the summed k_step device time (CUDA events on its stream).
+    traffic: (read, write) DRAM bytes per launch from an ncu capture of the
+    same command, or None."""
     lep_b, pho_b, new_b = species_bytes(dims, pairs)
     nbytes = (res["lep_slots"] * lep_b + res["pho_slots"] * pho_b
               + (res["photons_added"] + 2 * res["pairs_added"]) * new_b)
@@ -237,7 +275,9 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind):
     n = max(res["launches"][0], 1)
     achieved = nbytes / (t_ms * 1e-3) / 1e9
     return {"kernel": "k_step", "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
-            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+            "traffic": sum(traffic) if traffic else None,
+            "traffic_read_write": list(traffic) if traffic else None,
             "bytes_per_launch": round(nbytes / n), "avg_launch_us": round(t_ms * 1e3 / n, 3),
             "bytes_model": f"{lep_b} B per lepton slot-step, {pho_b} B per photon slot-step, "
                            f"{new_b} B per appended particle",
@@ -488,6 +528,8 @@ def ours_arm(args):
 
     v_mixed, t_mixed = agg(mixed)
     v_fp64, t_fp64 = agg(fp64)
+    profile = {"foil": "k_step_foil2d.md", "collision": "k_step_collision.md"}.get(
+        args.workload, "k_step_" + args.workload + ".md")
     line = None
     serv = None
     if rank == 0 and world == 1 and not args.no_serving:
@@ -513,10 +555,12 @@ def ours_arm(args):
                        "final_live": mixed["final_live"], "parallelism": f"shards x{world} (ids offset by rank, no exchange)"},
             "fp64": {"value": round(v_fp64, 1), "unit": UNIT,
                      "ms_per_step": round(t_fp64 / args.steps, 4), "dtype": "f64",
-                     "roofline": roofline(fp64, dims, pairs, hbm_peak, peak_kind),
+                     "roofline": roofline(fp64, dims, pairs, hbm_peak, peak_kind,
+                                          measured_traffic(profile, "fp64")),
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
                      "final_live": fp64["final_live"]},
-            "roofline": roofline(mixed, dims, pairs, hbm_peak, peak_kind),
+            "roofline": roofline(mixed, dims, pairs, hbm_peak, peak_kind,
+                                 measured_traffic(profile, "mixed")),
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
             "clocks": clk, "status": {"mixed": mixed["status"], "fp64": fp64["status"]},
         }
