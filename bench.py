@@ -444,7 +444,9 @@ def cpu_baseline(w, args):
     ppe = 256 if collision else 16
     steps = min(args.steps, 200)
     slots_c, dt_c, _ = oracle_sample(w, 2048, min(steps, 20), ppe)
-    target = CPU_BASELINE_SECONDS * slots_c / max(dt_c, 1e-6)  # particle-steps
+    # the collision's later steps (more photons) cost more than its first
+    seconds = CPU_BASELINE_SECONDS * (0.4 if collision else 1.0)
+    target = seconds * slots_c / max(dt_c, 1e-6)  # particle-steps
     n_all = len(w["electrons"]["x"])
     n = int(min(n_all, max(1024, target / steps)))
     if n == n_all:  # every electron: more steps, up to the timed count

@@ -68,9 +68,8 @@ struct MixedConsts {
     float nxf, nyf;                            // Yee grid size
 };
 
-// Device-resident control block of a launch sequence: the tile ticket (the
-// tiles after each block's first), the count of finished blocks and the
-// launch epoch that tags look-back words.  Blocks count their end in
+// Device-resident control block of a launch sequence: the tile ticket, the
+// count of finished blocks and the launch epoch that tags look-back words.  Blocks count their end in
 // kDoneGroups group counters (one 32-byte sector each) and the last of each
 // group in `done`: no counter sees more than a few tens of atomics at once.
 constexpr int kDoneGroups = 32;

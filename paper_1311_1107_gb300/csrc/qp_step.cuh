@@ -1071,12 +1071,14 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     __shared__ unsigned short s_map[kStashBufs][kMapEntries];
 
     const int tid = threadIdx.x;
-    // the first ticket of block b is b (all blocks of the grid are resident
-    // together: the grid is sized by the occupancy of the kernel, and a block
-    // that another stream's kernel delays only delays the tiles after its
-    // own); the later ones come from the atomic counter, offset by the grid.
-    // A block whose ticket is past the last tile leaves without work.
-    if (tid == 0) s_ticket[0] = blockIdx.x;
+    // the first ticket is taken at entry: its atomic overlaps the reads of
+    // the live counts below.  Every ticket comes from the counter, so a tile
+    // belongs to a block only once that block runs: a wait is always for a
+    // running block, even when kernels of other streams hold part of the
+    // GPU (a fixed first tile per block would let the running blocks wait
+    // for one that cannot start).  A block whose ticket is past the last
+    // tile leaves without work.
+    if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
     const int np = BATCH ? a.n_problems : 1;
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
@@ -1109,7 +1111,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
         // fetch the next ticket while this tile runs, when another tile is
         // likely left for this block (else the atomic only adds contention)
         const bool early = t + (long long)gridDim.x < n_tickets;
-        if (early && tid == 0) s_ticket[buf ^ 1] = gridDim.x + atomicAdd(&a.ctl->ticket, 1u);
+        if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
         int b = 0;
         if (BATCH && more) {
             // the problem of ticket t: the first b with s_off[b] > t
@@ -1203,7 +1205,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
                 r.room = room;
             }
         }
-        if (!early && tid == 0) s_ticket[buf ^ 1] = gridDim.x + atomicAdd(&a.ctl->ticket, 1u);
+        if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
         __syncthreads();  // the record and the next ticket are visible
         if (stashed) ++q;
     }
