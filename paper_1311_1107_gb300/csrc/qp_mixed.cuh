@@ -21,22 +21,26 @@ __device__ __forceinline__ float reduce_phase(df2 ph)
     return r.hi + r.lo;
 }
 
-// Fields at the double-float position (x, y, z) and time of the step.
+// Fields at the FP64 position (xd, yd, zd) and time of the step; each field
+// model converts the coordinates it needs to the precision it needs them in
+// (double-float where a phase or a cell index must resolve the position,
+// the nearest float elsewhere).
 template <int FK>
-__device__ __forceinline__ void eval_field_mixed(const FieldDev &f, const MixedConsts &m, df2 x,
-                                                 df2 y, df2 z, Vec3<float> &E, Vec3<float> &B)
+__device__ __forceinline__ void eval_field_mixed(const FieldDev &f, const MixedConsts &m,
+                                                 double xd, double yd, double zd,
+                                                 Vec3<float> &E, Vec3<float> &B)
 {
     E = {0.0f, 0.0f, 0.0f};
     B = {0.0f, 0.0f, 0.0f};
     if constexpr (FK == QP_FIELD_PLANE) {
         // E_y = B_z = a0 cos(t - x)
-        const float v = m.a0 * __cosf(reduce_phase(df_sub({m.t_hi, m.t_lo}, x)));
+        const float v = m.a0 * __cosf(reduce_phase(df_sub({m.t_hi, m.t_lo}, split_d(xd))));
         E.y = v;
         B.z = v;
     } else if constexpr (FK == QP_FIELD_GAUSSIAN) {
-        const df2 xi = df_sub(x, {m.xf_hi, m.xf_lo});
+        const df2 xi = df_sub(split_d(xd), {m.xf_hi, m.xf_lo});
         const df2 eta = df_sub({m.tr_hi, m.tr_lo}, xi);  // (t - t_f) - xi
-        const float xf = xi.hi, yf = df_to_f(y), zf = df_to_f(z);
+        const float xf = xi.hi, yf = hi_d(yd), zf = hi_d(zd);
         const float q = xf * m.inv_zr;
         const float wr2 = 1.0f + q * q;
         const float r2 = yf * yf + zf * zf;
@@ -51,8 +55,8 @@ __device__ __forceinline__ void eval_field_mixed(const FieldDev &f, const MixedC
         B.z = m.b0;
     } else if constexpr (FK == QP_FIELD_YEE2D) {
         // cell coordinates in double-float, then FP32 weights
-        const df2 gx = df_sub(df_mul(x, {m.idx_hi, m.idx_lo}), {m.x0s_hi, m.x0s_lo});
-        const df2 gy = df_sub(df_mul(y, {m.idy_hi, m.idy_lo}), {m.y0s_hi, m.y0s_lo});
+        const df2 gx = df_sub(df_mul(split_d(xd), {m.idx_hi, m.idx_lo}), {m.x0s_hi, m.x0s_lo});
+        const df2 gy = df_sub(df_mul(split_d(yd), {m.idy_hi, m.idy_lo}), {m.y0s_hi, m.y0s_lo});
         int ix[2], iy[2];
         float wx[2], wy[2];
 #pragma unroll
@@ -143,12 +147,6 @@ __device__ __forceinline__ float chi_mixed_auto(double u0x, double u0y, double u
 __device__ __forceinline__ float u53f(unsigned a, unsigned b)
 {
     return fmaf((float)(b >> 6) + 1.0f, 0x1.0p-26f, (float)(a >> 5)) * 0x1.0p-27f;
-}
-
-// 1 - u53 of the same bits, exactly: ((2^27-1-(a>>5)) 2^26 + (2^26-1-(b>>6))) 2^-53
-__device__ __forceinline__ float u53f_complement(unsigned a, unsigned b)
-{
-    return fmaf((float)((~b) >> 6), 0x1.0p-26f, (float)((~a) >> 5)) * 0x1.0p-27f;
 }
 
 // The same uniform and its complement 1 - u53 as unevaluated float pairs

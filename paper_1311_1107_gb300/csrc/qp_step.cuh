@@ -144,10 +144,6 @@ __device__ __forceinline__ int block_scan(int v, int *s_warp, int *total)
     return inc - v + (warp ? s_warp[warp - 1] : 0);
 }
 
-// Exact widening of a stashed value (FP32 values by integer instructions).
-__device__ __forceinline__ double to_double(double v) { return v; }
-__device__ __forceinline__ double to_double(float v) { return f_to_d(v); }
-
 // Counters kept in shared memory per block and species, flushed with one
 // atomic per counter when the block leaves.  The counts are 32-bit (shared
 // memory adds them natively; a block never counts 2^32 events in a launch),
@@ -443,7 +439,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         const double uxd = S.ux[i], uyd = S.uy[i], uzd = S.uz[i];
         const double taud = S.tau[i];
         Vec3<float> E, B;
-        eval_field_mixed<FK>(P.f, m, split_d(xd), split_d(yd), split_d(zd), E, B);
+        eval_field_mixed<FK>(P.f, m, xd, yd, zd, E, B);
 
         // Boris on the leading FP32 parts; the increment is kept in FP32
         const float u0x = hi_d(uxd), u0y = hi_d(uyd), u0z = hi_d(uzd);
@@ -786,7 +782,7 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             bool decayed = false;
             if (pairs && g > 2.0f) {
                 Vec3<float> E, B;
-                eval_field_mixed<FK>(P.f, m, split_d(px), split_d(py), split_d(pz), E, B);
+                eval_field_mixed<FK>(P.f, m, px, py, pz, E, B);
                 const float ig = 1.0f / g;
                 const float kx = fx * ig, ky = fy * ig, kz = fz * ig;
                 const float ax = E.x + (ky * B.z - kz * B.y);
