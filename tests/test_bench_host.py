@@ -1,0 +1,34 @@
+"""bench.py host logic (no GPU): the bytes model of the roofline and the
+rule that measured DRAM traffic is used only while the ncu summary names the
+current kernel sources."""
+import bench
+
+
+def test_bytes_model_per_unit():
+    # x, u, tau read and written; photons: read x, u, tau, write x (and tau
+    # with pairs); appended particle: its arrays plus the parent's weight
+    assert bench.species_bytes(3, True) == (112, 88, 64)
+    assert bench.species_bytes(2, True) == (96, 72, 56)
+    assert bench.species_bytes(3, False) == (112, 80, 64)
+
+
+def test_traffic_is_read_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
+    sid = bench.kernel_source_id()
+    assert len(sid) == 12 and int(sid, 16) >= 0
+    (tmp_path / "k_step_x.md").write_text(
+        "# summary\n\n"
+        f"traffic, mixed: read 1000 B, write 24 B per launch, kernel source {sid}\n"
+        "traffic, fp64: read 2000 B, write 8 B per launch, kernel source 000000000000\n")
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    assert bench.measured_traffic("k_step_x.md", "mixed") == (1000, 24)
+    assert bench.measured_traffic("k_step_x.md", "fp64") is None   # other sources
+    assert bench.measured_traffic("absent.md", "mixed") is None
+
+
+def test_roofline_reports_traffic_and_fraction():
+    res = {"lep_slots": 1000, "pho_slots": 0, "photons_added": 0, "pairs_added": 0,
+           "kernel_ms": [1e-3, 0.0, 0.0], "launches": [1, 0, 0]}
+    r = bench.roofline(res, 3, True, 100.0, "measured", (50, 10))
+    assert r["achieved"] == 112.0 and r["frac"] == 1.12  # 112 kB in 1 us
+    assert r["traffic"] == 60 and r["traffic_read_write"] == [50, 10]
+    assert bench.roofline(res, 3, True, 100.0, "measured")["traffic"] is None
