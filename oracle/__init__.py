@@ -124,8 +124,6 @@ def lib():
                                  i64, C.POINTER(_Species), C.POINTER(_Species),
                                  C.POINTER(_Species), C.POINTER(Stats)]),
             "or_init_tau": (None, [C.c_uint64, C.c_int, vp, i64, i64]),
-            "or_count_events_frozen": (i64, [C.POINTER(Units), vp, d, d, d, i64, C.c_uint64,
-                                             C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -412,7 +410,3 @@ class Sim:
             if s is not None:
                 s.n = st.n
         self.P.step += int(n_steps)
-
-    def count_events_frozen(self, chi, gam, dt, n_steps, seed, max_emit=8):
-        return lib().or_count_events_frozen(C.byref(self.U), self.T.ptr, float(chi), float(gam),
-                                            float(dt), int(n_steps), int(seed), int(max_emit))

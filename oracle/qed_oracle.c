@@ -1053,38 +1053,3 @@ int or_run(const or_units *U, const or_tables *T, const or_field *F, const or_pa
     }
     return 0;
 }
-
-/* Test hook: the optical-depth / emission sub-loop for a particle frozen at
- * a given chi and gamma (recoil off), counting events over n_steps; used to
- * check the event statistics against a Poisson law with mean W t. */
-int64_t or_count_events_frozen(const or_units *U, const or_tables *T, double chi, double gam,
-                               double dt, int64_t n_steps, uint64_t seed, int max_emit)
-{
-    uint32_t r[4];
-    or_draw(seed, OR_SP_ELECTRON, OR_RNG_INIT, 0, 0, 0, r);
-    double tau = -log(or_u53(r[0], r[1]));
-    int64_t events = 0;
-    int clamped = 0;
-    for (int64_t n = 0; n < n_steps; n++) {
-        double rr = 1.0;
-        for (int k = 0;; k++) {
-            double H = or_lookup_rate(T, 0, chi, &clamped);
-            double wdt = U->C_rate * H / gam * dt;
-            double dtau = wdt * rr;
-            if (!(dtau > 0.0) || tau > dtau) {
-                tau = tau - dtau;
-                break;
-            }
-            if (k == max_emit) {
-                tau = tau - dtau;
-                break;
-            }
-            rr = rr - tau / wdt;
-            uint32_t q[4];
-            or_draw(seed, OR_SP_ELECTRON, OR_RNG_EMIT, 0, n, k, q);
-            tau = -log(or_u53(q[2], q[3]));
-            events++;
-        }
-    }
-    return events;
-}

@@ -65,20 +65,68 @@ def test_emission_conserves_momentum_and_matches_recoil_energy_defect(units):
     assert events > 20
 
 
-@pytest.mark.parametrize("gam,dt", [(1000.0, 1e-3), (5.0, 2e-2)])
-def test_event_counts_are_poisson_with_mean_W_t(otables, units, gam, dt):
-    # frozen particle: counts over a time t follow Poisson(W t), W = C H / gamma;
-    # the second case has W dt > 1, exercising the residual-time sub-loop.
+@pytest.mark.parametrize("p0,wdt", [(1000.0, 0.05), (5.0, 3.0)])
+def test_event_counts_of_the_step_are_poisson_with_mean_W_t(otables, units, p0, wdt):
+    # Eq. 6 with the residual-time sub-loop, driven through the real step:
+    # electrons gyrating in a uniform B perpendicular to u with the recoil
+    # off keep |u| and chi fixed, so each one's emissions over a time t are
+    # Poisson(W t), W = C H(chi) / gamma.  The second case has W dt = 3: a
+    # wrong residual r of the sub-loop (never decremented, decremented by
+    # the optical depth instead of tau / (W dt), ...) changes the law.
     chi = 1.0
+    b0 = _b_for_chi(chi, p0, units)
+    gam = math.sqrt(1.0 + p0 * p0)
     H = otables.lookup(0, chi)[0]
     W = units.C_rate * H / gam
-    n_steps = int(round(25.0 / (W * dt)))
-    sim = O.Sim(O.plane_field(0), {"dt": dt})
-    counts = np.array([sim.count_events_frozen(chi, gam, dt, n_steps, seed, max_emit=64)
-                       for seed in range(300)])
+    dt = wdt / W
+    n, n_steps = 3000, 8 if wdt > 1 else 400
+    el = _species(n, n, (p0, 0, 0))
+    O.init_tau(21, O.ELECTRON, el)
+    sim = O.Sim(O.uniform_b_field(b0), _params(dt=dt, seed=21, recoil=0, max_emit=64),
+                electrons=el)
+    sim.run(n_steps)
+    # chi really stayed fixed (|u| conserved by the rotation)
+    pm = np.sqrt(el.ux[:n] ** 2 + el.uy[:n] ** 2 + el.uz[:n] ** 2)
+    np.testing.assert_allclose(pm, p0, rtol=1e-12)
+    np.testing.assert_allclose(el.chi[:n], chi, rtol=1e-10)
+    assert sim.stats.n_saturated == 0
+    counts = el.nemit[:n].astype(float)
+    assert counts.sum() == sim.stats.n_emit
     mean = W * dt * n_steps
-    assert counts.mean() == pytest.approx(mean, abs=4 * math.sqrt(mean / len(counts)))
-    assert counts.var() / counts.mean() == pytest.approx(1.0, abs=0.25)
+    assert counts.mean() == pytest.approx(mean, abs=4 * math.sqrt(mean / n))
+    assert counts.var() / counts.mean() == pytest.approx(1.0, abs=0.12)
+    # the whole distribution, by chi2 against the Poisson law
+    kmax = int(mean + 6 * math.sqrt(mean)) + 1
+    kk = np.arange(kmax + 1)
+    probs = st.poisson.pmf(kk, mean)
+    probs[-1] += st.poisson.sf(kmax, mean)
+    obs = np.bincount(np.minimum(counts.astype(int), kmax), minlength=kmax + 1)
+    keep = probs * n >= 5  # pool the sparse tails
+    e = np.append(probs[keep] * n, probs[~keep].sum() * n)
+    o = np.append(obs[keep], obs[~keep].sum())
+    chi2 = ((o - e) ** 2 / np.maximum(e, 1e-300)).sum()
+    assert st.chi2.sf(chi2, len(e) - 1) > 1e-3
+
+
+def test_saturated_sub_loop_carries_the_event_to_the_next_step(otables, units):
+    # with max_emit = 1 and W dt = 3 most steps reach the cap: the optical
+    # depth goes negative and is carried; the event count per step is at
+    # most max_emit + nothing else, and saturations are counted
+    p0, chi = 5.0, 1.0
+    b0 = _b_for_chi(chi, p0, units)
+    gam = math.sqrt(1.0 + p0 * p0)
+    W = units.C_rate * otables.lookup(0, chi)[0] / gam
+    n = 500
+    el = _species(n, n, (p0, 0, 0))
+    O.init_tau(4, O.ELECTRON, el)
+    sim = O.Sim(O.uniform_b_field(b0), _params(dt=3.0 / W, seed=4, recoil=0, max_emit=1),
+                electrons=el)
+    for step in range(5):
+        before = el.nemit[:n].copy()
+        sim.run(1)
+        assert np.all(el.nemit[:n] - before <= 2)
+    assert sim.stats.n_saturated > n
+    assert np.any(el.tau[:n] < 0.0)
 
 
 def test_emitted_spectrum_chi2_against_eq2(units):
@@ -159,6 +207,100 @@ def test_sokolov_energy_loss_equals_radiated_power(units):
     assert (g0 - g1) / dt == pytest.approx(prad, rel=2e-4)
     assert sim.stats.n_emit == 0 and sim.stats.n_continuous == 1
     assert el.tau[0] > 0  # optical depth frozen in the continuous regime
+
+
+def _uniform_eb(E, B, half=4):
+    """A 2D Yee grid with the same float32 value at every node: uniform E, B
+    around the origin."""
+    n = 2 * half
+    comps = [np.full((n, n), v, dtype=np.float32) for v in list(E) + list(B)]
+    return O.yee2d_field(comps, 1.0, 1.0, -half, -half)
+
+
+def _sokolov_expected(units, G, q, dt, E, B, u_half):
+    """The continuous step of Eq. 4-5 in the reading of the design notes,
+    written out from the equations: f_l = q (E + v x B),
+    dv = tau0 (f_l - v (v.f_l)) / (1 + tau0 v.f_l), du = dt (q dv x B - P_rad v),
+    dx = dt (v' + dv) with v' from the final momentum."""
+    g = math.sqrt(1.0 + u_half @ u_half)
+    v = u_half / g
+    f = q * (E + np.cross(v, B))
+    vf = v @ f
+    dv = units.tau0w * (f - v * vf) / (1.0 + units.tau0w * vf)
+    prad = units.C_rate * G
+    u1 = u_half + dt * (q * np.cross(dv, B) - prad * v)
+    g1 = math.sqrt(1.0 + u1 @ u1)
+    return u1, dt * (u1 / g1 + dv), dv
+
+
+@pytest.mark.parametrize("species,q", [(O.ELECTRON, -1.0), (O.POSITRON, 1.0)])
+def test_sokolov_delta_v_in_crossed_fields(otables, units, species, q):
+    # A generic E and B (neither perpendicular to v nor to each other), so
+    # v.f_l != 0 and the denominator 1 + tau0 v.f_l differs from 1 by ~1e-3;
+    # gamma ~ 4 and chi ~ 0.5 (the continuous branch forced by chi_th), so
+    # the q dv x B force is ~5 % of the momentum change of the step and dv
+    # is measured through the position with ~1e-12 relative precision.  A
+    # sign error in q dv x B, a dropped denominator or v(v.f_l) term, or a
+    # missing +dv in dx/dt fails one of the comparisons.
+    F = 6.0e4
+    E = np.array([0.3, 0.8, -0.2]) * F
+    B = np.array([0.1, -0.4, 0.9]) * F
+    field = _uniform_eb(E, B)
+    E, B = O.field_eval(field, 0.0, 0.0, 0.0, 0.0)  # the values the step sees
+    u0 = np.array([3.0, -2.0, 1.5])
+    arr = {"x": [0.0], "y": [0.0], "z": [0.0], "ux": [u0[0]], "uy": [u0[1]], "uz": [u0[2]],
+           "w": [1.0]}
+    sp = O.Species.from_arrays(arr, 1)
+    dt = 1e-6
+    kw = dict(electrons=sp) if species == O.ELECTRON else dict(positrons=sp)
+    sim = O.Sim(field, _params(dt=dt, chi_th=1e9), **kw)
+    sim.run(1)
+    assert sim.stats.n_continuous == 1 and sim.stats.n_emit == 0
+    u_half = O.boris(q, dt, E, B, u0)
+    g_half = math.sqrt(1.0 + u_half @ u_half)
+    chi = O.chi_e(E, B, u_half, g_half, units.a_S)
+    assert 0.1 < chi < 2.0
+    G = otables.lookup(1, chi)[0]
+    u1, dx, dv = _sokolov_expected(units, G, q, dt, E, B, u_half)
+    got_u = np.array([sp.ux[0], sp.uy[0], sp.uz[0]])
+    got_x = np.array([sp.x[0], sp.y[0], sp.z[0]])
+    # the size of what is checked
+    vf = (u_half / g_half) @ (q * (E + np.cross(u_half / g_half, B)))
+    assert abs(units.tau0w * vf) > 1e-4
+    dvxb = dt * np.linalg.norm(np.cross(dv, B))
+    assert dvxb > 0.02 * np.linalg.norm(u1 - u_half)
+    # momentum: the change of the step within 1e-10 of its size
+    np.testing.assert_allclose(got_u - u_half, u1 - u_half, rtol=0,
+                               atol=1e-10 * np.linalg.norm(u1 - u_half))
+    # position: x = dt (v' + dv); dv itself within 1e-8
+    g1 = math.sqrt(1.0 + got_u @ got_u)
+    dv_got = got_x / dt - got_u / g1
+    np.testing.assert_allclose(dv_got, dv, rtol=0, atol=1e-8 * np.linalg.norm(dv))
+    np.testing.assert_allclose(got_x, dx, rtol=0, atol=1e-12 * np.linalg.norm(dx))
+    # the optical depth does not move in the continuous regime
+    assert sp.tau[0] == 0.0
+
+
+def test_sokolov_step_without_radiation_reaction_is_the_boris_step(units):
+    # tau0 -> 0 and P_rad -> 0: the continuous step reduces to the plain
+    # Boris step and x += dt v, bit for bit
+    E = np.array([2.0e3, -1.0e3, 5.0e2])
+    B = np.array([-3.0e2, 4.0e3, 1.0e3])
+    field = _uniform_eb(E, B)
+    E, B = O.field_eval(field, 0.0, 0.0, 0.0, 0.0)
+    u0 = np.array([-1.0, 2.5, 0.5])
+    arr = {"x": [0.0], "y": [0.0], "z": [0.0], "ux": [u0[0]], "uy": [u0[1]], "uz": [u0[2]],
+           "w": [1.0]}
+    sp = O.Species.from_arrays(arr, 1)
+    dt = 1e-4
+    sim = O.Sim(field, _params(dt=dt, chi_th=1e9), electrons=sp)
+    sim.U.tau0w = 0.0
+    sim.U.C_rate = 0.0
+    sim.run(1)
+    u_half = O.boris(-1.0, dt, E, B, u0)
+    g = math.sqrt(1.0 + u_half @ u_half)
+    assert [sp.ux[0], sp.uy[0], sp.uz[0]] == list(u_half)
+    assert [sp.x[0], sp.y[0], sp.z[0]] == list(dt * (u_half / g))
 
 
 def test_photon_cut_and_subthreshold_energy(units):
