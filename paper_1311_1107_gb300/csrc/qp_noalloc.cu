@@ -16,15 +16,15 @@ constexpr size_t kScratchWords = (size_t)(QP_NOALLOC_MAX_TILES + 1) * qp::kDiagW
 static __device__ __align__(256) double g_noalloc_scratch[kScratchWords];
 
 // Device address of the array, looked up once per device with that device
-// current (in host code the symbol is only a host-side stand-in).
+// current (in host code the symbol is only a host-side stand-in, never an
+// address a kernel may be given).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch[kMaxDevices] = {nullptr};
 
-int scratch_for_current_device(double **out)
+int scratch_for_device(int dev, double **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QP_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return QP_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch[dev]) {
         void *p = nullptr;
@@ -34,6 +34,35 @@ int scratch_for_current_device(double **out)
     *out = g_scratch[dev];
     return QP_OK;
 }
+
+// The device that owns the species' buffers (its live counter), else the
+// current device.
+int owning_device(const qp_species_desc *d, int current)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, d->n_live) != cudaSuccess) {
+        (void)cudaGetLastError();  // a host pointer is not an error to keep
+        return current;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ? at.device
+                                                                                : current;
+}
+
+// Makes `dev` current for the life of the guard and restores the caller's
+// device afterwards.
+struct DeviceSwitch {
+    int prev = -1;
+    bool ok = true;
+    DeviceSwitch(int dev, int current) : prev(current)
+    {
+        if (dev != current) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceSwitch()
+    {
+        int now = -1;
+        if (cudaGetDevice(&now) == cudaSuccess && now != prev) (void)cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -46,8 +75,13 @@ extern "C" int qp_diagnostics_noalloc(const qp_species_desc *d, qp_diag *out, vo
     if (d->capacity > (int64_t)QP_NOALLOC_MAX_SLOTS) return QP_ERR_INVALID_ARG;
     if (d->capacity > 0 && (!d->x || !d->y || !d->ux || !d->uy || !d->uz || !d->tau || !d->w))
         return QP_ERR_INVALID_ARG;
+    int current = -1;
+    if (cudaGetDevice(&current) != cudaSuccess) return QP_ERR_CUDA;
+    const int dev = owning_device(d, current);
+    DeviceSwitch guard(dev, current);
+    if (!guard.ok) return QP_ERR_CUDA;
     double *scratch = nullptr;
-    int st = scratch_for_current_device(&scratch);
+    int st = scratch_for_device(dev, &scratch);
     if (st != QP_OK) return st;
 
     qp::SpeciesDev S{};

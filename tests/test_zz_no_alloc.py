@@ -1,8 +1,7 @@
 """qp_diagnostics_noalloc against qp_diagnostics (GPU only).
 
 The allocation-free entry point serves callers that cannot allocate device
-memory (for instance while a CUDA graph is being captured, or when the host
-application's pool owns all device memory).  It must give the same species
+memory: a host application whose pool allocator owns the device memory.  It must give the same species
 reductions as the context-based qp_diagnostics, call after call, although
 every call shares one static scratch array.  This file is collected last.
 """
@@ -68,3 +67,26 @@ def test_noalloc_rejects_capacity_above_its_scratch(sim):
     d.capacity = Q.QP_NOALLOC_MAX_SLOTS + 1
     out = Q.qp_diag()
     assert Q.lib().qp_diagnostics_noalloc(C.byref(d), C.byref(out), None) == Q.QP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n_live", [3000, Q.QP_NOALLOC_MAX_SLOTS])
+def test_noalloc_at_the_largest_capacity(sim, n_live):
+    # a species of exactly QP_NOALLOC_MAX_SLOTS slots uses every partial row
+    # of the scratch and the final row right after them
+    from paper_1311_1107_gb300.sim import DeviceSpecies
+    cap = Q.QP_NOALLOC_MAX_SLOTS
+    sp = DeviceSpecies(sim.ctx, Q.QP_ELECTRON, cap, 3, sim.dev)
+    g = torch.Generator(device=sim.dev).manual_seed(n_live)
+    src = sim.species["electron"].host()
+    for nm, t in sp.t.items():
+        if n_live <= len(src[nm]):
+            t[:n_live].copy_(torch.as_tensor(src[nm][:n_live]))
+        else:
+            t.copy_(torch.rand(cap, generator=g, device=sim.dev, dtype=torch.float64) * 100.0)
+    sp.chi.uniform_(0.0, 2.0, generator=g)
+    sp.n_live.fill_(n_live)
+    torch.cuda.synchronize()
+    ref = Q.qp_diagnostics(sim.ctx, sp.handle, None)
+    for _ in range(2):
+        _same(Q.qp_diagnostics_noalloc(sp._desc), ref)
+    Q.qp_destroy_species(sim.ctx, sp.handle)
