@@ -126,6 +126,14 @@ typedef struct {
                            id_base + i, the counter of its random streams.  A
                            population split over GPUs keeps every particle's
                            draws when each part gets the id of its first slot */
+    int64_t id_split;   /* 0: every slot i is particle id_base + i.  > 0: only
+                           slots below id_split are; slot i >= id_split is
+                           particle id_append + (i - id_split).  A part of a
+                           split population gives the particles it appends ids
+                           no other part uses (slots past its own primaries
+                           would otherwise take the next part's ids and share
+                           their random streams)                            */
+    int64_t id_append;  /* id of slot id_split when id_split > 0 (>= 0)      */
 } qp_species_desc;
 
 /*
@@ -350,9 +358,9 @@ int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
 
 /*
  * Allocation-free diagnostics, for callers that cannot allocate device
- * memory: code that runs while a CUDA graph is being captured (where
- * cudaMalloc is not allowed), or a host application whose device memory is
- * owned by its own pool allocator and must not be allocated behind its back.
+ * memory: a host application whose device memory is owned by its own pool
+ * allocator (a cudaMalloc behind the pool's back would take memory the pool
+ * has budgeted, or fail once the pool has reserved it all).
  * It needs no context: the caller passes the species' buffers (`d`, device
  * pointers as for qp_create_species) and a host `out`, and gets the same
  * state reductions as qp_diagnostics (n_live, n_alive, weight, energy,
@@ -363,11 +371,15 @@ int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
  * QP_NOALLOC_MAX_TILES tiles of 256 slots (QP_NOALLOC_MAX_SLOTS slots, about
  * 2.4 MB), which every GPU that loads the library holds until the process
  * exits.  A species whose capacity exceeds QP_NOALLOC_MAX_SLOTS is rejected
- * with QP_ERR_INVALID_ARG before anything is enqueued.  The first call on a
- * device looks the array up on that device (make it before any stream
- * capture).  Every call overwrites the part of the array it reads, but all
- * calls share it: calls that overlap on the GPU (other streams, no ordering
- * between them) race and return wrong results.  Synchronises `stream`.
+ * with QP_ERR_INVALID_ARG before anything is enqueued.  The call runs on the
+ * device that owns `d->n_live` (made current for the call, the caller's
+ * current device restored before it returns); `stream` must belong to that
+ * device.  The first call on a device looks the array up on that device
+ * (make it before any stream capture).  Every call overwrites the part of
+ * the array it reads, but all calls share it: calls that overlap on the GPU
+ * (other streams, no ordering between them) race and return wrong results.
+ * The result is copied to host memory and `stream` is synchronised before
+ * the call returns.
  * The paper has no counterpart: this is plumbing of the library.
  */
 #define QP_NOALLOC_MAX_TILES 4096

@@ -67,7 +67,8 @@ class Field(C.Structure):
 class _Species(C.Structure):
     _fields_ = [("n", C.c_int64), ("cap", C.c_int64)] + [
         (name, C.c_void_p) for name in ("x", "y", "z", "ux", "uy", "uz", "tau", "w", "chi",
-                                        "margin", "nemit", "ids")]
+                                        "margin", "nemit", "ids")] + [
+        ("id_base", C.c_int64), ("id_split", C.c_int64), ("id_append", C.c_int64)]
 
 
 class Params(C.Structure):
@@ -343,6 +344,9 @@ class Species:
         self.margin = np.full(self.cap, np.inf) if track else None
         self.nemit = np.zeros(self.cap, dtype=np.int32) if track else None
         self.ids = None  # optional int64 slot numbers for the random streams
+        # without ids: slot i is particle id_base + i below id_split (when
+        # id_split > 0) and id_append + (i - id_split) from there on
+        self.id_base, self.id_split, self.id_append = 0, 0, 0
 
     @classmethod
     def from_arrays(cls, arrays: dict, cap: int, dims: int = 3, track: bool = True,
@@ -362,6 +366,7 @@ class Species:
     def _struct(self):
         st = _Species()
         st.n, st.cap = self.n, self.cap
+        st.id_base, st.id_split, st.id_append = self.id_base, self.id_split, self.id_append
         for nm in self.NAMES + ("chi", "margin", "nemit", "ids"):
             a = getattr(self, nm)
             setattr(st, nm, None if a is None else a.ctypes.data)

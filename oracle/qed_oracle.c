@@ -724,9 +724,22 @@ typedef struct {
     int64_t *ids;     /* optional: the slot number each entry stands for
                          in the random streams (default: its index);
                          lets a test run a sample of a larger population */
+    int64_t id_base;  /* without ids: slot i is particle id_base + i ...     */
+    int64_t id_split; /* ... below id_split when id_split > 0, and particle
+                         id_append + (i - id_split) from there on (the ids a
+                         part of a split population gives what it appends) */
+    int64_t id_append;
 } or_species;
 
-static int64_t or_id(const or_species *S, int64_t i) { return S->ids ? S->ids[i] : i; }
+/* The particle id of slot i by the species' id rule (ids array aside). */
+static int64_t or_slot_id(const or_species *S, int64_t i)
+{
+    if (S->id_split > 0 && i >= S->id_split) return S->id_append + (i - S->id_split);
+    return S->id_base + i;
+}
+
+/* The particle id whose random streams slot i draws from. */
+static int64_t or_id(const or_species *S, int64_t i) { return S->ids ? S->ids[i] : or_slot_id(S, i); }
 
 typedef struct {
     double dt;
@@ -788,7 +801,7 @@ static void or_append_photon(or_species *P, int64_t base, int64_t *ord, const do
     if (P->chi) P->chi[slot] = 0.0;
     if (P->margin) P->margin[slot] = INFINITY;
     if (P->nemit) P->nemit[slot] = 0;
-    if (P->ids) P->ids[slot] = slot;
+    if (P->ids) P->ids[slot] = or_slot_id(P, slot);
     st->n_photon++;
 }
 
@@ -936,7 +949,7 @@ static void or_append_lepton(or_species *S, int64_t slot, const double x[3], con
     if (S->chi) S->chi[slot] = 0.0;
     if (S->margin) S->margin[slot] = INFINITY;
     if (S->nemit) S->nemit[slot] = 0;
-    if (S->ids) S->ids[slot] = slot;
+    if (S->ids) S->ids[slot] = or_slot_id(S, slot);
 }
 
 /* One step of one super-photon: ballistic motion at c along k, optical depth

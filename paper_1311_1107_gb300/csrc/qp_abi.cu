@@ -224,6 +224,8 @@ qp::SpeciesDev species_dev(const qp_ctx *c, int32_t h)
     s.n_live = d.n_live;
     s.cap = d.capacity;
     s.id_base = d.id_base;
+    s.id_split = d.id_split;
+    s.id_append = d.id_append;
     s.present = 1;
     s.slot_stats = h;
     return s;
@@ -349,6 +351,7 @@ int qp_create_species(qp_ctx *ctx, const qp_species_desc *d, int32_t *out_handle
     if (d->kind < QP_ELECTRON || d->kind > QP_PHOTON) return QP_ERR_INVALID_ARG;
     if (d->dims != 2 && d->dims != 3) return QP_ERR_INVALID_ARG;
     if (d->capacity < 0 || !d->n_live || d->id_base < 0) return QP_ERR_INVALID_ARG;
+    if (d->id_split < 0 || (d->id_split > 0 && d->id_append < 0)) return QP_ERR_INVALID_ARG;
     if (d->dims == 2 && d->z) return QP_ERR_INVALID_ARG;
     if (d->capacity > 0 && (!d->x || !d->y || !d->ux || !d->uy || !d->uz || !d->tau || !d->w ||
                             (d->dims == 3 && !d->z)))
@@ -386,8 +389,8 @@ int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t fi
     if (first < 0 || count < 0 || first + count > d.capacity) return QP_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return QP_ERR_CUDA;
-    return cuda_status(qp::launch_init_tau(d.tau, first, count, d.id_base, seed, d.kind,
-                                           (cudaStream_t)stream));
+    return cuda_status(qp::launch_init_tau(d.tau, first, count, d.id_base, d.id_split,
+                                           d.id_append, seed, d.kind, (cudaStream_t)stream));
 }
 
 int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch, int64_t count,

@@ -22,9 +22,22 @@ struct SpeciesDev {
     int64_t *n_live;
     int64_t cap;
     int64_t id_base;     // global number of slot 0: particle id = id_base + slot
+    int64_t id_split;    // > 0: slots from here on are id_append + (slot - id_split)
+    int64_t id_append;
     int32_t present;
     int32_t slot_stats;  // index of this species' counter block
 };
+
+// The particle id of a slot: the counter of its random streams.
+__device__ __forceinline__ int64_t particle_id(int64_t id_base, int64_t id_split,
+                                               int64_t id_append, int64_t slot)
+{
+    return (id_split > 0 && slot >= id_split) ? id_append + (slot - id_split) : id_base + slot;
+}
+__device__ __forceinline__ int64_t particle_id(const SpeciesDev &S, int64_t slot)
+{
+    return particle_id(S.id_base, S.id_split, S.id_append, slot);
+}
 
 // Per-species event counters (device; atomics aggregated per block).
 struct DevStats {

@@ -32,12 +32,13 @@ cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit,
 // -------------------------------------------------------------------- initial optical depth
 
 __global__ void k_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
-                           uint64_t seed, int species)
+                           int64_t id_split, int64_t id_append, uint64_t seed, int species)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
         const int64_t i = first + k;
-        const uint4 r = draw(seed, species, kRngInit, id_base + i, 0, 0);
+        const uint4 r =
+            draw(seed, species, kRngInit, particle_id(id_base, id_split, id_append, i), 0, 0);
         tau[i] = -log(u53(r.x, r.y));
     }
 }
@@ -152,12 +153,14 @@ cudaError_t launch_step(const StepArgs &a, int precision, int field_kind, bool b
 }
 
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
-                            uint64_t seed, int species, cudaStream_t st)
+                            int64_t id_split, int64_t id_append, uint64_t seed, int species,
+                            cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count + kDiagTile - 1) / kDiagTile;
     if (blocks > 4096) blocks = 4096;
-    k_init_tau<<<(int)blocks, kDiagTile, 0, st>>>(tau, first, count, id_base, seed, species);
+    k_init_tau<<<(int)blocks, kDiagTile, 0, st>>>(tau, first, count, id_base, id_split,
+                                                  id_append, seed, species);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ size_t step_smem_fp64();
 size_t step_smem_mixed();
 size_t step_smem_bytes(int precision);
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
-                            uint64_t seed, int species, cudaStream_t st);
+                            int64_t id_split, int64_t id_append, uint64_t seed, int species,
+                            cudaStream_t st);
 cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, int nblocks,
                         double *out, cudaStream_t st);
 cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit, int *status,

@@ -225,8 +225,13 @@ struct Smem {
 __device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepArgs &a)
 {
     if (!mbar_wait_bounded(bar, 0, a.spin_limit)) {
+        // the step's results are flagged invalid from here on; a second
+        // bounded wait gives the copy more time to land before the block
+        // reads the tables or leaves.  If it runs out too, the tile reads
+        // tables that may be incomplete (the raised status says so) and the
+        // kernel still terminates.
         raise_status(a.status, QP_ERR_TIMEOUT);
-        (void)mbar_wait_bounded(bar, 0, a.spin_limit);  // never leave with a copy in flight
+        (void)mbar_wait_bounded(bar, 0, a.spin_limit);
     }
 }
 
@@ -377,7 +382,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 }
                 r = r - tau / wdt;
                 // ---- emission: Eq. 7 sampling, Eq. 8 recoil
-                const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
+                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
                 const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
                 double ufrac;
                 ufrac = sample_cdf<double>(a.tab.Cg, a.tab.Gg, chi, xi_p, kSgMin, kSgSpan, true,
@@ -392,7 +397,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 }
                 ++n_emit;
                 if (gg > P.gmin) {
-                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
                     st[(kStashGg + nph) * kTile + tid] = gg;
                     st[(kStashTg + nph) * kTile + tid] = -log(u53(rp.x, rp.y));
                     ++nph;
@@ -514,7 +519,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 events = true;
                 r = r - df_to_f(TAU) / wdt;
                 // ---- emission: Eq. 7 sampling, Eq. 8 recoil
-                const uint4 rr = draw(P.seed, sp, kRngEmit, S.id_base + i, P.step, k);
+                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
                 const float xi = u53f(rr.z, rr.w);
                 const FracPair uf = sample_cdf_f(
                     a.tab.Cg2, a.tab.Qg2, a.tab.Gg, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
@@ -539,7 +544,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 }
                 ++n_emit;
                 if (gg > m.gmin) {
-                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, S.id_base + i, P.step, k);
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
                     st[(kStashGg + nph) * kTile + tid] = f_to_d(gg);
                     st[(kStashTg + nph) * kTile + tid] = f_to_d(-logf(u53f(rp.x, rp.y)));
                     ++nph;
@@ -735,8 +740,8 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 if (Ph.chi) Ph.chi[i] = chi;
                 if (dtau > 0.0 && !(tau > dtau)) {
                     // ---- pair creation at the photon position
-                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
-                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
+                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, particle_id(Ph, i), P.step, 0);
+                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, particle_id(Ph, i), P.step, 0);
                     v = sample_cdf<double>(a.tab.Cp, a.tab.Gp, chi, u53(r1.x, r1.y), kSpMin,
                                            kSpSpan, false, clamped);
                     omv = 1.0 - v;
@@ -797,8 +802,8 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                 const df2 TAU = split_d(taud);
                 if (dtau > 0.0f && !(TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f))) {
                     // ---- pair creation at the photon position
-                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, Ph.id_base + i, P.step, 0);
-                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, Ph.id_base + i, P.step, 0);
+                    const uint4 r1 = draw(P.seed, QP_PHOTON, kRngPair, particle_id(Ph, i), P.step, 0);
+                    const uint4 r2 = draw(P.seed, QP_PHOTON, kRngPairPos, particle_id(Ph, i), P.step, 0);
                     const FracPair vf = sample_cdf_f(
                         a.tab.Cp2, a.tab.Qp2, a.tab.Gp, a.tab.Ep, chi, u53_pair(r1.x, r1.y),
                         u53_pair_complement(r1.x, r1.y), (float)(kSpSpan / (kNNode - 1)), false,

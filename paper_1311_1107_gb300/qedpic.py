@@ -46,7 +46,8 @@ class qp_species_desc(C.Structure):
                 ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
                 ("ux", C.c_void_p), ("uy", C.c_void_p), ("uz", C.c_void_p),
                 ("tau", C.c_void_p), ("w", C.c_void_p), ("chi", C.c_void_p),
-                ("nemit", C.c_void_p), ("n_live", C.c_void_p), ("id_base", C.c_int64)]
+                ("nemit", C.c_void_p), ("n_live", C.c_void_p), ("id_base", C.c_int64),
+                ("id_split", C.c_int64), ("id_append", C.c_int64)]
 
 
 class qp_field(C.Structure):

@@ -30,6 +30,26 @@ def shard_arrays(arrays: dict, rank: int, world: int) -> tuple[dict, int]:
     return {k: v[first:first + count] for k, v in arrays.items()}, first
 
 
+def shard_ids(n_total: int, rank: int, world: int, capacity: dict) -> dict:
+    """Particle-id rule of each species of rank's part (species name ->
+    (id_base, id_split, id_append) of qp_species_desc).  Primary electrons
+    keep their global ids (first .. first + count - 1); what the rank appends
+    gets ids no other rank uses: electrons from n_total + rank * cap_e on,
+    positrons and photons from rank * cap on.  At world = 1 every slot i is
+    particle i, as in an unsplit run.  capacity: slots per species on every
+    rank (the same on all ranks)."""
+    first, count = shard_range(n_total, rank, world)
+    cap_e = int(capacity["electron"])
+    if count > cap_e:
+        raise ValueError("a rank's electrons exceed the electron capacity")
+    return {
+        "electron": (first, count, n_total + rank * cap_e) if count else
+                    (n_total + rank * cap_e, 0, 0),
+        "positron": (rank * int(capacity["positron"]), 0, 0),
+        "photon": (rank * int(capacity["photon"]), 0, 0),
+    }
+
+
 def aggregate(time_ms: float, units: float, dist=None, device="cpu") -> tuple[float, float]:
     """Whole-job figures over ranks: the slowest rank's time and the total
     units processed (torch.distributed with any backend; identity at N=1)."""

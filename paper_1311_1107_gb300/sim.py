@@ -33,9 +33,12 @@ class DeviceSpecies:
     """FP64 SoA buffers of one species on the GPU, registered with a context."""
 
     def __init__(self, ctx, kind: int, capacity: int, dims: int = 3, device="cuda:0",
-                 track_chi: bool = True, id_base: int = 0, n_live=None):
+                 track_chi: bool = True, id_base: int = 0, n_live=None, id_split: int = 0,
+                 id_append: int = 0):
         """n_live: a one-element int64 device tensor to hold the live count
-        (a view of a shared tensor lets a caller move all counts at once)."""
+        (a view of a shared tensor lets a caller move all counts at once).
+        id_base, id_split, id_append: the particle-id rule of the slots (the
+        counters of their random streams, see qp_species_desc)."""
         self.kind, self.cap, self.dims = kind, int(capacity), dims
         n = max(self.cap, 1)
         names = [nm for nm in NAMES if not (nm == "z" and dims == 2)]
@@ -55,6 +58,8 @@ class DeviceSpecies:
         d.nemit = _ptr(self.nemit)
         d.n_live = _ptr(self.n_live)
         d.id_base = int(id_base)
+        d.id_split = int(id_split)
+        d.id_append = int(id_append)
         self._desc = d
         self.ctx = ctx
         self.handle = Q.qp_create_species(ctx, d)
@@ -119,9 +124,11 @@ class Simulation:
 
     def __init__(self, workload: dict, precision: str = "fp64", device: int = 0, ctx=None,
                  track_chi: bool = True, init_tau: bool = True, load: bool = True,
-                 id_base: int = 0):
+                 id_base: int = 0, ids: dict | None = None):
         """id_base: particle id of the first electron slot (a shard of a larger
-        population keeps its particles' random streams)."""
+        population keeps its particles' random streams).  ids: optional
+        species name -> (id_base, id_split, id_append), the id rule of each
+        species (shard.shard_ids); it replaces id_base."""
         self.dev = f"cuda:{device}"
         self.own_ctx = ctx is None
         self.ctx = ctx if ctx is not None else Q.qp_init_tables(LAMBDA_M, device)
@@ -130,10 +137,12 @@ class Simulation:
         cap = workload["capacity"]
         # live counts of electrons, positrons, photons side by side
         self.counts = torch.zeros(3, dtype=torch.int64, device=self.dev)
+        if ids is None:
+            ids = {"electron": (id_base, 0, 0), "positron": (0, 0, 0), "photon": (0, 0, 0)}
         self.species = {
             name: DeviceSpecies(self.ctx, KIND[name], cap[name], dims, self.dev, track_chi,
-                                id_base if name == "electron" else 0,
-                                n_live=self.counts[k:k + 1])
+                                ids[name][0], n_live=self.counts[k:k + 1],
+                                id_split=ids[name][1], id_append=ids[name][2])
             for k, name in enumerate(("electron", "positron", "photon"))
         }
         self.field, self._keep = make_field(workload["field"], self.dev)

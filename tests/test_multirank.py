@@ -18,7 +18,8 @@ import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
 
 from paper_1311_1107_gb300 import workloads as W  # noqa: E402
-from paper_1311_1107_gb300.shard import aggregate, shard_arrays, shard_range  # noqa: E402
+from paper_1311_1107_gb300.shard import (aggregate, shard_arrays, shard_ids,  # noqa: E402
+                                          shard_range)
 
 N, STEPS = 96, 40
 
@@ -89,3 +90,28 @@ def test_two_ranks_reproduce_the_single_run(tmp_path):
             assert np.array_equal(v, full[k][a:b]), k
     assert sum(p["n_emit"] for p in parts) == osim.stats.n_emit
     assert sum(p["photons"] for p in parts) == osp["photon"].n
+
+
+def test_shard_ids_are_disjoint_and_keep_primaries():
+    # every slot of every species of every rank gets a particle id no other
+    # slot of that species uses; primary electrons keep their global ids;
+    # one rank is the unsplit rule (slot i is particle i)
+    cap = {"electron": 70, "positron": 40, "photon": 90}
+    n_total = 61
+    for world in (1, 2, 3, 5):
+        seen = {k: set() for k in cap}
+        for rank in range(world):
+            first, count = shard_range(n_total, rank, world)
+            rule = shard_ids(n_total, rank, world, cap)
+            for sp, (base, split, app) in rule.items():
+                for i in range(cap[sp]):
+                    pid = app + (i - split) if split > 0 and i >= split else base + i
+                    assert pid not in seen[sp], (world, rank, sp, i)
+                    seen[sp].add(pid)
+                    if sp == "electron" and i < count:
+                        assert pid == first + i
+            if world == 1:
+                for sp, (base, split, app) in rule.items():
+                    ids = [app + (i - split) if split > 0 and i >= split else base + i
+                           for i in range(cap[sp])]
+                    assert ids == list(range(cap[sp]))
