@@ -12,7 +12,8 @@ torch = pytest.importorskip("torch")
 from paper_1311_1107_gb300 import qedpic as Q
 from paper_1311_1107_gb300 import workloads as W
 from paper_1311_1107_gb300.sim import Simulation
-from tests.parity import chaos_aware_compare, head, oracle_arrays, run_oracle
+from tests.parity import (chaos_aware_compare, distribution_check, head, oracle_arrays,
+                          run_oracle)
 from tests.test_gpu_mixed import check
 
 pytestmark = pytest.mark.gpu
@@ -59,8 +60,10 @@ def _fp64_check(label, w, n_steps, el, osp, idx):
     for key in (0, 1):
         _, tsp = run_oracle(w, n_steps, sample=idx, noise=4e-16, noise_key=key)
         t.append(head(oracle_arrays(tsp["electron"]), n))
-    return chaos_aware_compare(g, o, t, 1e-6, label, margin=osp["electron"].margin[:n],
-                               margin_min=1e-10, min_comparable=0.5)
+    rep = chaos_aware_compare(g, o, t, 1e-6, label, margin=osp["electron"].margin[:n],
+                              margin_min=1e-10, min_comparable=0.5)
+    distribution_check(g, o, label + " sampled")
+    return rep
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
