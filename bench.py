@@ -7,21 +7,33 @@ photons and pairs tracked), run on the mixed-precision path (the headline
 `value`) and on the FP64 path (`fp64`) on the same GPU.  A step is one
 qp_step (one launch of the fused step kernel) over every live particle;
 K steps are timed from the initial state (K = 500 is the whole job).
-The line also carries `serving`: a stream of beam-collision requests served
-with continuous batching (Poisson arrivals at ~70 % of the measured batched
-throughput), its throughput and p50/p99 request latency; `--workload
-serving` runs the full 256-request stream on its own.
-L2 is flushed (256 MB write) between timed steps; each step is timed with
-CUDA events on its stream; clocks are sampled with nvidia-smi meanwhile.
+The line also carries
+  `collision`: the beam collision at full size (1e7 e-, 1e8-slot photon
+      and pair buffers, the K steps from step 980, around the pulse peak),
+      mixed and FP64, each with its roofline: the many-particle state in
+      which the step's HBM bound can be approached;
+  `serving`: the 256-request stream of beam-collision requests (n_e
+      log-uniform 1e3-1e6) served with continuous batching (Poisson arrivals
+      at ~70 % of the measured batched throughput), its throughput and
+      p50/p99 request latency;
+  `e2e`: the same steps through the public API with the state copied from
+      and to pinned host memory every step;
+  `cpu_baseline`: the FP64 oracle on a bounded sample, on one core and on
+      every host core.
+Particle-steps count the live slots at each step start, decayed photons
+(tau < 0, kept in their slots) left out.  L2 is flushed (256 MB write)
+between timed steps; each step is timed with CUDA events on its stream;
+clocks are sampled with nvidia-smi meanwhile.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload foil|collision|plane|serving] [--requests R]
 
 Under torchrun each rank steps its own shard of a population of N copies of
-the workload (particle ids offset by rank x n, so every particle has its own
-random streams) on its own GPU: weak scaling with no collective in the data
-path; the barrier and the max over ranks of the timed region come from
-torch.distributed.
+the workload (disjoint particle ids, so every particle has its own random
+streams) on its own GPU: weak scaling with no collective in the data path;
+the barrier and the max over ranks of the timed region come from
+torch.distributed.  The reference arm (`--impl reference`) is the CPU
+oracle on every host core: the paper has no code to install.
 """
 from __future__ import annotations
 
@@ -57,12 +69,12 @@ def parse():
     p.add_argument("--workload", choices=("foil", "collision", "plane", "serving"),
                    default="foil")
     p.add_argument("--requests", type=int, default=None,
-                   help="serving: requests in the stream (default 256 for --workload serving, "
-                        "32 inside the default line)")
+                   help="serving: requests in the stream (default 256)")
     p.add_argument("--serving-nmax", type=float, default=None,
-                   help="serving: largest electron count of a request (default 1e6; 1e5 "
-                        "inside the default line)")
+                   help="serving: largest electron count of a request (default 1e6)")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-collision", action="store_true",
+                   help="leave the full-size collision leg out of the default line")
     p.add_argument("--collision-n", type=float, default=None,
                    help="collision: electrons (default 1e7; buffers 10x)")
     p.add_argument("--start-step", type=int, default=None,
@@ -106,6 +118,9 @@ def species_bytes(dims: int, pairs: bool):
     pho = pos + 24 + 8 + pos + (8 if pairs else 0)
     new = pos + 24 + 8 + 8
     return lep, pho, new
+
+
+DEAD_B = 8  # a decayed photon's slot: its optical-depth sentinel is read
 
 
 def peaks():
@@ -170,7 +185,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- GPU path
 
-def run_path(w, precision, steps, warmup, dev, dist, flush, id_base=0):
+def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
     import torch
 
     from paper_1311_1107_gb300 import qedpic as Q
@@ -178,8 +193,7 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, id_base=0):
     from paper_1311_1107_gb300.workloads import LAMBDA_M
 
     ctx = Q.qp_init_tables(LAMBDA_M, dev)
-    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False,
-                     id_base=id_base)
+    sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False, ids=ids)
     stream = torch.cuda.current_stream()
     # warm-up steps on the initial state, then back to the initial state
     for _ in range(warmup):
@@ -214,10 +228,17 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, id_base=0):
     c = counts.cpu().numpy()
     diag = {n: sim.diagnostics(n) for n in names}
     lep_slots = int(c[:, 0].sum() + c[:, 1].sum())
-    pho_slots = int(c[:, 2].sum())
+    # photons that decayed keep their slot (tau < 0) and are only tested:
+    # each pair event kills one photon and appends one electron, so the dead
+    # slots at the start of step k are the electrons appended since step 0
+    # (exact while no pair was dropped at the capacity)
+    dead = c[:, 0] - c[0, 0]
+    pho_all = int(c[:, 2].sum())
+    pho_slots = int((c[:, 2] - dead).sum())
     res = {
         "ctx": ctx, "sim": sim, "step_ms": step_ms, "kernel_ms": ms, "launches": launches,
-        "lep_slots": lep_slots, "pho_slots": pho_slots, "wall_s": wall,
+        "lep_slots": lep_slots, "pho_slots": pho_slots, "dead_slots": pho_all - pho_slots,
+        "pair_drops": int(diag["photon"].n_pair_drop), "wall_s": wall,
         "photons_added": int(sum(diag[n].n_photon for n in ("electron", "positron"))),
         "pairs_added": int(diag["photon"].n_pair - diag["photon"].n_pair_drop),
         "emitters": int(sum(diag[n].n_emit for n in ("electron", "positron"))),
@@ -270,6 +291,7 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
     same command, or None."""
     lep_b, pho_b, new_b = species_bytes(dims, pairs)
     nbytes = (res["lep_slots"] * lep_b + res["pho_slots"] * pho_b
+              + res.get("dead_slots", 0) * DEAD_B
               + (res["photons_added"] + 2 * res["pairs_added"]) * new_b)
     t_ms = res["kernel_ms"][0]
     n = max(res["launches"][0], 1)
@@ -280,6 +302,7 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
             "traffic_read_write": list(traffic) if traffic else None,
             "bytes_per_launch": round(nbytes / n), "avg_launch_us": round(t_ms * 1e3 / n, 3),
             "bytes_model": f"{lep_b} B per lepton slot-step, {pho_b} B per photon slot-step, "
+                           f"{DEAD_B} B per decayed-photon slot (tau read), "
                            f"{new_b} B per appended particle",
             "peak_source": ("measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
                             else "fallback 6.8 TB/s")}
@@ -404,16 +427,21 @@ def serving_arm(args):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(w, n_sample: int, n_steps: int, photons_per_electron: int = 256):
+def oracle_sample(w, n_sample: int, n_steps: int, photons_per_electron: int = 256,
+                  part=(0, 1), warmup: int = 0):
     """Time the CPU oracle (single thread) on a bounded sample of the
     workload: n_sample electrons (evenly spaced slots, each with its own
-    random stream) for n_steps steps."""
+    random stream) for n_steps steps, after `warmup` untimed steps.
+    part = (k, P): only the k-th of P contiguous parts of the sample (one
+    process of an all-core run)."""
     import oracle as O
     from tests.parity import oracle_field
 
     n_all = len(w["electrons"]["x"])
     idx = np.linspace(0, n_all - 1, min(n_sample, n_all)).astype(np.int64)
-    sub = {k: np.asarray(v)[idx] for k, v in w["electrons"].items()}
+    k, P = part
+    idx = np.array_split(idx, P)[k]
+    sub = {kk: np.asarray(v)[idx] for kk, v in w["electrons"].items()}
     dims = w["dims"]
     el = O.Species.from_arrays(sub, len(idx) * 4 + 64, dims, track=False, ids=idx)
     tau = np.zeros(n_all)
@@ -424,6 +452,8 @@ def oracle_sample(w, n_sample: int, n_steps: int, photons_per_electron: int = 25
     ph = O.Species(len(idx) * photons_per_electron + 64, dims, track=False)
     O.tables()
     sim = O.Sim(oracle_field(w["field"]), w["params"], electrons=el, positrons=po, photons=ph)
+    if warmup:
+        sim.run(warmup)
     slots = 0
     t0 = time.perf_counter()
     for _ in range(n_steps):
@@ -433,14 +463,42 @@ def oracle_sample(w, n_sample: int, n_steps: int, photons_per_electron: int = 25
     return slots, dt, len(idx)
 
 
+def _oracle_part(args):
+    """One process of an all-core oracle run (module level: spawn start)."""
+    spec, n_sample, n_steps, ppe, k, P, warmup = args
+    w = workload(*spec)
+    return oracle_sample(w, n_sample, n_steps, ppe, (k, P), warmup)
+
+
+def oracle_all_cores(spec, n_sample: int, n_steps: int, ppe: int, procs: int, warmup: int = 0):
+    """The same sample split over `procs` processes (one per host core; each
+    steps its part of the electrons with the oracle as it stands).  Returns
+    (slot-steps, seconds of the slowest process, electrons)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    jobs = [(spec, n_sample, n_steps, ppe, k, procs, warmup) for k in range(procs)]
+    with ctx.Pool(procs) as pool:
+        parts = pool.map(_oracle_part, jobs)
+    return (sum(p[0] for p in parts), max(p[1] for p in parts), sum(p[2] for p in parts))
+
+
 CPU_BASELINE_SECONDS = 18.0
 
 
-def cpu_baseline(w, args):
-    """The oracle on about CPU_BASELINE_SECONDS of the same workload: a short
-    calibration sample sets how many evenly spaced electrons the timed sample
-    steps (at most all of them, for the timed number of steps)."""
-    collision = args.workload == "collision"
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(w, spec, args):
+    """The oracle on about CPU_BASELINE_SECONDS of the same workload, on one
+    core and on every host core (one process per core, the sample split
+    between them): a short calibration sets how many evenly spaced electrons
+    the timed sample steps (at most all of them, for the timed number of
+    steps)."""
+    collision = spec[0] == "collision"
     ppe = 256 if collision else 16
     steps = min(args.steps, 200)
     slots_c, dt_c, _ = oracle_sample(w, 2048, min(steps, 20), ppe)
@@ -451,10 +509,20 @@ def cpu_baseline(w, args):
     n = int(min(n_all, max(1024, target / steps)))
     if n == n_all:  # every electron: more steps, up to the timed count
         steps = int(min(args.steps, max(steps, target / n_all)))
-    slots, dt, n = oracle_sample(w, n, steps, ppe)
-    return {"value": round(slots / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} electrons (evenly spaced slots) for {steps} steps "
-                      f"of the same workload, FP64 oracle, {dt:.1f} s"}
+    slots, dt, n1 = oracle_sample(w, n, steps, ppe)
+    cores = host_cores()
+    one = {"value": round(slots / dt, 1), "unit": UNIT, "cores": 1,
+           "sample": f"{n1} electrons (evenly spaced slots) for {steps} steps, {dt:.1f} s"}
+    if cores <= 1:
+        return dict(one, kind="oracle")
+    # all cores: the same seconds of work per process
+    n_all_cores = int(min(n_all, n * cores))
+    slots_a, dt_a, na = oracle_all_cores(spec, n_all_cores, steps, ppe, cores)
+    return {"value": round(slots_a / dt_a, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{na} electrons (evenly spaced slots) split over {cores} processes "
+                      f"(one per host core) for {steps} steps of the same workload, FP64 "
+                      f"oracle, slowest process {dt_a:.1f} s",
+            "one_core": one}
 
 
 # ----------------------------------------------------------------------------- arms
@@ -479,19 +547,24 @@ def reference_arm(args):
         if dist:
             dist.destroy_process_group()
         return
-    w = workload(args.workload, 0)
-    n_sample = 16384 if args.workload != "collision" else 4096
-    slots_w, dt_w, _ = oracle_sample(w, n_sample, args.warmup)
-    slots, dt, n = oracle_sample(w, n_sample, args.steps)
+    spec = (args.workload, 0, args.start_step, args.collision_n)
+    w = workload(*spec)
+    cores = host_cores()
+    per_core = 2048 if args.workload != "collision" else 512
+    n_sample = per_core * cores
+    ppe = 256 if args.workload == "collision" else 16
+    slots, dt, n = oracle_all_cores(spec, n_sample, args.steps, ppe, cores, args.warmup)
     v = slots / dt
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "sample": f"{n} electrons"},
-            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} evenly spaced electrons of the workload, "
-                                       f"{args.steps} steps, single thread"},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{n} evenly spaced electrons of the workload split "
+                                       f"over {cores} processes (one per host core), "
+                                       f"{args.warmup} untimed + {args.steps} timed steps"},
             "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -499,77 +572,126 @@ def reference_arm(args):
         dist.destroy_process_group()
 
 
+def leg(w, args, dev, dist, flush, ids, profile, hbm_peak, peak_kind):
+    """Mixed and FP64 paths on one workload: throughput over ranks, the
+    roofline of each and the launch count."""
+    from paper_1311_1107_gb300.shard import aggregate
+    dims = w["dims"]
+    pairs = bool(w["params"].get("pairs", False))
+    mixed = run_path(w, "mixed", args.steps, args.warmup, dev, dist, flush, ids)
+    fp64 = run_path(w, "fp64", args.steps, args.warmup, dev, dist, flush, ids)
+    out = {}
+    for name, res in (("mixed", mixed), ("fp64", fp64)):
+        t_ms, slots = aggregate(sum(res["step_ms"]), res["lep_slots"] + res["pho_slots"], dist,
+                                f"cuda:{dev}")
+        out[name] = {
+            "value": round(slots / (t_ms * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(t_ms / args.steps, 4),
+            "roofline": roofline(res, dims, pairs, hbm_peak, peak_kind,
+                                 measured_traffic(profile, name)),
+            "final_live": res["final_live"], "status": res["status"],
+            "launches": int(sum(res["launches"])),
+            "decayed_photon_slot_steps": res["dead_slots"], "pair_drops": res["pair_drops"],
+        }
+    for res in (mixed, fp64):
+        res["sim"].close()
+        del res["sim"]
+    import torch
+    from paper_1311_1107_gb300 import qedpic as Q
+    torch.cuda.synchronize()
+    for res in (mixed, fp64):
+        Q.qp_destroy(res["ctx"])
+    torch.cuda.empty_cache()
+    return out
+
+
 def ours_arm(args):
     import torch
 
-    from paper_1311_1107_gb300.shard import aggregate
+    from paper_1311_1107_gb300.shard import shard_ids
 
     world, rank, local, dist = dist_setup(args)
     dev = local
     torch.cuda.set_device(dev)
     # every rank steps its own shard of one population of `world` copies of
-    # the workload: the same initial state, particle ids offset by the rank
-    # (independent random streams), no exchange between ranks
-    w = workload(args.workload, 0, args.start_step, args.collision_n)
-    id_base = rank * len(w["electrons"]["x"])
-    dims = w["dims"]
-    pairs = bool(w["params"].get("pairs", False))
+    # the workload: the same initial state, disjoint particle ids (its own
+    # random streams), no exchange between ranks
+    spec = (args.workload, 0, args.start_step, args.collision_n)
+    w = workload(*spec)
+    ids = shard_ids(world * len(w["electrons"]["x"]), rank, world, w["capacity"])
     hbm_peak, peak_kind = peaks()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    profile = {"foil": "k_step_foil2d.md", "collision": "k_step_collision.md"}.get(
+        args.workload, "k_step_" + args.workload + ".md")
 
     clocks = ClockSampler(dev)
     clocks.start()
-    mixed = run_path(w, "mixed", args.steps, args.warmup, dev, dist, flush, id_base)
-    fp64 = run_path(w, "fp64", args.steps, args.warmup, dev, dist, flush, id_base)
-    clk = clocks.stop()
-
-    def agg(res):
-        t_ms, slots = aggregate(sum(res["step_ms"]), res["lep_slots"] + res["pho_slots"], dist,
-                                f"cuda:{dev}")
-        return slots / (t_ms * 1e-3), t_ms
-
-    v_mixed, t_mixed = agg(mixed)
-    v_fp64, t_fp64 = agg(fp64)
-    profile = {"foil": "k_step_foil2d.md", "collision": "k_step_collision.md"}.get(
-        args.workload, "k_step_" + args.workload + ".md")
-    line = None
+    main_leg = leg(w, args, dev, dist, flush, ids, profile, hbm_peak, peak_kind)
+    # the beam collision at full size (1e7 e-, 1e8-slot buffers, the steps
+    # around the pulse peak): the many-particle state of the HBM roofline
+    coll = None
+    if world == 1 and args.workload == "foil" and not args.no_collision:
+        wc = workload("collision", 0, args.start_step, args.collision_n)
+        idc = shard_ids(len(wc["electrons"]["x"]), 0, 1, wc["capacity"])
+        c = leg(wc, args, dev, dist, flush, idc, "k_step_collision.md", hbm_peak, peak_kind)
+        coll = {"workload": wc["name"], "value": c["mixed"]["value"], "unit": UNIT,
+                "ms_per_step": c["mixed"]["ms_per_step"], "roofline": c["mixed"]["roofline"],
+                "final_live": c["mixed"]["final_live"],
+                "decayed_photon_slot_steps": c["mixed"]["decayed_photon_slot_steps"],
+                "fp64": {k: c["fp64"][k] for k in ("value", "ms_per_step", "roofline",
+                                                   "final_live")},
+                "mixed_over_fp64": round(c["mixed"]["value"] / c["fp64"]["value"], 3),
+                "status": {"mixed": c["mixed"]["status"], "fp64": c["fp64"]["status"]},
+                "launches": c["mixed"]["launches"] + c["fp64"]["launches"]}
+        del wc
     serv = None
     if rank == 0 and world == 1 and not args.no_serving:
-        serv = serving(dev, args.requests or 32, args.serving_nmax or 1e5)
+        serv = serving(dev, args.requests or 256, args.serving_nmax or 1e6)
+    clk = clocks.stop()
+    v_mixed, v_fp64 = main_leg["mixed"]["value"], main_leg["fp64"]["value"]
     if rank == 0:
         e2e_res = None
         if not args.no_e2e:
             e2e_res = e2e(w, "mixed", min(args.e2e_steps, args.steps), dev)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline(w, args)
-        launches = int(sum(mixed["launches"]))
+            cpu = cpu_baseline(w, spec, args)
+        launches = main_leg["mixed"]["launches"]
         line = {
-            "metric": METRIC, "value": round(v_mixed, 1), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": v_mixed, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(t_mixed / args.steps, 4), "higher_is_better": True,
+            "ms_per_step": main_leg["mixed"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed path)",
             "data": "synthetic",
             "config": {"workload": w["name"], "precision": "mixed",
                        "l2": "flushed between timed steps (256 MB write)",
-                       "particle_steps": "live slots of e-, e+ and photons at each step start",
-                       "steps_timed": "steps 0..K-1 of the job from the initial state",
-                       "final_live": mixed["final_live"], "parallelism": f"shards x{world} (ids offset by rank, no exchange)"},
-            "fp64": {"value": round(v_fp64, 1), "unit": UNIT,
-                     "ms_per_step": round(t_fp64 / args.steps, 4), "dtype": "f64",
-                     "roofline": roofline(fp64, dims, pairs, hbm_peak, peak_kind,
-                                          measured_traffic(profile, "fp64")),
+                       "particle_steps": "live slots of e-, e+ and photons at each step start, "
+                                         "decayed photons (tau < 0) left out",
+                       "steps_timed": "steps 0..K-1 of the job from the initial state"
+                       if args.workload != "collision" else
+                       f"K steps from step {wc_start(args)}",
+                       "final_live": main_leg["mixed"]["final_live"],
+                       "parallelism": f"shards x{world} (disjoint particle ids per rank, "
+                                      "no exchange)"},
+            "fp64": {"value": v_fp64, "unit": UNIT,
+                     "ms_per_step": main_leg["fp64"]["ms_per_step"], "dtype": "f64",
+                     "roofline": main_leg["fp64"]["roofline"],
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
-                     "final_live": fp64["final_live"]},
-            "roofline": roofline(mixed, dims, pairs, hbm_peak, peak_kind,
-                                 measured_traffic(profile, "mixed")),
+                     "final_live": main_leg["fp64"]["final_live"]},
+            "roofline": main_leg["mixed"]["roofline"],
+            "collision": coll,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
-            "clocks": clk, "status": {"mixed": mixed["status"], "fp64": fp64["status"]},
+            "clocks": clk,
+            "status": {"mixed": main_leg["mixed"]["status"], "fp64": main_leg["fp64"]["status"]},
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def wc_start(args) -> int:
+    return 980 if args.start_step is None else args.start_step
 
 
 def main():

@@ -32,3 +32,20 @@ def test_roofline_reports_traffic_and_fraction():
     assert r["achieved"] == 112.0 and r["frac"] == 1.12  # 112 kB in 1 us
     assert r["traffic"] == 60 and r["traffic_read_write"] == [50, 10]
     assert bench.roofline(res, 3, True, 100.0, "measured")["traffic"] is None
+
+
+def test_roofline_counts_decayed_photons_as_their_tau_read_only():
+    res = {"lep_slots": 1000, "pho_slots": 500, "dead_slots": 300, "photons_added": 0,
+           "pairs_added": 0, "kernel_ms": [1e-3, 0.0, 0.0], "launches": [1, 0, 0]}
+    r = bench.roofline(res, 3, True, 100.0, "measured")
+    assert r["bytes_per_launch"] == 1000 * 112 + 500 * 88 + 300 * 8
+
+
+def test_all_core_oracle_steps_the_same_particles_as_one_core():
+    # the sample split over processes steps the same electrons (each with its
+    # own random streams) as the single-process run of the same sample
+    spec = ("plane", 0, None, None)
+    w = bench.workload(*spec)
+    slots1, _, n1 = bench.oracle_sample(w, 96, 3, 16)
+    slots2, _, n2 = bench.oracle_all_cores(spec, 96, 3, 16, 2)
+    assert n1 == n2 == 96 and slots1 == slots2
