@@ -515,12 +515,18 @@ def cpu_baseline(w, spec, args):
            "sample": f"{n1} electrons (evenly spaced slots) for {steps} steps, {dt:.1f} s"}
     if cores <= 1:
         return dict(one, kind="oracle")
-    # all cores: the same seconds of work per process
+    # all cores: about the same seconds of work per process; once every
+    # electron is in the sample, more of the workload's steps
     n_all_cores = int(min(n_all, n * cores))
-    slots_a, dt_a, na = oracle_all_cores(spec, n_all_cores, steps, ppe, cores)
+    steps_a = steps
+    if n_all_cores == n_all:
+        total = cores * slots / max(dt, 1e-6) * seconds
+        steps_a = int(min(max(args.steps, int(w["params"].get("n_steps", args.steps))),
+                          max(steps, total / n_all)))
+    slots_a, dt_a, na = oracle_all_cores(spec, n_all_cores, steps_a, ppe, cores)
     return {"value": round(slots_a / dt_a, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{na} electrons (evenly spaced slots) split over {cores} processes "
-                      f"(one per host core) for {steps} steps of the same workload, FP64 "
+                      f"(one per host core) for {steps_a} steps of the same workload, FP64 "
                       f"oracle, slowest process {dt_a:.1f} s",
             "one_core": one}
 
