@@ -78,6 +78,18 @@ class Params(C.Structure):
                 ("dims", C.c_int32), ("noise", C.c_double), ("noise_key", C.c_uint64)]
 
 
+class CoalesceParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("x0", "y0", "z0", "dx", "dy", "dz")] + [
+        ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
+        ("ebins_per_octave", C.c_int32), ("dir_bins", C.c_int32), ("min_group", C.c_int32),
+        ("dims", C.c_int32), ("seed", C.c_uint64), ("step", C.c_int64)]
+
+
+class CoalesceStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_before", "n_dead", "n_after", "groups_merged",
+                                         "photons_merged")]
+
+
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("n_emit", "n_photon", "n_photon_drop",
                                          "n_subthreshold", "n_pair", "n_pair_drop",
@@ -125,6 +137,8 @@ def lib():
                                  i64, C.POINTER(_Species), C.POINTER(_Species),
                                  C.POINTER(_Species), C.POINTER(Stats)]),
             "or_init_tau": (None, [C.c_uint64, C.c_int, vp, i64, i64]),
+            "or_coalesce": (C.c_int, [C.POINTER(_Species), C.POINTER(CoalesceParams),
+                                      C.POINTER(CoalesceStats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -415,3 +429,27 @@ class Sim:
             if s is not None:
                 s.n = st.n
         self.P.step += int(n_steps)
+
+
+def coalesce_params(box, cells, ebins_per_octave=8, dir_bins=8, min_group=3, dims=3, seed=0,
+                    step=0) -> CoalesceParams:
+    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz)."""
+    c = CoalesceParams()
+    c.x0, c.y0, c.z0, c.dx, c.dy, c.dz = (float(v) for v in box)
+    c.nx, c.ny, c.nz = (int(v) for v in cells)
+    c.ebins_per_octave, c.dir_bins, c.min_group = ebins_per_octave, dir_bins, min_group
+    c.dims, c.seed, c.step = dims, seed, step
+    return c
+
+
+def coalesce(sp: Species, params: CoalesceParams | None):
+    """Compaction (params None: decayed photons removed, order kept) or
+    coalescence of a photon species in place; returns the stats as a dict."""
+    st = CoalesceStats()
+    s = sp._struct()
+    r = lib().or_coalesce(C.byref(s), None if params is None else C.byref(params),
+                          C.byref(st))
+    if r != 0:
+        raise ValueError("or_coalesce: bad parameters")
+    sp.n = s.n
+    return {name: getattr(st, name) for name, _ in st._fields_}

@@ -1066,3 +1066,295 @@ int or_run(const or_units *U, const or_tables *T, const or_field *F, const or_pa
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Super-photon compaction and coalescence (section 3, last paragraph)        */
+/* ------------------------------------------------------------------------- */
+
+/* The paper names a coalescence of super-photons that conserves energy and
+ * momentum on average and gives no algorithm.  READING (design notes): the
+ * live photons are grouped by (cell of a box grid, log2-energy bin,
+ * direction bin on the faces of a cube); a group of at least min_group
+ * photons is replaced by two photons of weight W/2 each, energy E/W each and
+ * momenta P/W +- d, d perpendicular to P with |P/W|^2 + |d|^2 = (E/W)^2, so
+ * that the group's weight W = sum w, energy E = sum w |u| and momentum
+ * P = sum w u are conserved exactly (to rounding), and both stay massless.
+ * d lies in the plane of P and the group's first photon (the lowest slot);
+ * when that photon is parallel to P, in the plane of P and the coordinate
+ * axis least aligned with it.  The merged pair sits at the weighted mean
+ * position of the group and draws fresh optical depths -log(xi) (the
+ * remaining optical depth of a photon is memoryless).  Decayed photons
+ * (tau < 0) are removed; what remains keeps its slot order, a merged pair
+ * taking the place of its group's first photon.  Slots are renumbered, so a
+ * photon's later draws follow its new slot. */
+
+typedef struct {
+    double x0, y0, z0, dx, dy, dz;
+    int64_t nx, ny, nz;
+    int32_t ebins_per_octave; /* power of two, 1 .. 64                      */
+    int32_t dir_bins;         /* power of two, 1 .. 64, per face axis        */
+    int32_t min_group;        /* >= 3                                        */
+    int32_t dims;
+    uint64_t seed;
+    int64_t step;
+} or_coalesce_params;
+
+typedef struct {
+    int64_t n_before, n_dead, n_after, groups_merged, photons_merged;
+} or_coalesce_stats;
+
+enum { OR_RNG_COALESCE = 5 };
+
+#define OR_NOMERGE UINT64_MAX
+
+static int or_log2i(int v)
+{
+    int k = 0;
+    while ((1 << k) < v) k++;
+    return k;
+}
+
+/* The group key of a live photon, or OR_NOMERGE (outside the box, zero or
+ * non-finite momentum).  Every decision is an exact FP64 operation (a
+ * subtraction, a division, a comparison) or a bit extraction. */
+static uint64_t or_coalesce_key(const or_coalesce_params *C, double x, double y, double z,
+                                double ux, double uy, double uz)
+{
+    double gx = floor((x - C->x0) / C->dx);
+    double gy = floor((y - C->y0) / C->dy);
+    double gz = C->dims == 3 ? floor((z - C->z0) / C->dz) : 0.0;
+    if (!(gx >= 0.0 && gx < (double)C->nx && gy >= 0.0 && gy < (double)C->ny && gz >= 0.0 &&
+          gz < (double)C->nz))
+        return OR_NOMERGE;
+    double e = sqrt(ux * ux + uy * uy + uz * uz);
+    uint64_t eb;
+    memcpy(&eb, &e, 8);
+    uint64_t ex = (eb >> 52) & 0x7FF;
+    if (ex == 0 || ex == 0x7FF) return OR_NOMERGE;
+    /* energy bin: the exponent, then the leading mantissa bits */
+    int lb = or_log2i(C->ebins_per_octave);
+    uint64_t ebin = (ex << lb) | ((eb & ((1ull << 52) - 1)) >> (52 - lb));
+    /* direction bin: the dominant axis with its sign (a cube face), then the
+     * two other components over the dominant one, each in dir_bins bins */
+    double u[3] = {ux, uy, uz};
+    int f = 0;
+    if (fabs(u[1]) > fabs(u[f])) f = 1;
+    if (fabs(u[2]) > fabs(u[f])) f = 2;
+    int face = 2 * f + (u[f] < 0.0 ? 1 : 0);
+    double a = u[(f + 1) % 3] / fabs(u[f]);
+    double b = u[(f + 2) % 3] / fabs(u[f]);
+    int64_t D = C->dir_bins;
+    int64_t ia = (int64_t)floor((a + 1.0) * (0.5 * (double)D));
+    int64_t ib = (int64_t)floor((b + 1.0) * (0.5 * (double)D));
+    if (ia > D - 1) ia = D - 1;
+    if (ib > D - 1) ib = D - 1;
+    uint64_t dbin = ((uint64_t)face * (uint64_t)D + (uint64_t)ia) * (uint64_t)D + (uint64_t)ib;
+    uint64_t cell = ((uint64_t)gx * (uint64_t)C->ny + (uint64_t)gy) * (uint64_t)C->nz +
+                    (uint64_t)gz;
+    uint64_t n_e = 2048ull << lb, n_d = 6ull * (uint64_t)D * (uint64_t)D;
+    return (cell * n_e + ebin) * n_d + dbin;
+}
+
+typedef struct {
+    uint64_t key;
+    int64_t slot;
+} or_keyslot;
+
+static int or_keyslot_cmp(const void *pa, const void *pb)
+{
+    const or_keyslot *a = (const or_keyslot *)pa, *b = (const or_keyslot *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->slot < b->slot ? -1 : (a->slot > b->slot ? 1 : 0);
+}
+
+/* The merged pair of one group (members m[0..n), in slot order). */
+static void or_merge_group(const or_species *Ph, const int64_t *m, int64_t n,
+                           const or_coalesce_params *C, int64_t anchor_id, double out[2][8])
+{
+    double W = 0.0, E = 0.0, P[3] = {0.0, 0.0, 0.0}, X[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = m[k];
+        double w = Ph->w[i];
+        double ux = Ph->ux[i], uy = Ph->uy[i], uz = Ph->uz[i];
+        double e = sqrt(ux * ux + uy * uy + uz * uz);
+        W = W + w;
+        E = E + w * e;
+        P[0] = P[0] + w * ux;
+        P[1] = P[1] + w * uy;
+        P[2] = P[2] + w * uz;
+        X[0] = X[0] + w * Ph->x[i];
+        X[1] = X[1] + w * Ph->y[i];
+        X[2] = X[2] + w * (Ph->z ? Ph->z[i] : 0.0);
+    }
+    double eps = E / W;
+    double c[3] = {P[0] / W, P[1] / W, P[2] / W};
+    double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    double d2 = eps * eps - c2;
+    double dm = d2 > 0.0 ? sqrt(d2) : 0.0;
+    /* unit vector of P, and the reference direction: the first photon */
+    double cm = sqrt(c2);
+    double ph[3] = {c[0] / cm, c[1] / cm, c[2] / cm};
+    double r[3] = {Ph->ux[m[0]], Ph->uy[m[0]], Ph->uz[m[0]]};
+    double rp = r[0] * ph[0] + r[1] * ph[1] + r[2] * ph[2];
+    double v[3] = {r[0] - rp * ph[0], r[1] - rp * ph[1], r[2] - rp * ph[2]};
+    double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double rm = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(vm > 1e-12 * rm)) {
+        /* the first photon is parallel to P: the axis least aligned with P */
+        int a = 0;
+        if (fabs(ph[1]) < fabs(ph[a])) a = 1;
+        if (fabs(ph[2]) < fabs(ph[a])) a = 2;
+        double ax[3] = {0.0, 0.0, 0.0};
+        ax[a] = 1.0;
+        double ap = ph[a];
+        v[0] = ax[0] - ap * ph[0];
+        v[1] = ax[1] - ap * ph[1];
+        v[2] = ax[2] - ap * ph[2];
+        vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+    double dv[3] = {dm * (v[0] / vm), dm * (v[1] / vm), dm * (v[2] / vm)};
+    for (int s = 0; s < 2; s++) {
+        double sg = s == 0 ? 1.0 : -1.0;
+        uint32_t rr[4];
+        or_draw(C->seed, OR_SP_PHOTON, OR_RNG_COALESCE, anchor_id, C->step, s, rr);
+        out[s][0] = X[0] / W;
+        out[s][1] = X[1] / W;
+        out[s][2] = X[2] / W;
+        out[s][3] = c[0] + sg * dv[0];
+        out[s][4] = c[1] + sg * dv[1];
+        out[s][5] = c[2] + sg * dv[2];
+        out[s][6] = -log(or_u53(rr[0], rr[1]));
+        out[s][7] = 0.5 * W;
+    }
+}
+
+/* Compaction (min_group = 0: nothing merged) or coalescence of the live
+ * photons of Ph, in place.  Returns 0, or -1 on bad parameters or memory. */
+int or_coalesce(or_species *Ph, const or_coalesce_params *C, or_coalesce_stats *st)
+{
+    int64_t n = Ph->n;
+    memset(st, 0, sizeof(*st));
+    st->n_before = n;
+    int merge = C && C->min_group > 0;
+    if (merge && (C->min_group < 3 || C->ebins_per_octave < 1 || C->ebins_per_octave > 64 ||
+                  C->dir_bins < 1 || C->dir_bins > 64 || !(C->dx > 0.0) || !(C->dy > 0.0) ||
+                  (C->dims == 3 && !(C->dz > 0.0)) || C->nx < 1 || C->ny < 1 || C->nz < 1))
+        return -1;
+    /* role of each slot: 0 dead or merged away, 1 kept, 2 anchor of a pair */
+    int8_t *role = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    int64_t *grp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    or_keyslot *ks = (or_keyslot *)malloc(sizeof(or_keyslot) * (size_t)(n > 0 ? n : 1));
+    if (!role || !grp || !ks) {
+        free(role);
+        free(grp);
+        free(ks);
+        return -1;
+    }
+    int64_t nk = 0;
+    for (int64_t i = 0; i < n; i++) {
+        role[i] = Ph->tau[i] < 0.0 ? 0 : 1;
+        grp[i] = -1;
+        if (!role[i]) {
+            st->n_dead++;
+            continue;
+        }
+        if (!merge) continue;
+        uint64_t key = or_coalesce_key(C, Ph->x[i], Ph->y[i], Ph->z ? Ph->z[i] : 0.0,
+                                       Ph->ux[i], Ph->uy[i], Ph->uz[i]);
+        if (key == OR_NOMERGE) continue;
+        ks[nk].key = key;
+        ks[nk].slot = i;
+        nk++;
+    }
+    qsort(ks, (size_t)nk, sizeof(or_keyslot), or_keyslot_cmp);
+    /* groups: runs of one key; merged ones are recorded at their anchor */
+    double (*pairs)[2][8] = NULL;
+    int64_t n_pairs = 0;
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk > 0 ? nk : 1));
+    for (int64_t a = 0; a < nk;) {
+        int64_t b = a;
+        while (b < nk && ks[b].key == ks[a].key) b++;
+        if (b - a >= C->min_group) {
+            for (int64_t k = a; k < b; k++) members[k - a] = ks[k].slot;
+            double c2 = 0.0;
+            {
+                double P[3] = {0.0, 0.0, 0.0};
+                for (int64_t k = a; k < b; k++) {
+                    int64_t i = ks[k].slot;
+                    P[0] = P[0] + Ph->w[i] * Ph->ux[i];
+                    P[1] = P[1] + Ph->w[i] * Ph->uy[i];
+                    P[2] = P[2] + Ph->w[i] * Ph->uz[i];
+                }
+                c2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+            }
+            if (c2 > 0.0) {
+                pairs = realloc(pairs, sizeof(*pairs) * (size_t)(n_pairs + 1));
+                int64_t anchor = members[0];
+                or_merge_group(Ph, members, b - a, C, or_id(Ph, anchor), pairs[n_pairs]);
+                grp[anchor] = n_pairs;
+                for (int64_t k = a; k < b; k++) role[ks[k].slot] = 0;
+                role[anchor] = 2;
+                n_pairs++;
+                st->groups_merged++;
+                st->photons_merged += b - a;
+            }
+        }
+        a = b;
+    }
+    /* the survivors in slot order, into fresh arrays, then back */
+    int64_t out = 0;
+    for (int64_t i = 0; i < n; i++) out += role[i];
+    /* per survivor: x y z ux uy uz tau w, then chi, margin and nemit (kept
+     * photons carry theirs along; a merged pair starts from 0, inf, 0) */
+    enum { NB = 11 };
+    double *buf = (double *)malloc(sizeof(double) * NB * (size_t)(out > 0 ? out : 1));
+    int64_t j = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (role[i] == 1) {
+            double *o = buf + NB * j++;
+            o[0] = Ph->x[i];
+            o[1] = Ph->y[i];
+            o[2] = Ph->z ? Ph->z[i] : 0.0;
+            o[3] = Ph->ux[i];
+            o[4] = Ph->uy[i];
+            o[5] = Ph->uz[i];
+            o[6] = Ph->tau[i];
+            o[7] = Ph->w[i];
+            o[8] = Ph->chi ? Ph->chi[i] : 0.0;
+            o[9] = Ph->margin ? Ph->margin[i] : INFINITY;
+            o[10] = Ph->nemit ? (double)Ph->nemit[i] : 0.0;
+        } else if (role[i] == 2) {
+            for (int s = 0; s < 2; s++) {
+                double *o = buf + NB * j++;
+                memcpy(o, pairs[grp[i]][s], 8 * sizeof(double));
+                o[8] = 0.0;
+                o[9] = INFINITY;
+                o[10] = 0.0;
+            }
+        }
+    }
+    for (int64_t k = 0; k < out; k++) {
+        const double *o = buf + NB * k;
+        Ph->x[k] = o[0];
+        Ph->y[k] = o[1];
+        if (Ph->z) Ph->z[k] = o[2];
+        Ph->ux[k] = o[3];
+        Ph->uy[k] = o[4];
+        Ph->uz[k] = o[5];
+        Ph->tau[k] = o[6];
+        Ph->w[k] = o[7];
+        if (Ph->chi) Ph->chi[k] = o[8];
+        if (Ph->margin) Ph->margin[k] = o[9];
+        if (Ph->nemit) Ph->nemit[k] = (int32_t)o[10];
+        if (Ph->ids) Ph->ids[k] = or_slot_id(Ph, k);
+    }
+    Ph->n = out;
+    st->n_after = out;
+    free(buf);
+    free(pairs);
+    free(members);
+    free(role);
+    free(grp);
+    free(ks);
+    return 0;
+}
