@@ -356,6 +356,73 @@ typedef struct {
  * (caller-owned).  Synchronous. */
 int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
 
+/* ---- super-photon compaction and coalescence ---------------------------- */
+
+/* Grid and bins of qp_coalesce_photons.  A live photon belongs to the group
+ * of (cell, energy bin, direction bin):
+ *   cell        floor((x - x0)/dx), floor((y - y0)/dy), floor((z - z0)/dz)
+ *               (z cell 0 for dims 2), each in [0, n); photons outside the
+ *               box are never merged;
+ *   energy bin  the binary exponent of |u| and its leading log2(E) mantissa
+ *               bits (E = energy_bins_per_octave bins per octave, linear in
+ *               |u| within the octave);
+ *   direction   the dominant axis of u with its sign (a face of a cube) and
+ *               the two other components over the dominant one, each in D =
+ *               direction_bins bins over [-1, 1].
+ * Every decision is an exact FP64 operation or a bit extraction, so the CPU
+ * oracle forms the same groups. */
+typedef struct {
+    double x0, y0, z0;      /* corner of the grid (normalised length)            */
+    double dx, dy, dz;      /* cell sizes (> 0; dz unused for dims 2)            */
+    int64_t nx, ny, nz;     /* cells per axis (>= 1; nz = 1 for dims 2)          */
+    int32_t energy_bins_per_octave; /* E: a power of two, 1..64                  */
+    int32_t direction_bins; /* D: a power of two, 1..64                          */
+    int32_t min_group;      /* groups of at least this many photons merge (>= 3) */
+    int32_t reserved;       /* 0                                                 */
+    uint64_t seed;          /* key of the merged photons' optical-depth draws    */
+    int64_t step;           /* step counter of those draws                       */
+} qp_coalesce_params;
+
+typedef struct {
+    int64_t groups_merged;  /* groups replaced by two photons                    */
+    int64_t photons_merged; /* photons in those groups                           */
+    int64_t n_before;       /* live slots before (decayed photons included)      */
+    int64_t n_after;        /* live slots after                                  */
+} qp_coalesce_stats;
+
+/*
+ * Coalescence of super-photons (section 3, last paragraph: a coalescence of
+ * super-photons conserving energy and momentum; the paper gives no
+ * algorithm).  Every group (see qp_coalesce_params) of at least min_group
+ * live photons is replaced by two photons of weight W/2 each, energy E/W
+ * each and momenta P/W +- d, where W, E and P are the group's total
+ * weight, energy (sum w |u|) and momentum (sum w u), d is perpendicular to P
+ * with |P/W|^2 + |d|^2 = (E/W)^2 and lies in the plane of P and the group's
+ * first photon (lowest slot; if that one is parallel to P, the coordinate
+ * axis least aligned with P); both sit at the group's weighted mean
+ * position and draw fresh optical depths -log(xi) from the Philox stream
+ * (seed; photon species, purpose 5, the first photon's particle id, step,
+ * k = 0, 1).  A group whose momentum vanishes is kept as it is.  W, E and P
+ * of every group are conserved to rounding and both photons are massless.
+ * Decayed photons (tau < 0) are removed.  The survivors keep their slot
+ * order, a merged pair taking its group's first slot; their chi and nemit
+ * go with them (0 for a merged pair).  Slots are renumbered, so a photon's
+ * later draws follow its new slot (particle id rule of qp_species_desc).
+ * `P` = NULL: compaction only (decayed photons removed, nothing merged).
+ * Photon species only, capacity below 2^32 slots.  Stream-ordered on
+ * `stream`; the live count is read and rewritten on the device.  The first
+ * call for a capacity allocates the context's scratch (about 105 bytes per
+ * slot: sort keys, offsets and staging arrays; not during a stream capture).
+ * `out` (host, may be NULL): if given, the call synchronises `stream` and
+ * fills it.  QP_ERR_INVALID_ARG for bad parameters or a non-photon species;
+ * a live count outside [0, capacity] raises the sticky status.
+ */
+int qp_coalesce_photons(qp_ctx *ctx, int32_t handle, const qp_coalesce_params *P,
+                        qp_coalesce_stats *out, void *stream);
+
+/* Compaction of decayed photons: qp_coalesce_photons with P = NULL. */
+int qp_compact_photons(qp_ctx *ctx, int32_t handle, qp_coalesce_stats *out, void *stream);
+
 /*
  * Allocation-free diagnostics, for callers that cannot allocate device
  * memory: a host application whose device memory is owned by its own pool

@@ -20,13 +20,15 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqedpic.so")
 
 SOURCES = ["qp_step_fp64.cu", "qp_step_mixed.cu", "qp_kernels.cu", "qp_abi.cu", "qp_noalloc.cu",
-           "qp_tables.cpp"]
+           "qp_coalesce.cu", "qp_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-unit flags.  The mixed-precision step divides in FP32 with the
 # hardware reciprocal (2 ulp): its tolerance is set by FP32 physics, and the
 # IEEE division's range checks and slow path cost more than the division.
 # The FP64 step keeps IEEE arithmetic throughout.
-UNIT_FLAGS = {"qp_step_mixed.cu": ["-prec-div=false"]}
+# The coalescence forms its groups and sums with the oracle's FP64
+# operations in the oracle's order: no FMA contraction there.
+UNIT_FLAGS = {"qp_step_mixed.cu": ["-prec-div=false"], "qp_coalesce.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

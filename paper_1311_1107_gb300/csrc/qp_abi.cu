@@ -59,6 +59,9 @@ struct qp_ctx {
     double *d_diag = nullptr;         // partials + final
     double *d_stash = nullptr;        // append records of qp_step launches
     size_t stash_blocks = 0;          // blocks the stash is sized for
+    void *d_coal = nullptr;           // scratch of qp_coalesce_photons
+    size_t coal_bytes = 0;
+    long long *d_coal_stats = nullptr;  // [4] of the last coalescence
     std::vector<SpeciesRec> species;
     int grid_cache[2][2][5];          // [batch][precision][field] blocks per SM, 0 = unknown
     // kernel timing (qp_profile_*): event pool and (kernel, start event) records
@@ -127,6 +130,8 @@ void release(qp_ctx *c)
     cudaFree(c->d_chain);
     cudaFree(c->d_diag);
     cudaFree(c->d_stash);
+    cudaFree(c->d_coal);
+    cudaFree(c->d_coal_stats);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -926,6 +931,66 @@ int qp_diagnostics(qp_ctx *ctx, int32_t handle, qp_diag *out, void *stream)
     out->e_dropped = ds.e_dropped;
     out->status = status;
     return status;
+}
+
+static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+int qp_coalesce_photons(qp_ctx *ctx, int32_t handle, const qp_coalesce_params *P,
+                        qp_coalesce_stats *out, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &d = ctx->species[handle].d;
+    if (d.kind != QP_PHOTON || d.capacity >= (int64_t)0xFFFFFFFFll) return QP_ERR_INVALID_ARG;
+    if (P) {
+        if (P->min_group < 3 || !pow2_in(P->energy_bins_per_octave, 1, 64) ||
+            !pow2_in(P->direction_bins, 1, 64) || !(P->dx > 0.0) || !(P->dy > 0.0) ||
+            (d.dims == 3 && !(P->dz > 0.0)) || P->nx < 1 || P->ny < 1 || P->nz < 1 ||
+            (d.dims == 2 && P->nz != 1) || !isfinite(P->x0) || !isfinite(P->y0) ||
+            !isfinite(P->z0))
+            return QP_ERR_INVALID_ARG;
+        // the key space (cells x 2048 E x 6 D^2) must stay below 2^63
+        const double space = (double)P->nx * (double)P->ny * (double)P->nz * 2048.0 *
+                             P->energy_bins_per_octave * 6.0 * P->direction_bins *
+                             P->direction_bins;
+        if (!(space < 9.2e18)) return QP_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    const int grid = 2 * ctx->num_sms;
+    const size_t bytes = qp::coalesce_scratch_bytes(d.capacity, grid);
+    if (bytes > ctx->coal_bytes) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(ctx->d_coal);
+        ctx->d_coal = p;
+        ctx->coal_bytes = bytes;
+    }
+    if (!ctx->d_coal_stats) {
+        cudaError_t e = cudaMalloc(&ctx->d_coal_stats, 4 * sizeof(long long));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = qp::launch_coalesce(species_dev(ctx, handle), P, ctx->d_coal, grid,
+                                        ctx->d_coal_stats, ctx->d_status, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (out) {
+        long long h[4];
+        e = cudaMemcpyAsync(h, ctx->d_coal_stats, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        out->groups_merged = h[0];
+        out->photons_merged = h[1];
+        out->n_before = h[2];
+        out->n_after = h[3];
+    }
+    return QP_OK;
+}
+
+int qp_compact_photons(qp_ctx *ctx, int32_t handle, qp_coalesce_stats *out, void *stream)
+{
+    return qp_coalesce_photons(ctx, handle, nullptr, out, stream);
 }
 
 int qp_export_tables(qp_ctx *ctx, qp_tables_export *out)

@@ -24,6 +24,14 @@ cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, in
 cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit, int *status,
                                  cudaStream_t st);
 
+// Compaction / coalescence of a photon species (qp_coalesce.cu): scratch
+// bytes for `cap` slots and `grid` blocks, and the stream-ordered pipeline
+// (P = NULL: compaction only).  stats: 4 device int64 (groups merged,
+// photons merged, slots before, slots after).
+size_t coalesce_scratch_bytes(int64_t cap, int grid);
+cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, void *scratch,
+                            int grid, long long *stats, int *status, cudaStream_t st);
+
 constexpr int kDiagBlocks = 256;
 constexpr int kDiagWords = 8 + QP_HIST_BINS;  // scalars + histogram per block
 

@@ -98,13 +98,30 @@ class QPError(RuntimeError):
 _lock = threading.Lock()
 _lib = None
 
+class qp_coalesce_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("x0", "y0", "z0", "dx", "dy", "dz")] + [
+        ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
+        ("energy_bins_per_octave", C.c_int32), ("direction_bins", C.c_int32),
+        ("min_group", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+        ("step", C.c_int64)]
+
+
+class qp_coalesce_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("groups_merged", "photons_merged", "n_before",
+                                         "n_after")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
            "qp_species_copy",
            "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
            "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
            "qp_batch_create", "qp_batch_destroy", "qp_batch_scratch_words", "qp_batch_set",
-           "qp_batch_clear", "qp_batch_step", "qp_batch_progress")
+           "qp_batch_clear", "qp_batch_step", "qp_batch_progress", "qp_coalesce_photons",
+           "qp_compact_photons")
 
 
 def library_path() -> str:
@@ -147,6 +164,9 @@ def lib(build_if_missing: bool = False):
         L.qp_batch_step.argtypes = [vp, i32, vp]
         L.qp_batch_progress.argtypes = [vp, vp, vp, vp, vp]
         L.qp_status_string.argtypes = [C.c_int]
+        L.qp_coalesce_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_params),
+                                          C.POINTER(qp_coalesce_stats), vp]
+        L.qp_compact_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_stats), vp]
         L.qp_status_string.restype = C.c_char_p
         for name in EXPORTS:
             if name != "qp_status_string":
@@ -299,3 +319,32 @@ def qp_batch_progress(batch, steps_left_ptr: int, next_step_ptr: int | None = No
     opt = lambda p: None if p is None else C.c_void_p(p)
     return _check("qp_batch_progress", lib().qp_batch_progress(
         batch, C.c_void_p(steps_left_ptr), opt(next_step_ptr), opt(work_ptr), stream))
+
+
+def coalesce_params(box, cells, energy_bins_per_octave=8, direction_bins=8, min_group=3,
+                    seed=0, step=0) -> qp_coalesce_params:
+    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz)."""
+    p = qp_coalesce_params()
+    p.x0, p.y0, p.z0, p.dx, p.dy, p.dz = (float(v) for v in box)
+    p.nx, p.ny, p.nz = (int(v) for v in cells)
+    p.energy_bins_per_octave, p.direction_bins = energy_bins_per_octave, direction_bins
+    p.min_group, p.seed, p.step = min_group, seed, step
+    return p
+
+
+def qp_coalesce_photons(ctx, handle: int, params: qp_coalesce_params | None, stream=None,
+                        stats: bool = True):
+    """Compaction (params None) or coalescence of a photon species; with
+    stats, synchronises the stream and returns the counts as a dict."""
+    out = qp_coalesce_stats() if stats else None
+    _check("qp_coalesce_photons",
+           lib().qp_coalesce_photons(ctx, handle, None if params is None else C.byref(params),
+                                     None if out is None else C.byref(out), stream))
+    return out.as_dict() if out is not None else None
+
+
+def qp_compact_photons(ctx, handle: int, stream=None, stats: bool = True):
+    out = qp_coalesce_stats() if stats else None
+    _check("qp_compact_photons",
+           lib().qp_compact_photons(ctx, handle, None if out is None else C.byref(out), stream))
+    return out.as_dict() if out is not None else None

@@ -54,7 +54,9 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(tmp_path):
     structs = {"qp_table_params": Q.qp_table_params, "qp_species_desc": Q.qp_species_desc,
                "qp_field": Q.qp_field, "qp_step_params": Q.qp_step_params,
-               "qp_diag": Q.qp_diag, "qp_tables_export": Q.qp_tables_export}
+               "qp_diag": Q.qp_diag, "qp_tables_export": Q.qp_tables_export,
+               "qp_coalesce_params": Q.qp_coalesce_params,
+               "qp_coalesce_stats": Q.qp_coalesce_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qedpic.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
