@@ -12,6 +12,8 @@ The line also carries
       and pair buffers, the K steps from step 980, around the pulse peak),
       mixed and FP64, each with its roofline: the many-particle state in
       which the step's HBM bound can be approached;
+  `refill`: the same foil with its E_y and B_z refilled from the pulse
+      before every step (qp_fill_yee2d), mixed and FP64;
   `serving`: the 256-request stream of beam-collision requests (n_e
       log-uniform 1e3-1e6) served with continuous batching (Poisson arrivals
       at ~70 % of the measured batched throughput), its throughput and
@@ -650,6 +652,20 @@ def ours_arm(args):
                 "status": {"mixed": c["mixed"]["status"], "fp64": c["fp64"]["status"]},
                 "launches": c["mixed"]["launches"] + c["fp64"]["launches"]}
         del wc
+    # the same foil with its fields refilled from the pulse before every step
+    # (qp_fill_yee2d: two more launches a step, inside the timed steps)
+    refill = None
+    if world == 1 and args.workload == "foil" and not args.no_collision:
+        from paper_1311_1107_gb300 import workloads as W
+        wr = W.laser_on_foil(seed=0, refill=True)
+        r = leg(wr, args, dev, dist, flush, ids, "k_step_foil2d.md", hbm_peak, peak_kind)
+        refill = {"workload": wr["name"], "value": r["mixed"]["value"], "unit": UNIT,
+                  "ms_per_step": r["mixed"]["ms_per_step"],
+                  "roofline": dict(r["mixed"]["roofline"], traffic=None,
+                                   traffic_read_write=None),
+                  "fp64": {k: r["fp64"][k] for k in ("value", "ms_per_step")},
+                  "status": {"mixed": r["mixed"]["status"], "fp64": r["fp64"]["status"]}}
+        del wr
     serv = None
     if rank == 0 and world == 1 and not args.no_serving:
         serv = serving(dev, args.requests or 256, args.serving_nmax or 1e6)
@@ -685,7 +701,7 @@ def ours_arm(args):
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
                      "final_live": main_leg["fp64"]["final_live"]},
             "roofline": main_leg["mixed"]["roofline"],
-            "collision": coll,
+            "collision": coll, "refill": refill,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
             "clocks": clk,
             "status": {"mixed": main_leg["mixed"]["status"], "fp64": main_leg["fp64"]["status"]},

@@ -356,6 +356,34 @@ typedef struct {
  * (caller-owned).  Synchronous. */
 int qp_export_tables(qp_ctx *ctx, qp_tables_export *out);
 
+/* ---- refill of a 2D Yee grid from the analytic pulse ----------------------- */
+
+/* A 2D paraxial Gaussian pulse along +x, polarised along y (normalised
+ * units; not in the paper: the laser of the foil workload):
+ *   xi = x - x_focus, eta = (t - t_focus) - xi, zr = w0^2/2, q = xi/zr,
+ *   E_y = B_z = a0 (1 + q^2)^(-1/4) exp(-r^2/(w0^2 (1 + q^2)) - 2 ln2 eta^2/tau^2)
+ *               cos(-eta + r^2 xi/(2 (xi^2 + zr^2)) - atan(q)/2),  r = y - y_axis. */
+typedef struct {
+    double a0, w0, tau_fwhm, x_focus, t_focus, y_axis;
+} qp_pulse2d;
+
+/*
+ * Per-step refill of a 2D Yee grid's fields from the pulse at time t (the
+ * fields a fixed snapshot freezes: the refill lets them follow the pulse
+ * across the target; the PIC context of the paper's section 3).  Writes E_y
+ * at (x0 + i dx, y0 + (j + 1/2) dy) and B_z at (x0 + (i + 1/2) dx, y0 +
+ * (j + 1/2) dy) of `grid` (kind QP_FIELD_YEE2D; its yee[1] and yee[5] are
+ * written through, the other components are not touched).  The x-dependent
+ * factors (amplitude, envelope, Gouy phase and curvature, the phase reduced
+ * modulo 2 pi) are formed per column in FP64, the nodes in FP32: every node
+ * is within ~1e-6 of a0 of the FP64 formula rounded to float.  Give the
+ * step that follows t = n dt, as the particle step evaluates its fields at
+ * that time.  Stream-ordered; the first call for a grid size allocates
+ * context scratch (32 nx + 4 ny bytes).  QP_ERR_INVALID_ARG for a grid of
+ * another kind, missing E_y/B_z pointers or a non-positive size.
+ */
+int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double t, void *stream);
+
 /* ---- super-photon compaction and coalescence ---------------------------- */
 
 /* Grid and bins of qp_coalesce_photons.  A live photon belongs to the group

@@ -90,6 +90,11 @@ class CoalesceStats(C.Structure):
                                          "photons_merged")]
 
 
+class Pulse2D(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("a0", "w0", "tau_fwhm", "x_focus", "t_focus",
+                                          "y_axis")]
+
+
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("n_emit", "n_photon", "n_photon_drop",
                                          "n_subthreshold", "n_pair", "n_pair_drop",
@@ -139,6 +144,8 @@ def lib():
             "or_init_tau": (None, [C.c_uint64, C.c_int, vp, i64, i64]),
             "or_coalesce": (C.c_int, [C.POINTER(_Species), C.POINTER(CoalesceParams),
                                       C.POINTER(CoalesceStats)]),
+            "or_pulse2d_eval": (d, [C.POINTER(Pulse2D), d, d, d]),
+            "or_fill_pulse2d": (None, [C.POINTER(Pulse2D), vp, vp, i64, i64, d, d, d, d, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -310,7 +317,7 @@ def yee2d_field(comps, dx, dy, x0=0.0, y0=0.0) -> Field:
     """comps: 6 float32 arrays (Ex Ey Ez Bx By Bz) of shape (ny, nx)."""
     f = Field()
     f.kind = FIELD_YEE2D
-    keep = [np.ascontiguousarray(c, dtype=np.float32) for c in comps]
+    keep = [np.array(c, dtype=np.float32, copy=True, order="C") for c in comps]
     ny, nx = keep[0].shape
     for k, c in enumerate(keep):
         f.yee[k] = c.ctypes.data
@@ -453,3 +460,26 @@ def coalesce(sp: Species, params: CoalesceParams | None):
         raise ValueError("or_coalesce: bad parameters")
     sp.n = s.n
     return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def pulse2d(a0, w0, tau_fwhm, x_focus, t_focus, y_axis) -> Pulse2D:
+    p = Pulse2D()
+    p.a0, p.w0, p.tau_fwhm, p.x_focus, p.t_focus, p.y_axis = (float(v) for v in (
+        a0, w0, tau_fwhm, x_focus, t_focus, y_axis))
+    return p
+
+
+def pulse2d_eval(p: Pulse2D, x, y, t):
+    f = lib().or_pulse2d_eval
+    return np.vectorize(lambda a, b, c: f(C.byref(p), float(a), float(b), float(c)),
+                        otypes=[float])(x, y, t)
+
+
+def fill_pulse2d(p: Pulse2D, field: Field, t: float):
+    """Refill E_y and B_z of a yee2d_field (its float32 arrays, in place)
+    with the pulse at time t."""
+    ey, bz = field._keep[1], field._keep[5]
+    lib().or_fill_pulse2d(C.byref(p), ey.ctypes.data_as(C.c_void_p),
+                          bz.ctypes.data_as(C.c_void_p), int(field.nx), int(field.ny),
+                          float(field.dx), float(field.dy), float(field.x0), float(field.y0),
+                          float(t))

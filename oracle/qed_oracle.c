@@ -1358,3 +1358,49 @@ int or_coalesce(or_species *Ph, const or_coalesce_params *C, or_coalesce_stats *
     free(ks);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Refill of a 2D Yee grid from the analytic pulse                            */
+/* ------------------------------------------------------------------------- */
+
+/* The fields of a 2D paraxial Gaussian pulse along +x, polarised along y
+ * (the laser of the foil workload; not in the paper), at time t:
+ *   xi = x - x_focus, eta = (t - t_focus) - xi, zr = w0^2/2, q = xi/zr,
+ *   E_y = B_z = a0 (1 + q^2)^(-1/4) exp(-r^2/(w0^2 (1 + q^2)) - 2 ln2 eta^2/tau^2)
+ *               cos(-eta + r^2 xi / (2 (xi^2 + zr^2)) - atan(q)/2),
+ * r = y - y_axis (the Gouy phase of a 2D beam is half that of a 3D one).
+ * READING: the per-step refill of the fixed snapshot (the workload's fields
+ * follow the pulse as it crosses the foil); E and B both at t. */
+typedef struct {
+    double a0, w0, tau_fwhm, x_focus, t_focus, y_axis;
+} or_pulse2d;
+
+double or_pulse2d_eval(const or_pulse2d *p, double x, double y, double t)
+{
+    double xi = x - p->x_focus;
+    double eta = (t - p->t_focus) - xi;
+    double zr = 0.5 * p->w0 * p->w0;
+    double q = xi / zr;
+    double wr2 = 1.0 + q * q;
+    double r2 = (y - p->y_axis) * (y - p->y_axis);
+    double env = -r2 / (p->w0 * p->w0 * wr2) -
+                 2.0 * log(2.0) * eta * eta / (p->tau_fwhm * p->tau_fwhm);
+    double amp = p->a0 * pow(wr2, -0.25) * exp(env);
+    double phase = -eta + r2 * xi / (2.0 * (xi * xi + zr * zr)) - 0.5 * atan(q);
+    return amp * cos(phase);
+}
+
+/* E_y at (x0 + i dx, y0 + (j + 1/2) dy) and B_z at (x0 + (i + 1/2) dx,
+ * y0 + (j + 1/2) dy), each rounded to float; ny rows of nx values.  The
+ * other components are not touched. */
+void or_fill_pulse2d(const or_pulse2d *p, float *ey, float *bz, int64_t nx, int64_t ny,
+                     double dx, double dy, double x0, double y0, double t)
+{
+    for (int64_t j = 0; j < ny; j++) {
+        double y = y0 + ((double)j + 0.5) * dy;
+        for (int64_t i = 0; i < nx; i++) {
+            ey[j * nx + i] = (float)or_pulse2d_eval(p, x0 + (double)i * dx, y, t);
+            bz[j * nx + i] = (float)or_pulse2d_eval(p, x0 + ((double)i + 0.5) * dx, y, t);
+        }
+    }
+}

@@ -174,4 +174,69 @@ cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, in
     return cudaGetLastError();
 }
 
+// -------------------------------------------------------------------- pulse refill
+
+// Per-column factors of the 2D pulse (FP64, one thread per Ey column, Bz
+// column and row): E = A exp(-c r^2) cos(phi + kappa r^2) with
+// A = a0 (1 + q^2)^(-1/4) exp(-2 ln2 eta^2/tau^2), c = 1/(w0^2 (1 + q^2)),
+// kappa = xi / (2 (xi^2 + zr^2)), phi = -eta - atan(q)/2 reduced to
+// [-pi, pi]; rows: r^2 = (y - y_axis)^2.  The nodes then need only FP32.
+__global__ void k_pulse_cols(Pulse2DDev p, int64_t nx, int64_t ny, double dx, double dy,
+                             double x0, double y0, double t, float4 *cols, float *rows)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 2 * nx) {
+        const int s = k >= nx ? 1 : 0;
+        const int64_t i = k - s * nx;
+        const double x = x0 + ((double)i + 0.5 * s) * dx;
+        const double xi = x - p.x_focus;
+        const double eta = (t - p.t_focus) - xi;
+        const double zr = 0.5 * p.w0 * p.w0;
+        const double q = xi / zr;
+        const double wr2 = 1.0 + q * q;
+        const double A = p.a0 * pow(wr2, -0.25) *
+                         exp(-2.0 * 0.69314718055994530942 * eta * eta / (p.tau_fwhm * p.tau_fwhm));
+        double phi = -eta - 0.5 * atan(q);
+        phi -= 6.283185307179586477 * rint(phi * 0.15915494309189533577);
+        cols[k] = make_float4((float)A, (float)(1.0 / (p.w0 * p.w0 * wr2)),
+                              (float)(xi / (2.0 * (xi * xi + zr * zr))), (float)phi);
+    } else if (k < 2 * nx + ny) {
+        const int64_t j = k - 2 * nx;
+        const double r = y0 + ((double)j + 0.5) * dy - p.y_axis;
+        rows[j] = (float)(r * r);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pulse_fill(const float4 *cols, const float *rows,
+                                                    int64_t nx, int64_t ny, float *ey,
+                                                    float *bz)
+{
+    const int64_t n = nx * ny;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const int64_t j = k / nx, i = k - j * nx;
+        const float r2 = rows[j];
+        const float4 e = cols[i], b = cols[nx + i];
+        ey[k] = e.x * expf(-e.y * r2) * cosf(fmaf(e.z, r2, e.w));
+        bz[k] = b.x * expf(-b.y * r2) * cosf(fmaf(b.z, r2, b.w));
+    }
+}
+
+cudaError_t launch_pulse_fill(const Pulse2DDev &p, int64_t nx, int64_t ny, double dx, double dy,
+                              double x0, double y0, double t, float *ey, float *bz, float4 *cols,
+                              float *rows, int num_sms, cudaStream_t st)
+{
+    if (nx <= 0 || ny <= 0) return cudaSuccess;
+    const int64_t m = 2 * nx + ny;
+    k_pulse_cols<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(p, nx, ny, dx, dy, x0, y0, t, cols,
+                                                               rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (nx * ny + 255) / 256;
+    const int64_t cap = (int64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_pulse_fill<<<(unsigned)blocks, 256, 0, st>>>(cols, rows, nx, ny, ey, bz);
+    return cudaGetLastError();
+}
+
 }  // namespace qp

@@ -98,6 +98,11 @@ class QPError(RuntimeError):
 _lock = threading.Lock()
 _lib = None
 
+class qp_pulse2d(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("a0", "w0", "tau_fwhm", "x_focus", "t_focus",
+                                          "y_axis")]
+
+
 class qp_coalesce_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("x0", "y0", "z0", "dx", "dy", "dz")] + [
         ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
@@ -121,7 +126,7 @@ EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
            "qp_batch_create", "qp_batch_destroy", "qp_batch_scratch_words", "qp_batch_set",
            "qp_batch_clear", "qp_batch_step", "qp_batch_progress", "qp_coalesce_photons",
-           "qp_compact_photons")
+           "qp_compact_photons", "qp_fill_yee2d")
 
 
 def library_path() -> str:
@@ -167,6 +172,8 @@ def lib(build_if_missing: bool = False):
         L.qp_coalesce_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_params),
                                           C.POINTER(qp_coalesce_stats), vp]
         L.qp_compact_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_stats), vp]
+        L.qp_fill_yee2d.argtypes = [vp, C.POINTER(qp_pulse2d), C.POINTER(qp_field), C.c_double,
+                                    vp]
         L.qp_status_string.restype = C.c_char_p
         for name in EXPORTS:
             if name != "qp_status_string":
@@ -348,3 +355,15 @@ def qp_compact_photons(ctx, handle: int, stream=None, stats: bool = True):
     _check("qp_compact_photons",
            lib().qp_compact_photons(ctx, handle, None if out is None else C.byref(out), stream))
     return out.as_dict() if out is not None else None
+
+
+def pulse2d(a0, w0, tau_fwhm, x_focus, t_focus, y_axis) -> qp_pulse2d:
+    p = qp_pulse2d()
+    p.a0, p.w0, p.tau_fwhm, p.x_focus, p.t_focus, p.y_axis = (float(v) for v in (
+        a0, w0, tau_fwhm, x_focus, t_focus, y_axis))
+    return p
+
+
+def qp_fill_yee2d(ctx, pulse: qp_pulse2d, grid: qp_field, t: float, stream=None) -> int:
+    return _check("qp_fill_yee2d",
+                  lib().qp_fill_yee2d(ctx, C.byref(pulse), C.byref(grid), float(t), stream))

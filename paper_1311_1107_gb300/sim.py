@@ -146,6 +146,9 @@ class Simulation:
             for k, name in enumerate(("electron", "positron", "photon"))
         }
         self.field, self._keep = make_field(workload["field"], self.dev)
+        rf = workload["field"].get("refill")
+        self.pulse = (Q.pulse2d(rf["a0"], rf["w0"], rf["tau_fwhm"], rf["x_focus"],
+                                rf["t_focus"], rf["y_axis"]) if rf else None)
         p = workload["params"]
         s = Q.qp_step_params()
         s.field = self.field
@@ -178,6 +181,17 @@ class Simulation:
         self.step_index = int(self.workload["params"].get("step", 0))
 
     def run(self, n_steps: int, stream=None) -> int:
+        if self.pulse is not None:
+            # fields refilled from the pulse at each step's time, then the step
+            st = 0
+            for _ in range(int(n_steps)):
+                Q.qp_fill_yee2d(self.ctx, self.pulse, self.field,
+                                self.step_index * self.params.dt, stream_handle(stream))
+                self.params.step = self.step_index
+                self.params.n_steps = 1
+                st = max(st, Q.qp_step(self.ctx, self.params, stream_handle(stream)))
+                self.step_index += 1
+            return st
         self.params.step = self.step_index
         self.params.n_steps = int(n_steps)
         st = Q.qp_step(self.ctx, self.params, stream_handle(stream))

@@ -98,11 +98,15 @@ def gaussian_2d_snapshot(nx: int, ny: int, dx: float, dy: float, a0: float, w0: 
 
 def laser_on_foil(nx: int = 2048, ny: int = 512, ppc: int = 8, a0: float = 200.0,
                   n_steps: int = 500, seed: int = 0, foil_cells: int = 32,
-                  photon_capacity: int = 1 << 25, pair_capacity: int = 1 << 20):
+                  photon_capacity: int = 1 << 25, pair_capacity: int = 1 << 20,
+                  refill: bool = False):
     """2048x512 grid, dx = lambda/32, a 1-lambda foil of electrons at
     n = 100 n_c, 8 per cell, Maxwellian 1 keV, in the fixed fields of a
     Gaussian pulse (a0 200, waist 3 lambda, 30 fs FWHM) whose peak sits at the
-    foil front.  Sokolov damping below chi 1e-3, Monte-Carlo above."""
+    foil front.  Sokolov damping below chi 1e-3, Monte-Carlo above.
+    refill: the grid's E_y and B_z are refilled from the pulse before every
+    step instead (qp_fill_yee2d); the pulse's peak reaches the foil front at
+    mid-run; the grid starts empty."""
     rng = np.random.default_rng(seed)
     dx = dy = T_PERIOD / 32.0
     i0 = nx // 2
@@ -116,15 +120,23 @@ def laser_on_foil(nx: int = 2048, ny: int = 512, ppc: int = 8, a0: float = 200.0
     u = rng.normal(0.0, sigma_u, size=(3, n))
     w = np.full(n, 100.0 * dx * dy / ppc)
     el = {"x": x, "y": y, "ux": u[0], "uy": u[1], "uz": u[2], "w": w}
-    comps = gaussian_2d_snapshot(nx, ny, dx, dy, a0=a0, w0=length(3 * LAMBDA_M),
-                                 tau_fwhm=duration(30e-15), x_focus=i0 * dx,
-                                 y_axis=0.5 * ny * dy)
+    w0, tau = length(3 * LAMBDA_M), duration(30e-15)
+    dt = 0.95 * dx / math.sqrt(2.0)
+    field = {"kind": "yee2d", "dx": dx, "dy": dy, "x0": 0.0, "y0": 0.0}
+    if refill:
+        field["comps"] = [np.zeros((ny, nx), dtype=np.float32) for _ in range(6)]
+        field["refill"] = {"a0": a0, "w0": w0, "tau_fwhm": tau, "x_focus": i0 * dx,
+                           "t_focus": (n_steps // 2) * dt, "y_axis": 0.5 * ny * dy}
+    else:
+        field["comps"] = gaussian_2d_snapshot(nx, ny, dx, dy, a0=a0, w0=w0, tau_fwhm=tau,
+                                              x_focus=i0 * dx, y_axis=0.5 * ny * dy)
     return {
-        "name": f"2D laser-on-foil: {nx}x{ny} Yee grid, {n} e-, a0 {a0:g}, {n_steps} steps",
+        "name": (f"2D laser-on-foil: {nx}x{ny} Yee grid, {n} e-, a0 {a0:g}, {n_steps} steps"
+                 + (", fields refilled from the pulse every step" if refill else "")),
         "dims": 2,
         "electrons": el,
-        "field": {"kind": "yee2d", "comps": comps, "dx": dx, "dy": dy, "x0": 0.0, "y0": 0.0},
-        "params": {"dt": 0.95 * dx / math.sqrt(2.0), "n_steps": n_steps, "seed": seed,
+        "field": field,
+        "params": {"dt": dt, "n_steps": n_steps, "seed": seed,
                    "chi_th": 1e-3, "photon_min_gamma": 2.0, "pairs": True, "max_emit": 8},
         "capacity": {"electron": n + pair_capacity, "positron": pair_capacity,
                      "photon": photon_capacity},

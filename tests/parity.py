@@ -28,6 +28,27 @@ def oracle_field(desc):
     return f
 
 
+def oracle_pulse(desc):
+    rf = desc.get("refill")
+    if not rf:
+        return None
+    return O.pulse2d(rf["a0"], rf["w0"], rf["tau_fwhm"], rf["x_focus"], rf["t_focus"],
+                     rf["y_axis"])
+
+
+def oracle_steps(sim, workload, n_steps):
+    """n_steps of an oracle run; a workload with a refilled grid gets the
+    oracle's own refill (from the pulse, FP64 rounded to float) before each
+    step."""
+    pulse = oracle_pulse(workload["field"])
+    if pulse is None:
+        sim.run(n_steps)
+        return
+    for _ in range(n_steps):
+        O.fill_pulse2d(pulse, sim.field, sim.P.step * sim.P.dt)
+        sim.run(1)
+
+
 def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, noise_key=0):
     """Run the oracle on a workload.  sample: optional slot indices of the
     electrons to keep (each keeps its random stream).  extra: optional dict
@@ -79,7 +100,7 @@ def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, 
         params["noise_key"] = noise_key
     sim = O.Sim(oracle_field(workload["field"]), params, electrons=el, positrons=po,
                 photons=ph)
-    sim.run(n_steps)
+    oracle_steps(sim, workload, n_steps)
     return sim, {"electron": el, "positron": po, "photon": ph}
 
 
@@ -105,7 +126,7 @@ def run_oracle_from_state(workload, state, step, n_steps=1):
     params["step"] = int(step)
     sim = O.Sim(oracle_field(workload["field"]), params, electrons=sps["electron"],
                 positrons=sps["positron"], photons=sps["photon"])
-    sim.run(n_steps)
+    oracle_steps(sim, workload, n_steps)
     return sim, sps
 
 

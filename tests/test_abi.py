@@ -56,7 +56,7 @@ def test_struct_layouts_match_header(tmp_path):
                "qp_field": Q.qp_field, "qp_step_params": Q.qp_step_params,
                "qp_diag": Q.qp_diag, "qp_tables_export": Q.qp_tables_export,
                "qp_coalesce_params": Q.qp_coalesce_params,
-               "qp_coalesce_stats": Q.qp_coalesce_stats}
+               "qp_coalesce_stats": Q.qp_coalesce_stats, "qp_pulse2d": Q.qp_pulse2d}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qedpic.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
