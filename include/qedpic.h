@@ -230,6 +230,28 @@ typedef struct {
  */
 int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream);
 
+/*
+ * Fused steps: the s->n_steps steps of qp_step, `fuse` steps per launch
+ * window, every lepton held in registers from the first step of a window to
+ * its last (the data-parallel step has nothing to exchange between
+ * particles when the fields are given: analytic fields, or a Yee grid that
+ * stays fixed over the call).  Requires s->pairs == 0: leptons then never
+ * change in number and photons only move.  The results are those of
+ * qp_step with the same parameters, bit for bit: the same per-particle
+ * arithmetic, photons in the same slots (step, then emitter slot, then
+ * emission index), the same counters.  A window is a count pass (photons
+ * stored per step and 32-lepton tile), a scan of the counts into first
+ * slots, a write pass (the same physics again; photons written at their
+ * slots) and the motion of the window's photons, one thread a photon (those
+ * that existed at its start over K steps, the new ones over the steps left
+ * after their birth).  The call reads the live lepton counts to the host
+ * once (it synchronises `stream`) and grows the context's scratch (12 bytes
+ * per step and tile, 2 per photon slot; an allocation): not during a stream
+ * capture.  Windows hold at most 65535 steps.  QP_ERR_INVALID_ARG (nothing
+ * enqueued) for pairs on, fuse < 1, or what qp_step rejects.
+ */
+int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stream);
+
 /* ---- batches: several independent runs in shared launches --------------
  *
  * A batch is a device table of up to max_problems independent problems

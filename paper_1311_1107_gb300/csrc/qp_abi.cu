@@ -59,6 +59,8 @@ struct qp_ctx {
     double *d_diag = nullptr;         // partials + final
     double *d_stash = nullptr;        // append records of qp_step launches
     size_t stash_blocks = 0;          // blocks the stash is sized for
+    void *d_fuse = nullptr;           // scratch of qp_step_fused
+    size_t fuse_bytes = 0;
     void *d_pulse = nullptr;          // scratch of qp_fill_yee2d
     size_t pulse_bytes = 0;
     void *d_coal = nullptr;           // scratch of qp_coalesce_photons
@@ -135,6 +137,7 @@ void release(qp_ctx *c)
     cudaFree(c->d_coal);
     cudaFree(c->d_coal_stats);
     cudaFree(c->d_pulse);
+    cudaFree(c->d_fuse);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -934,6 +937,69 @@ int qp_diagnostics(qp_ctx *ctx, int32_t handle, qp_diag *out, void *stream)
     out->e_dropped = ds.e_dropped;
     out->status = status;
     return status;
+}
+
+int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!s || fuse < 1 || s->pairs) return QP_ERR_INVALID_ARG;
+    qp::StepArgs a{};
+    int st = build_problem(ctx, s, a.single);
+    if (st != QP_OK) return st;
+    if (s->n_steps == 0) return QP_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the lepton counts (they do not change without pairs): read once
+    long long n[2] = {0, 0};
+    const int32_t hs[2] = {s->electron, s->positron};
+    for (int k = 0; k < 2; ++k) {
+        if (hs[k] == -1) continue;
+        const qp_species_desc &d = ctx->species[hs[k]].d;
+        cudaError_t e = cudaMemcpyAsync(&n[k], d.n_live, sizeof(long long),
+                                        cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < 2; ++k) {
+        const int64_t cap = hs[k] == -1 ? 0 : ctx->species[hs[k]].d.capacity;
+        if (n[k] < 0 || n[k] > cap) return QP_ERR_INVALID_ARG;
+    }
+    const long long tiles_e = (n[0] + 31) / 32, tiles = tiles_e + (n[1] + 31) / 32;
+    const int K = fuse < s->n_steps ? fuse : s->n_steps;
+    if (K > 65535) return QP_ERR_INVALID_ARG;
+    const size_t entries = (size_t)K * (size_t)(tiles > 0 ? tiles : 1);
+    const int64_t cap_g = s->photon == -1 ? 0 : ctx->species[s->photon].d.capacity;
+    const size_t bytes = entries * sizeof(int) + 256 + entries * sizeof(long long) + 256 + 16 +
+                         256 + (size_t)(cap_g > 0 ? cap_g : 1) * sizeof(unsigned short);
+    if (bytes > ctx->fuse_bytes) {
+        void *p = nullptr;
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(ctx->d_fuse);
+        ctx->d_fuse = p;
+        ctx->fuse_bytes = bytes;
+    }
+    int *counts = (int *)ctx->d_fuse;
+    long long *offs = (long long *)((char *)ctx->d_fuse + (entries * sizeof(int) + 255) / 256 * 256);
+    long long *win = offs + (entries + 31) / 32 * 32;
+    unsigned short *moves = (unsigned short *)(win + 32);
+    fill_globals(ctx, a);
+    a.ctl = ctx->d_ctl;
+    qp::Problem &P = a.single;
+    P.pending = ctx->d_pending;
+    P.device_step = 0;
+    for (int32_t w0 = 0; w0 < s->n_steps; w0 += K) {
+        const int Kw = s->n_steps - w0 < K ? s->n_steps - w0 : K;
+        set_time_host(P, s->step + w0);
+        e = timed(ctx, 0, cs, [&] {
+            return qp::launch_fused(a, s->precision, s->field.kind, Kw, tiles_e, tiles, counts,
+                                    offs, win, moves, ctx->num_sms, cs);
+        });
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return QP_OK;
 }
 
 int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double t, void *stream)

@@ -152,6 +152,39 @@ cudaError_t launch_step(const StepArgs &a, int precision, int field_kind, bool b
     return cudaLaunchKernel(fn, dim3(grid), dim3(kTile), args, smem, st);
 }
 
+cudaError_t launch_fused(const StepArgs &a, int precision, int field_kind, int K,
+                         long long tiles_e, long long tiles, int *counts, long long *offs,
+                         long long *win, unsigned short *moves, int num_sms, cudaStream_t st)
+{
+    const bool mixed = precision == QP_MIXED;
+    const void *count = mixed ? fused_kernel_mixed(field_kind, 0) : fused_kernel_fp64(field_kind, 0);
+    const void *write = mixed ? fused_kernel_mixed(field_kind, 1) : fused_kernel_fp64(field_kind, 1);
+    const void *photons = mixed ? fused_photons_mixed() : fused_photons_fp64();
+    if (!count || !write) return cudaErrorInvalidValue;
+    FusedArgs f{};
+    f.a = a;
+    f.K = K;
+    f.tiles_e = tiles_e;
+    f.tiles = tiles;
+    f.counts = counts;
+    f.offs = offs;
+    f.win = win;
+    f.moves = moves;
+    void *args[] = {(void *)&f};
+    const long long resident = (long long)num_sms * 32;
+    const unsigned grid = (unsigned)(tiles < resident ? (tiles > 0 ? tiles : 1) : resident);
+    cudaError_t e = cudaLaunchKernel(count, dim3(grid), dim3(32), args, 0, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(fused_scan_kernel(), dim3(1), dim3(1024), args, 0, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(write, dim3(grid), dim3(32), args, 0, st);
+    const long long cap = a.single.sp[2].present ? a.single.sp[2].cap : 0;
+    if (e == cudaSuccess && cap > 0) {
+        long long pb = (cap + 255) / 256;
+        if (pb > (long long)num_sms * 8) pb = (long long)num_sms * 8;
+        e = cudaLaunchKernel(photons, dim3((unsigned)pb), dim3(256), args, 0, st);
+    }
+    return e;
+}
+
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
                             int64_t id_split, int64_t id_append, uint64_t seed, int species,
                             cudaStream_t st)

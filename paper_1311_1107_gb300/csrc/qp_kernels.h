@@ -16,6 +16,17 @@ const void *step_kernel_mixed(int field_kind, bool batch);
 size_t step_smem_fp64();
 size_t step_smem_mixed();
 size_t step_smem_bytes(int precision);
+// Fused steps (qp_step_fused): one window of K steps of the single problem
+// a.single (its time set for the window's first step).  counts and offs hold
+// K x tiles entries, win two, moves one per photon slot.
+cudaError_t launch_fused(const StepArgs &a, int precision, int field_kind, int K,
+                         long long tiles_e, long long tiles, int *counts, long long *offs,
+                         long long *win, unsigned short *moves, int num_sms, cudaStream_t st);
+const void *fused_kernel_fp64(int field_kind, int pass);
+const void *fused_kernel_mixed(int field_kind, int pass);
+const void *fused_photons_fp64();
+const void *fused_photons_mixed();
+const void *fused_scan_kernel();
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
                             int64_t id_split, int64_t id_append, uint64_t seed, int species,
                             cudaStream_t st);

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <stddef.h>
+
 #include <type_traits>
 
 #include "qp_device.cuh"
@@ -237,6 +239,350 @@ __device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepA
 
 // -------------------------------------------------------------------- lepton tile
 
+// State of one lepton at the start of a step (the FP64 storage of both
+// paths; component c of the new state goes to the sink's put<c> as soon as
+// it is formed, c = x y z ux uy uz tau, tau only when it changed).
+struct LeptonState {
+    double x, y, z, ux, uy, uz, tau;
+};
+
+// What one lepton's step produced besides its new state.
+struct LeptonOut {
+    int n_emit, nph, n_sub;
+    double e_sub;   // sum of gamma_gamma of the photons below the cut
+    bool cont, sat, clamped;
+};
+
+// One step of one lepton (a1..a8 of the hot path): fields at (x, t), Boris
+// push, chi_e, then Sokolov damping below chi_th or the optical depth with
+// its emission sub-loop (Eq. 6-8), then the position (Eq. 4).  The sink
+// receives the new state (put<c>, see LeptonState) and what an append needs: tables() before the
+// rate tables H and G are first read, chi(c) with chi_e after the push,
+// direction(k) with the momentum direction before the first recoil,
+// photon(j, gamma, tau) for the j-th stored photon, origin(x) with the
+// position at the start of the step when photons were stored.  S, i: the
+// particle's species and slot (its id keys the random streams).
+template <int PREC, int FK, typename R, class Sink>
+__device__ __forceinline__ void lepton_particle(const StepArgs &a, const Problem &P, const R *H,
+                                                const R *G, int sp, const SpeciesDev &S,
+                                                int64_t i, const LeptonState &s, LeptonOut &o,
+                                                Sink &sink)
+{
+    o.n_emit = o.nph = o.n_sub = 0;
+    o.e_sub = 0.0;
+    o.cont = o.sat = o.clamped = false;
+    bool clamped = false;
+    int nph = 0, n_emit = 0, n_sub = 0;
+    if constexpr (PREC == kFP64) {
+        const double q = sp == 0 ? -1.0 : 1.0;
+        const double dt = P.dt;
+        const double x0 = s.x, y0 = s.y, z0 = s.z;
+        double ux = s.ux, uy = s.uy, uz = s.uz;
+        double tau = s.tau;
+        Vec3<R> E, B;
+        eval_field<FK, R>(P.f, x0, y0, z0, P.t, E, B);
+
+        // ---- Boris push of the Lorentz force (f_l of Eq. 4)
+        {
+            const double h = 0.5 * q * dt;
+            const double mx = ux + h * E.x, my = uy + h * E.y, mz = uz + h * E.z;
+            const double g = sqrt(1.0 + mx * mx + my * my + mz * mz);
+            const double tx = h * B.x / g, ty = h * B.y / g, tz = h * B.z / g;
+            const double t2 = tx * tx + ty * ty + tz * tz;
+            const double sx = 2.0 * tx / (1.0 + t2), sy = 2.0 * ty / (1.0 + t2),
+                         sz = 2.0 * tz / (1.0 + t2);
+            const double px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+                         pz = mz + (mx * ty - my * tx);
+            ux = mx + (py * sz - pz * sy) + h * E.x;
+            uy = my + (pz * sx - px * sz) + h * E.y;
+            uz = mz + (px * sy - py * sx) + h * E.z;
+        }
+        double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+        const double Ex = E.x, Ey = E.y, Ez = E.z, Bx = B.x, By = B.y, Bz = B.z;
+        sink.tables();  // tables are needed from here on
+        double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
+        sink.chi(chi);
+        double dvx = 0.0, dvy = 0.0, dvz = 0.0;
+
+        if (chi < P.chi_th) {
+            // ---- Sokolov continuous regime (Eq. 4, P_rad of Eq. 5)
+            o.cont = true;
+            const double vx = ux / gam, vy = uy / gam, vz = uz / gam;
+            const double fx = q * (Ex + (vy * Bz - vz * By));
+            const double fy = q * (Ey + (vz * Bx - vx * Bz));
+            const double fz = q * (Ez + (vx * By - vy * Bx));
+            const double vf = vx * fx + vy * fy + vz * fz;
+            const double den = 1.0 + a.tau0w * vf;
+            dvx = a.tau0w * (fx - vx * vf) / den;
+            dvy = a.tau0w * (fy - vy * vf) / den;
+            dvz = a.tau0w * (fz - vz * vf) / den;
+            const double prad = a.C_rate * rate64<1>(G, chi, clamped);
+            ux = ux + dt * (q * (dvy * Bz - dvz * By) - prad * vx);
+            uy = uy + dt * (q * (dvz * Bx - dvx * Bz) - prad * vy);
+            uz = uz + dt * (q * (dvx * By - dvy * Bx) - prad * vz);
+            gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+        } else {
+            // ---- optical depth (Eq. 6) with the residual-time sub-loop
+            double r = 1.0;
+            for (int k = 0;; ++k) {
+                const double Hv = rate64<0>(H, chi, clamped);
+                const double wdt = a.C_rate * Hv / gam * dt;
+                const double dtau = wdt * r;
+                if (!(dtau > 0.0) || tau > dtau) {
+                    tau = tau - dtau;
+                    break;
+                }
+                if (k == P.max_emit) {
+                    tau = tau - dtau;
+                    o.sat = true;
+                    break;
+                }
+                r = r - tau / wdt;
+                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
+                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
+                const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
+                const double ufrac = sample_cdf<double>(a.tab.Cg, a.tab.Gg, chi, xi_p, kSgMin,
+                                                        kSgSpan, true, clamped);
+                const double pmag = sqrt(ux * ux + uy * uy + uz * uz);
+                double gg = ufrac * gam;
+                if (gg > pmag) gg = pmag;
+                if (n_emit == 0 && pmag > 0.0) sink.direction(ux / pmag, uy / pmag, uz / pmag);
+                ++n_emit;
+                if (gg > P.gmin) {
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
+                    sink.photon(nph, gg, -log(u53(rp.x, rp.y)));
+                    ++nph;
+                } else {
+                    ++n_sub;
+                    o.e_sub += gg;
+                }
+                if (pmag > 0.0) {
+                    const double scale = (pmag - gg) / pmag;
+                    ux *= scale;
+                    uy *= scale;
+                    uz *= scale;
+                }
+                tau = -log(xi);
+                gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+                chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
+            }
+        }
+
+        // ---- position (Eq. 4: dx/dt = v + delta v)
+        if (nph) sink.origin(x0, y0, z0);
+        sink.template put<0>(x0 + dt * (ux / gam + dvx));
+        sink.template put<1>(y0 + dt * (uy / gam + dvy));
+        sink.template put<2>(z0 + dt * (uz / gam + dvz));
+        sink.template put<3>(ux);
+        sink.template put<4>(uy);
+        sink.template put<5>(uz);
+        sink.template put<6>(tau);
+    } else {
+        // ---- mixed precision: FP32 physics; the FP64 state is read once,
+        // increments are formed in FP32 and added back by integer
+        // instructions; chi_e falls back to double-float where FP32 cancels
+        const MixedConsts &m = P.mc;
+        const double xd = s.x, yd = s.y, zd = s.z;
+        const double uxd = s.ux, uyd = s.uy, uzd = s.uz;
+        const double taud = s.tau;
+        Vec3<float> E, B;
+        eval_field_mixed<FK>(P.f, m, xd, yd, zd, E, B);
+
+        // Boris on the leading FP32 parts; the increment is kept in FP32
+        const float u0x = hi_d(uxd), u0y = hi_d(uyd), u0z = hi_d(uzd);
+        const float h = m.h[sp];
+        const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
+        const float mx = u0x + hx, my = u0y + hy, mz = u0z + hz;
+        const float ig = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+        const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
+        const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
+        const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
+        const float px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
+                    pz = mz + (mx * ty - my * tx);
+        float dux = (py * sz - pz * sy) + 2.0f * hx, duy = (pz * sx - px * sz) + 2.0f * hy,
+              duz = (px * sy - py * sx) + 2.0f * hz;
+        float ux = u0x + dux, uy = u0y + duy, uz = u0z + duz;
+        float gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        sink.tables();  // tables are needed from here on
+        float chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B, m.inv_aS,
+                                   m.inv_aS_lo);
+        sink.chi(f_to_d(chi));
+        float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
+        float dtau_once = 0.0f, esub_f = 0.0f;
+        bool events = false;
+        df2 TAU = {0.0f, 0.0f};
+
+        if (chi < m.chi_th) {
+            // ---- Sokolov (Eq. 4, 5); denominator 1 + tau0 v.f_l in double-float
+            o.cont = true;
+            const float q = sp == 0 ? -1.0f : 1.0f;
+            const float gi = 1.0f / gam;
+            const float vx = ux * gi, vy = uy * gi, vz = uz * gi;
+            const float fx = q * (E.x + (vy * B.z - vz * B.y));
+            const float fy = q * (E.y + (vz * B.x - vx * B.z));
+            const float fz = q * (E.z + (vx * B.y - vy * B.x));
+            const float vf = vx * fx + vy * fy + vz * fz;
+            const df2 den = two_sum(1.0f, m.tau0w * vf);
+            const float c = m.tau0w / den.hi * (1.0f - den.lo / den.hi);
+            dvx = c * (fx - vx * vf);
+            dvy = c * (fy - vy * vf);
+            dvz = c * (fz - vz * vf);
+            const float prad = m.C_rate * rate32<1>(G, chi, clamped);
+            const float sx_ = m.dt * (q * (dvy * B.z - dvz * B.y) - prad * vx);
+            const float sy_ = m.dt * (q * (dvz * B.x - dvx * B.z) - prad * vy);
+            const float sz_ = m.dt * (q * (dvx * B.y - dvy * B.x) - prad * vz);
+            dux += sx_;
+            duy += sy_;
+            duz += sz_;
+            ux += sx_;
+            uy += sy_;
+            uz += sz_;
+            gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        } else {
+            // ---- optical depth (Eq. 6) with the residual-time sub-loop
+            TAU = split_d(taud);
+            float r = 1.0f;
+            for (int k = 0;; ++k) {
+                const float Hv = rate32<0>(H, chi, clamped);
+                const float wdt = m.C_rate * Hv / gam * m.dt;
+                const float dtau = wdt * r;
+                // tau > dtau decided on the double-float optical depth
+                if (!(dtau > 0.0f) || TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f)) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    break;
+                }
+                if (k == P.max_emit) {
+                    TAU = df_add_f(TAU, -dtau);
+                    dtau_once = dtau;
+                    o.sat = true;
+                    break;
+                }
+                events = true;
+                r = r - df_to_f(TAU) / wdt;
+                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
+                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
+                const float xi = u53f(rr.z, rr.w);
+                const FracPair uf = sample_cdf_f(
+                    a.tab.Cg2, a.tab.Qg2, a.tab.Gg, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
+                    u53_pair_complement(rr.x, rr.y), (float)(kSgSpan / (kNNode - 1)), true,
+                    clamped);
+                const float pmag = sqrtf(ux * ux + uy * uy + uz * uz);
+                float gg = uf.x * gam;
+                // what the electron keeps, |p| - u gamma = (1-u) gamma - 1/(gamma + |p|),
+                // formed without cancellation
+                float keep = uf.omx * gam - 1.0f / (gam + pmag);
+                if (gg > pmag || keep < 0.0f) {
+                    gg = pmag;
+                    keep = 0.0f;
+                }
+                if (n_emit == 0) {
+                    // the photons' direction goes to the append record now
+                    // (fewer values live through the loop)
+                    const float ip = pmag > 0.0f ? 1.0f / pmag : 0.0f;
+                    sink.direction(f_to_d(ux * ip), f_to_d(uy * ip), f_to_d(uz * ip));
+                }
+                ++n_emit;
+                if (gg > m.gmin) {
+                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
+                    sink.photon(nph, f_to_d(gg), f_to_d(-logf(u53f(rp.x, rp.y))));
+                    ++nph;
+                } else {
+                    ++n_sub;
+                    esub_f += gg;
+                }
+                if (pmag > 0.0f) {
+                    const float s1 = keep / pmag;
+                    const float s1m = s1 - 1.0f;  // exact (Sterbenz) for s1 in [1/2, 1]
+                    dux = fmaf(ux, s1m, dux);
+                    duy = fmaf(uy, s1m, duy);
+                    duz = fmaf(uz, s1m, duz);
+                    ux *= s1;
+                    uy *= s1;
+                    uz *= s1;
+                }
+                TAU = {-logf(xi), 0.0f};
+                gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B,
+                                     m.inv_aS, m.inv_aS_lo);
+            }
+        }
+
+        // ---- position and state: FP64 accumulation of FP32 increments
+        if (nph) sink.origin(xd, yd, zd);
+        const float gi = 1.0f / gam;
+        sink.template put<0>(add_fd(xd, m.dt * (ux * gi + dvx)));
+        sink.template put<1>(add_fd(yd, m.dt * (uy * gi + dvy)));
+        sink.template put<2>(add_fd(zd, m.dt * (uz * gi + dvz)));
+        sink.template put<3>(add_fd(uxd, dux));
+        sink.template put<4>(add_fd(uyd, duy));
+        sink.template put<5>(add_fd(uzd, duz));
+        if (events)
+            sink.template put<6>(merge_df(TAU));
+        else if (dtau_once != 0.0f)
+            sink.template put<6>(add_fd(taud, -dtau_once));
+        if (n_sub) o.e_sub = f_to_d(esub_f);
+    }
+    o.n_emit = n_emit;
+    o.nph = nph;
+    o.n_sub = n_sub;
+    o.clamped = clamped;
+}
+
+// The append sink of a step tile: the block's tables are waited for once,
+// and the records go to the tile's stash ([field][thread]).
+template <int PREC>
+struct StashSink {
+    const StepArgs &a;
+    unsigned long long *bar;
+    bool loaded;
+    double *st;
+    int tid;
+    double *chi_slot;  // the particle's chi, or NULL
+    const SpeciesDev &S;
+    int64_t i;
+    // each component is stored as soon as it is formed (a value kept across
+    // the called write-back helpers would have to be saved and restored)
+    template <int C>
+    __device__ __forceinline__ void put(double v)
+    {
+        if constexpr (C == 0) S.x[i] = v;
+        if constexpr (C == 1) S.y[i] = v;
+        if constexpr (C == 2) {
+            if (S.z) S.z[i] = v;
+        }
+        if constexpr (C == 3) S.ux[i] = v;
+        if constexpr (C == 4) S.uy[i] = v;
+        if constexpr (C == 5) S.uz[i] = v;
+        if constexpr (C == 6) S.tau[i] = v;
+    }
+    __device__ __forceinline__ void tables()
+    {
+        if (!loaded) wait_tables(bar, a);
+    }
+    __device__ __forceinline__ void chi(double c)
+    {
+        if (chi_slot) *chi_slot = c;
+    }
+    __device__ __forceinline__ void direction(double kx, double ky, double kz)
+    {
+        st[3 * kTile + tid] = kx;
+        st[4 * kTile + tid] = ky;
+        st[5 * kTile + tid] = kz;
+    }
+    __device__ __forceinline__ void photon(int j, double gg, double tau)
+    {
+        st[(kStashGg + j) * kTile + tid] = gg;
+        st[(kStashTg + j) * kTile + tid] = tau;
+    }
+    __device__ __forceinline__ void origin(double x, double y, double z)
+    {
+        st[0 * kTile + tid] = x;
+        st[1 * kTile + tid] = y;
+        st[2 * kTile + tid] = z;
+    }
+};
+
 template <int PREC, int FK, typename R>
 __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned long long *bar, bool &loaded, unsigned chain_tile, int sp,
@@ -263,335 +609,16 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     const int64_t i = first + tid;
     const bool active = i < n;
 
-    int nph = 0;
-    double x0 = 0, y0 = 0, z0 = 0, kx = 0, ky = 0, kz = 0, wgt = 0;
-    bool cont = false, sat = false, clamped = false;
-    int n_emit = 0, n_sub = 0;
-    double e_sub = 0.0;
-
-    if constexpr (PREC == kFP64) {
+    LeptonOut o{};
+    double wgt = 0;
     if (active) {
-        const double q = sp == 0 ? -1.0 : 1.0;
-        const double dt = P.dt;
-        x0 = S.x[i];
-        y0 = S.y[i];
-        z0 = S.z ? S.z[i] : 0.0;
-        double ux = S.ux[i], uy = S.uy[i], uz = S.uz[i];
-        double tau = S.tau[i];
-        Vec3<R> E, B;
-        eval_field<FK, R>(P.f, x0, y0, z0, P.t, E, B);
-
-        // ---- Boris push of the Lorentz force (f_l of Eq. 4)
-        if constexpr (PREC == kFP64) {
-            const double h = 0.5 * q * dt;
-            const double mx = ux + h * E.x, my = uy + h * E.y, mz = uz + h * E.z;
-            const double g = sqrt(1.0 + mx * mx + my * my + mz * mz);
-            const double tx = h * B.x / g, ty = h * B.y / g, tz = h * B.z / g;
-            const double t2 = tx * tx + ty * ty + tz * tz;
-            const double sx = 2.0 * tx / (1.0 + t2), sy = 2.0 * ty / (1.0 + t2),
-                         sz = 2.0 * tz / (1.0 + t2);
-            const double px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
-                         pz = mz + (mx * ty - my * tx);
-            ux = mx + (py * sz - pz * sy) + h * E.x;
-            uy = my + (pz * sx - px * sz) + h * E.y;
-            uz = mz + (px * sy - py * sx) + h * E.z;
-        } else {
-            // FP32 rotation, FP64 accumulation of the momentum
-            const float h = (float)(0.5 * q * dt);
-            const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
-            const double mx = ux + hx, my = uy + hy, mz = uz + hz;
-            const float fx = (float)mx, fy = (float)my, fz = (float)mz;
-            const float ig = rsqrtf(1.0f + fx * fx + fy * fy + fz * fz);
-            const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
-            const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
-            const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
-            const float px = fx + (fy * tz - fz * ty), py = fy + (fz * tx - fx * tz),
-                        pz = fz + (fx * ty - fy * tx);
-            ux = mx + (double)((py * sz - pz * sy) + hx);
-            uy = my + (double)((pz * sx - px * sz) + hy);
-            uz = mz + (double)((px * sy - py * sx) + hz);
-        }
-        double gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-        const double Ex = E.x, Ey = E.y, Ez = E.z, Bx = B.x, By = B.y, Bz = B.z;
-        if (!loaded) wait_tables(bar, a);  // tables are needed from here on
-        double chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
-        if (S.chi) S.chi[i] = chi;
-        double dvx = 0.0, dvy = 0.0, dvz = 0.0;
-
-        if (chi < P.chi_th) {
-            // ---- Sokolov continuous regime (Eq. 4, P_rad of Eq. 5)
-            cont = true;
-            if constexpr (PREC == kFP64) {
-                const double vx = ux / gam, vy = uy / gam, vz = uz / gam;
-                const double fx = q * (Ex + (vy * Bz - vz * By));
-                const double fy = q * (Ey + (vz * Bx - vx * Bz));
-                const double fz = q * (Ez + (vx * By - vy * Bx));
-                const double vf = vx * fx + vy * fy + vz * fz;
-                const double den = 1.0 + a.tau0w * vf;
-                dvx = a.tau0w * (fx - vx * vf) / den;
-                dvy = a.tau0w * (fy - vy * vf) / den;
-                dvz = a.tau0w * (fz - vz * vf) / den;
-                const double prad = a.C_rate * rate64<1>(sm.G, chi, clamped);
-                ux = ux + dt * (q * (dvy * Bz - dvz * By) - prad * vx);
-                uy = uy + dt * (q * (dvz * Bx - dvx * Bz) - prad * vy);
-                uz = uz + dt * (q * (dvx * By - dvy * Bx) - prad * vz);
-            } else {
-                const float ig = (float)(1.0 / gam), qf = (float)q;
-                const float vx = (float)ux * ig, vy = (float)uy * ig, vz = (float)uz * ig;
-                const float fx = qf * (E.x + (vy * B.z - vz * B.y));
-                const float fy = qf * (E.y + (vz * B.x - vx * B.z));
-                const float fz = qf * (E.z + (vx * B.y - vy * B.x));
-                const float vf = vx * fx + vy * fy + vz * fz;
-                const double den = 1.0 + a.tau0w * (double)vf;  // FP64 denominator
-                const float c = (float)(a.tau0w / den);
-                const float dx_ = c * (fx - vx * vf), dy_ = c * (fy - vy * vf),
-                            dz_ = c * (fz - vz * vf);
-                dvx = dx_;
-                dvy = dy_;
-                dvz = dz_;
-                const float prad = (float)a.C_rate * rate32<1>(sm.G, (float)chi, clamped);
-                const float dtf = (float)dt;
-                ux += (double)(dtf * (qf * (dy_ * B.z - dz_ * B.y) - prad * vx));
-                uy += (double)(dtf * (qf * (dz_ * B.x - dx_ * B.z) - prad * vy));
-                uz += (double)(dtf * (qf * (dx_ * B.y - dy_ * B.x) - prad * vz));
-            }
-            gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-        } else {
-            // ---- optical depth (Eq. 6) with the residual-time sub-loop
-            double r = 1.0;
-            for (int k = 0;; ++k) {
-                double wdt, dtau;
-                if constexpr (PREC == kFP64) {
-                    const double H = rate64<0>(sm.H, chi, clamped);
-                    wdt = a.C_rate * H / gam * dt;
-                    dtau = wdt * r;
-                } else {
-                    const float H = rate32<0>(sm.H, (float)chi, clamped);
-                    const float wf = (float)a.C_rate * H / (float)gam * (float)dt;
-                    wdt = wf;
-                    dtau = (double)(wf * (float)r);
-                }
-                if (!(dtau > 0.0) || tau > dtau) {
-                    tau = tau - dtau;
-                    break;
-                }
-                if (k == P.max_emit) {
-                    tau = tau - dtau;
-                    sat = true;
-                    break;
-                }
-                r = r - tau / wdt;
-                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
-                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
-                const double xi_p = u53(rr.x, rr.y), xi = u53(rr.z, rr.w);
-                double ufrac;
-                ufrac = sample_cdf<double>(a.tab.Cg, a.tab.Gg, chi, xi_p, kSgMin, kSgSpan, true,
-                                           clamped);
-                const double pmag = sqrt(ux * ux + uy * uy + uz * uz);
-                double gg = ufrac * gam;
-                if (gg > pmag) gg = pmag;
-                if (n_emit == 0 && pmag > 0.0) {
-                    kx = ux / pmag;
-                    ky = uy / pmag;
-                    kz = uz / pmag;
-                }
-                ++n_emit;
-                if (gg > P.gmin) {
-                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
-                    st[(kStashGg + nph) * kTile + tid] = gg;
-                    st[(kStashTg + nph) * kTile + tid] = -log(u53(rp.x, rp.y));
-                    ++nph;
-                } else {
-                    ++n_sub;
-                    e_sub += gg;
-                }
-                if (pmag > 0.0) {
-                    const double scale = (pmag - gg) / pmag;
-                    ux *= scale;
-                    uy *= scale;
-                    uz *= scale;
-                }
-                tau = -log(xi);
-                gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
-                chi = chi_e64(Ex, Ey, Ez, Bx, By, Bz, ux, uy, uz, gam, a.a_S);
-            }
-        }
-
-        // ---- position (Eq. 4: dx/dt = v + delta v)
-        if constexpr (PREC == kFP64) {
-            S.x[i] = x0 + dt * (ux / gam + dvx);
-            S.y[i] = y0 + dt * (uy / gam + dvy);
-            if (S.z) S.z[i] = z0 + dt * (uz / gam + dvz);
-        } else {
-            const float ig = (float)(1.0 / gam), dtf = (float)dt;
-            S.x[i] = x0 + (double)(dtf * ((float)ux * ig + (float)dvx));
-            S.y[i] = y0 + (double)(dtf * ((float)uy * ig + (float)dvy));
-            if (S.z) S.z[i] = z0 + (double)(dtf * ((float)uz * ig + (float)dvz));
-        }
-        S.ux[i] = ux;
-        S.uy[i] = uy;
-        S.uz[i] = uz;
-        S.tau[i] = tau;
-        if (nph || n_sub) wgt = S.w[i];
+        LeptonState s{S.x[i], S.y[i], S.z ? S.z[i] : 0.0, S.ux[i], S.uy[i], S.uz[i], S.tau[i]};
+        StashSink<PREC> sink{a, bar, loaded, st, tid, S.chi ? S.chi + i : nullptr, S, i};
+        lepton_particle<PREC, FK, R>(a, P, sm.H, sm.G, sp, S, i, s, o, sink);
+        if (o.nph || o.n_sub) wgt = S.w[i];
+        if (o.nph) st[6 * kTile + tid] = wgt;
+        if (o.n_emit && S.nemit) S.nemit[i] += o.n_emit;
     }
-    } else {
-    if (active) {
-        // ---- mixed precision: FP32 physics; the FP64 state is read once,
-        // increments are formed in FP32 and added back by integer
-        // instructions; chi_e falls back to double-float where FP32 cancels
-        const MixedConsts &m = P.mc;
-        const double xd = S.x[i], yd = S.y[i], zd = S.z ? S.z[i] : 0.0;
-        const double uxd = S.ux[i], uyd = S.uy[i], uzd = S.uz[i];
-        const double taud = S.tau[i];
-        Vec3<float> E, B;
-        eval_field_mixed<FK>(P.f, m, xd, yd, zd, E, B);
-
-        // Boris on the leading FP32 parts; the increment is kept in FP32
-        const float u0x = hi_d(uxd), u0y = hi_d(uyd), u0z = hi_d(uzd);
-        const float h = m.h[sp];
-        const float hx = h * E.x, hy = h * E.y, hz = h * E.z;
-        const float mx = u0x + hx, my = u0y + hy, mz = u0z + hz;
-        const float ig = rsqrtf(1.0f + mx * mx + my * my + mz * mz);
-        const float tx = h * B.x * ig, ty = h * B.y * ig, tz = h * B.z * ig;
-        const float k2 = 2.0f / (1.0f + tx * tx + ty * ty + tz * tz);
-        const float sx = k2 * tx, sy = k2 * ty, sz = k2 * tz;
-        const float px = mx + (my * tz - mz * ty), py = my + (mz * tx - mx * tz),
-                    pz = mz + (mx * ty - my * tx);
-        float dux = (py * sz - pz * sy) + 2.0f * hx, duy = (pz * sx - px * sz) + 2.0f * hy,
-              duz = (px * sy - py * sx) + 2.0f * hz;
-        float ux = u0x + dux, uy = u0y + duy, uz = u0z + duz;
-        float gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-        if (!loaded) wait_tables(bar, a);  // tables are needed from here on
-        float chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B, m.inv_aS,
-                                   m.inv_aS_lo);
-        if (S.chi) S.chi[i] = f_to_d(chi);
-        float dvx = 0.0f, dvy = 0.0f, dvz = 0.0f;
-        float dtau_once = 0.0f, esub_f = 0.0f;
-        bool events = false;
-        df2 TAU = {0.0f, 0.0f};
-
-        if (chi < m.chi_th) {
-            // ---- Sokolov (Eq. 4, 5); denominator 1 + tau0 v.f_l in double-float
-            cont = true;
-            const float q = sp == 0 ? -1.0f : 1.0f;
-            const float gi = 1.0f / gam;
-            const float vx = ux * gi, vy = uy * gi, vz = uz * gi;
-            const float fx = q * (E.x + (vy * B.z - vz * B.y));
-            const float fy = q * (E.y + (vz * B.x - vx * B.z));
-            const float fz = q * (E.z + (vx * B.y - vy * B.x));
-            const float vf = vx * fx + vy * fy + vz * fz;
-            const df2 den = two_sum(1.0f, m.tau0w * vf);
-            const float c = m.tau0w / den.hi * (1.0f - den.lo / den.hi);
-            dvx = c * (fx - vx * vf);
-            dvy = c * (fy - vy * vf);
-            dvz = c * (fz - vz * vf);
-            const float prad = m.C_rate * rate32<1>(sm.G, chi, clamped);
-            const float sx_ = m.dt * (q * (dvy * B.z - dvz * B.y) - prad * vx);
-            const float sy_ = m.dt * (q * (dvz * B.x - dvx * B.z) - prad * vy);
-            const float sz_ = m.dt * (q * (dvx * B.y - dvy * B.x) - prad * vz);
-            dux += sx_;
-            duy += sy_;
-            duz += sz_;
-            ux += sx_;
-            uy += sy_;
-            uz += sz_;
-            gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-        } else {
-            // ---- optical depth (Eq. 6) with the residual-time sub-loop
-            TAU = split_d(taud);
-            float r = 1.0f;
-            for (int k = 0;; ++k) {
-                const float H = rate32<0>(sm.H, chi, clamped);
-                const float wdt = m.C_rate * H / gam * m.dt;
-                const float dtau = wdt * r;
-                // tau > dtau decided on the double-float optical depth
-                if (!(dtau > 0.0f) || TAU.hi > dtau || (TAU.hi == dtau && TAU.lo > 0.0f)) {
-                    TAU = df_add_f(TAU, -dtau);
-                    dtau_once = dtau;
-                    break;
-                }
-                if (k == P.max_emit) {
-                    TAU = df_add_f(TAU, -dtau);
-                    dtau_once = dtau;
-                    sat = true;
-                    break;
-                }
-                events = true;
-                r = r - df_to_f(TAU) / wdt;
-                // ---- emission: Eq. 7 sampling, Eq. 8 recoil
-                const uint4 rr = draw(P.seed, sp, kRngEmit, particle_id(S, i), P.step, k);
-                const float xi = u53f(rr.z, rr.w);
-                const FracPair uf = sample_cdf_f(
-                    a.tab.Cg2, a.tab.Qg2, a.tab.Gg, a.tab.Eg, chi, u53_pair(rr.x, rr.y),
-                    u53_pair_complement(rr.x, rr.y), (float)(kSgSpan / (kNNode - 1)), true,
-                    clamped);
-                const float pmag = sqrtf(ux * ux + uy * uy + uz * uz);
-                float gg = uf.x * gam;
-                // what the electron keeps, |p| - u gamma = (1-u) gamma - 1/(gamma + |p|),
-                // formed without cancellation
-                float keep = uf.omx * gam - 1.0f / (gam + pmag);
-                if (gg > pmag || keep < 0.0f) {
-                    gg = pmag;
-                    keep = 0.0f;
-                }
-                if (n_emit == 0) {
-                    // the photons' direction goes to the append record now
-                    // (fewer values live through the loop)
-                    const float ip = pmag > 0.0f ? 1.0f / pmag : 0.0f;
-                    st[3 * kTile + tid] = f_to_d(ux * ip);
-                    st[4 * kTile + tid] = f_to_d(uy * ip);
-                    st[5 * kTile + tid] = f_to_d(uz * ip);
-                }
-                ++n_emit;
-                if (gg > m.gmin) {
-                    const uint4 rp = draw(P.seed, sp, kRngPhotonTau, particle_id(S, i), P.step, k);
-                    st[(kStashGg + nph) * kTile + tid] = f_to_d(gg);
-                    st[(kStashTg + nph) * kTile + tid] = f_to_d(-logf(u53f(rp.x, rp.y)));
-                    ++nph;
-                } else {
-                    ++n_sub;
-                    esub_f += gg;
-                }
-                if (pmag > 0.0f) {
-                    const float s1 = keep / pmag;
-                    const float s1m = s1 - 1.0f;  // exact (Sterbenz) for s1 in [1/2, 1]
-                    dux = fmaf(ux, s1m, dux);
-                    duy = fmaf(uy, s1m, duy);
-                    duz = fmaf(uz, s1m, duz);
-                    ux *= s1;
-                    uy *= s1;
-                    uz *= s1;
-                }
-                TAU = {-logf(xi), 0.0f};
-                gam = sqrtf(1.0f + ux * ux + uy * uy + uz * uz);
-                chi = chi_mixed_auto(uxd, uyd, uzd, dux, duy, duz, ux, uy, uz, gam, E, B,
-                                     m.inv_aS, m.inv_aS_lo);
-            }
-        }
-
-        // ---- position and write-back: FP64 accumulation of FP32 increments
-        const float gi = 1.0f / gam;
-        S.x[i] = add_fd(xd, m.dt * (ux * gi + dvx));
-        S.y[i] = add_fd(yd, m.dt * (uy * gi + dvy));
-        if (S.z) S.z[i] = add_fd(zd, m.dt * (uz * gi + dvz));
-        S.ux[i] = add_fd(uxd, dux);
-        S.uy[i] = add_fd(uyd, duy);
-        S.uz[i] = add_fd(uzd, duz);
-        if (events)
-            S.tau[i] = merge_df(TAU);
-        else if (dtau_once != 0.0f)
-            S.tau[i] = add_fd(taud, -dtau_once);
-        if (n_sub) e_sub = f_to_d(esub_f);
-        if (nph || n_sub) wgt = S.w[i];
-        if (nph) {
-            st[0 * kTile + tid] = xd;
-            st[1 * kTile + tid] = yd;
-            st[2 * kTile + tid] = zd;
-            st[6 * kTile + tid] = wgt;
-        }
-    }
-    }
-    if (active && n_emit && S.nemit) S.nemit[i] += n_emit;
     if (!loaded) {
         // threads without a particle also wait, so the block never leaves
         // (or reuses the tables) with the copy in flight
@@ -600,29 +627,21 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     }
 
     // ---- counters (warp-aggregated into shared memory)
-    warp_count(&bs.c[sp][cCont], cont);
-    warp_count(&bs.c[sp][cSat], sat);
-    warp_count(&bs.c[sp][cClamp], clamped);
-    if (__any_sync(0xFFFFFFFFu, n_emit > 0)) {
-        warp_add(&bs.c[sp][cEmit], (unsigned)n_emit);
-        warp_add(&bs.c[sp][cSub], (unsigned)n_sub);
-        warp_add(&bs.e[sp][0], n_sub ? wgt * e_sub : 0.0);
+    warp_count(&bs.c[sp][cCont], o.cont);
+    warp_count(&bs.c[sp][cSat], o.sat);
+    warp_count(&bs.c[sp][cClamp], o.clamped);
+    if (__any_sync(0xFFFFFFFFu, o.n_emit > 0)) {
+        warp_add(&bs.c[sp][cEmit], (unsigned)o.n_emit);
+        warp_add(&bs.c[sp][cSub], (unsigned)o.n_sub);
+        warp_add(&bs.e[sp][0], o.n_sub ? wgt * o.e_sub : 0.0);
     }
 
     // ---- this tile's appends: the aggregate is published now, the records
     // stashed and mapped; their slots are written later (write_photons)
     int tile_total;
+    const int nph = o.nph;
     const int local = block_scan(nph, s_warp, &tile_total);
     if (tid == 0) publish_aggregate(P.lep_words, chain_tile, tile_total, epoch);
-    if (PREC == kFP64 && nph) {
-        st[0 * kTile + tid] = x0;
-        st[1 * kTile + tid] = y0;
-        st[2 * kTile + tid] = z0;
-        st[3 * kTile + tid] = kx;
-        st[4 * kTile + tid] = ky;
-        st[5 * kTile + tid] = kz;
-        st[6 * kTile + tid] = wgt;
-    }
     for (int k = 0; k < nph; ++k) s_map[local + k] = (unsigned short)(tid | (k << 8));
     return tile_total;
 }
@@ -667,6 +686,28 @@ __device__ void write_photons(const Problem &P, const double *st, const unsigned
     }
 }
 
+// Ballistic motion of a photon over one step, x += c k^ dt: one copy of the
+// arithmetic for every place a photon moves (the step's photon tiles and
+// the fused steps), with every rounding explicit (a product left to the
+// compiler could be fused into the add in one place and hoisted out of a
+// loop in the other), so both give the same bits.
+__device__ __forceinline__ double photon_speed64(double ux, double uy, double uz)
+{
+    return __dsqrt_rn(__fma_rn(uz, uz, __fma_rn(uy, uy, __dmul_rn(ux, ux))));
+}
+__device__ __forceinline__ double photon_move64(double x, double u, double g, double dt)
+{
+    return __fma_rn(dt, __ddiv_rn(u, g), x);
+}
+__device__ __forceinline__ float photon_speed32(float fx, float fy, float fz)
+{
+    return sqrtf(fx * fx + fy * fy + fz * fz);
+}
+__device__ __forceinline__ double photon_move32(double x, float f, float c)
+{
+    return add_fd(x, c * f);
+}
+
 // -------------------------------------------------------------------- photon tile
 
 template <int PREC, int FK, typename R>
@@ -707,7 +748,7 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             gux = Ph.ux[i];
             guy = Ph.uy[i];
             guz = Ph.uz[i];
-            const double g = sqrt(gux * gux + guy * guy + guz * guz);
+            const double g = photon_speed64(gux, guy, guz);
             const double dt = P.dt;
             bool decayed = false;
             if (pairs && g > 2.0) {
@@ -757,9 +798,9 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             }
             if (!decayed && g > 0.0) {
                 if constexpr (PREC == kFP64) {
-                    Ph.x[i] = px + dt * (gux / g);
-                    Ph.y[i] = py + dt * (guy / g);
-                    if (Ph.z) Ph.z[i] = pz + dt * (guz / g);
+                    Ph.x[i] = photon_move64(px, gux, g, dt);
+                    Ph.y[i] = photon_move64(py, guy, g, dt);
+                    if (Ph.z) Ph.z[i] = photon_move64(pz, guz, g, dt);
                 } else {
                     const float c = (float)(dt / g);
                     Ph.x[i] = px + (double)(c * (float)gux);
@@ -783,7 +824,7 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             guy = Ph.uy[i];
             guz = Ph.uz[i];
             const float fx = hi_d(gux), fy = hi_d(guy), fz = hi_d(guz);
-            const float g = sqrtf(fx * fx + fy * fy + fz * fz);
+            const float g = photon_speed32(fx, fy, fz);
             bool decayed = false;
             if (pairs && g > 2.0f) {
                 Vec3<float> E, B;
@@ -822,9 +863,9 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
             }
             if (!decayed && g > 0.0f) {
                 const float c = m.dt / g;
-                Ph.x[i] = add_fd(px, c * fx);
-                Ph.y[i] = add_fd(py, c * fy);
-                if (Ph.z) Ph.z[i] = add_fd(pz, c * fz);
+                Ph.x[i] = photon_move32(px, fx, c);
+                Ph.y[i] = photon_move32(py, fy, c);
+                if (Ph.z) Ph.z[i] = photon_move32(pz, fz, c);
             }
         }
     }
@@ -1255,6 +1296,341 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
             __threadfence();
         }
     }
+}
+
+// -------------------------------------------------------------------- fused steps
+//
+// K steps of every lepton in one launch, the particle held in registers
+// from the first step to the last (analytic or fixed fields, pairs off: the
+// leptons then never change in number and the photons only move).  The
+// physics is lepton_particle, the photon motion photon_move*: the same
+// arithmetic as K launches of k_step, so the results are the same bits.
+// Photon slots keep the order of K separate steps (step, then emitter
+// slot, then emission index): a count pass records the photons each tile
+// stores at each step, one scan turns the counts into first slots, and the
+// write pass runs the same physics again and writes every photon at its
+// slot, moved over the window's remaining steps.  Tiles are one warp (a
+// tile's per-step count is a warp sum).
+
+struct FusedArgs {
+    StepArgs a;              // a.single: the problem at the window's first step
+    int32_t K;               // steps in the window
+    int32_t pad;
+    long long tiles_e, tiles; // lepton tiles (electron tiles first)
+    int *counts;             // [K][tiles] photons stored per step and tile
+    long long *offs;         // [K][tiles] first slot of those photons
+    long long *win;          // [2] photons at the window start, photons stored in it
+    unsigned short *moves;   // [slot - win[0]] steps left to a new photon in the window
+};
+
+// The append sinks of a fused lepton: the state stays in registers.
+struct FusedCountSink {
+    LeptonState &cur;
+    template <int C>
+    __device__ __forceinline__ void put(double v)
+    {
+        (&cur.x)[C] = v;
+    }
+    __device__ __forceinline__ void tables() {}
+    __device__ __forceinline__ void chi(double) {}
+    __device__ __forceinline__ void direction(double, double, double) {}
+    __device__ __forceinline__ void photon(int, double, double) {}
+    __device__ __forceinline__ void origin(double, double, double) {}
+};
+
+struct FusedWriteSink {
+    LeptonState &cur;
+    double chi_last, kx, ky, kz, ox, oy, oz;
+    double gg[QP_MAX_EMISSIONS], tg[QP_MAX_EMISSIONS];
+    template <int C>
+    __device__ __forceinline__ void put(double v)
+    {
+        (&cur.x)[C] = v;
+    }
+    __device__ __forceinline__ void tables() {}
+    __device__ __forceinline__ void chi(double c) { chi_last = c; }
+    __device__ __forceinline__ void direction(double x, double y, double z)
+    {
+        kx = x;
+        ky = y;
+        kz = z;
+    }
+    __device__ __forceinline__ void photon(int j, double g, double t)
+    {
+        gg[j] = g;
+        tg[j] = t;
+    }
+    __device__ __forceinline__ void origin(double x, double y, double z)
+    {
+        ox = x;
+        oy = y;
+        oz = z;
+    }
+};
+
+static_assert(offsetof(LeptonState, tau) == 6 * sizeof(double), "LeptonState layout");
+
+// A new photon written at `slot` where the step that emitted it leaves it
+// (its emitter's position at the start of that step); k_fused_photons moves
+// it over the window's remaining steps.
+__device__ __forceinline__ void fused_photon(const SpeciesDev &Ph, int64_t slot, double ox,
+                                             double oy, double oz, double ux, double uy,
+                                             double uz, double tau, double w)
+{
+    Ph.x[slot] = ox;
+    Ph.y[slot] = oy;
+    if (Ph.z) Ph.z[slot] = oz;
+    Ph.ux[slot] = ux;
+    Ph.uy[slot] = uy;
+    Ph.uz[slot] = uz;
+    Ph.tau[slot] = tau;
+    Ph.w[slot] = w;
+    if (Ph.chi) Ph.chi[slot] = 0.0;
+    if (Ph.nemit) Ph.nemit[slot] = 0;
+}
+
+// One warp a block, at most 64 registers a thread (32 resident warps an SM).
+template <int PREC, int FK, int PASS>
+__global__ void __launch_bounds__(32, 32) k_fused(const __grid_constant__ FusedArgs f)
+{
+    using R = typename std::conditional<PREC == kFP64, double, float>::type;
+    __shared__ __align__(16) Problem sP;
+    const int lane = threadIdx.x;
+    const StepArgs &a = f.a;
+    const R *H, *G;
+    if constexpr (PREC == kFP64) {
+        H = a.tab.H;
+        G = a.tab.Gs;
+    } else {
+        H = a.tab.Hf;
+        G = a.tab.Gsf;
+    }
+    for (long long tile = blockIdx.x; tile < f.tiles; tile += gridDim.x) {
+        {
+            const int *src = reinterpret_cast<const int *>(&a.single);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int k = lane; k < (int)(sizeof(Problem) / sizeof(int)); k += 32) dst[k] = src[k];
+        }
+        __syncwarp();
+        const int sp = tile < f.tiles_e ? 0 : 1;
+        const SpeciesDev &S = sP.sp[sp];
+        const int64_t i = (tile - (sp ? f.tiles_e : 0)) * 32 + lane;
+        long long n = *((volatile long long *)S.n_live);
+        if (n < 0 || n > S.cap) {
+            if (lane == 0) raise_status(a.status, QP_ERR_INVALID_ARG);
+            n = n < 0 ? 0 : S.cap;
+        }
+        const bool active = i < n;
+        LeptonState cur{};
+        double w = 0.0;
+        if (active) {
+            cur = {S.x[i], S.y[i], S.z ? S.z[i] : 0.0, S.ux[i], S.uy[i], S.uz[i], S.tau[i]};
+            if (PASS == 1) w = S.w[i];
+        }
+        const uint64_t s0 = sP.step;
+        unsigned c_emit = 0, c_sub = 0, c_cont = 0, c_sat = 0, c_clamp = 0, c_ph = 0, c_drop = 0;
+        double e_sub = 0.0, e_drop = 0.0, chi_last = 0.0;
+        for (int k = 0; k < f.K; ++k) {
+            if (k > 0) {
+                __syncwarp();
+                if (lane == 0) set_time(sP, (long long)(s0 + k));
+                __syncwarp();
+            }
+            LeptonOut o{};
+            if constexpr (PASS == 0) {
+                FusedCountSink sink{cur};
+                if (active) {
+                    const LeptonState in = cur;
+                    lepton_particle<PREC, FK, R>(a, sP, H, G, sp, S, i, in, o, sink);
+                }
+                const unsigned tot = __reduce_add_sync(0xFFFFFFFFu, (unsigned)o.nph);
+                if (lane == 0) f.counts[(size_t)k * f.tiles + tile] = (int)tot;
+            } else {
+                FusedWriteSink sink{cur};
+                if (active) {
+                    const LeptonState in = cur;
+                    lepton_particle<PREC, FK, R>(a, sP, H, G, sp, S, i, in, o, sink);
+                    chi_last = sink.chi_last;
+                }
+                // slots of this step's photons: the tile's first slot plus
+                // the stored photons of the lanes before
+                int inc = o.nph;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                const long long first = f.offs[(size_t)k * f.tiles + tile] + (inc - o.nph);
+                const SpeciesDev &Ph = sP.sp[2];
+                for (int j = 0; j < o.nph; ++j) {
+                    const long long slot = first + j;
+                    const double g = sink.gg[j];
+                    if (Ph.present && slot < Ph.cap) {
+                        fused_photon(Ph, slot, sink.ox, sink.oy, sink.oz, g * sink.kx,
+                                     g * sink.ky, g * sink.kz, sink.tg[j], w);
+                        f.moves[slot - f.win[0]] = (unsigned short)(f.K - 1 - k);
+                        ++c_ph;
+                    } else {
+                        ++c_drop;
+                        e_drop += w * g;
+                    }
+                }
+                c_emit += (unsigned)o.n_emit;
+                c_sub += (unsigned)o.n_sub;
+                if (o.n_sub) e_sub += w * o.e_sub;
+                c_cont += o.cont;
+                c_sat += o.sat;
+                c_clamp += o.clamped;
+            }
+        }
+        if constexpr (PASS == 1) {
+            if (active) {
+                S.x[i] = cur.x;
+                S.y[i] = cur.y;
+                if (S.z) S.z[i] = cur.z;
+                S.ux[i] = cur.ux;
+                S.uy[i] = cur.uy;
+                S.uz[i] = cur.uz;
+                S.tau[i] = cur.tau;
+                if (S.chi) S.chi[i] = chi_last;
+                if (c_emit && S.nemit) S.nemit[i] += (int)c_emit;
+            }
+            const unsigned t_emit = __reduce_add_sync(0xFFFFFFFFu, c_emit);
+            const unsigned t_sub = __reduce_add_sync(0xFFFFFFFFu, c_sub);
+            const unsigned t_cont = __reduce_add_sync(0xFFFFFFFFu, c_cont);
+            const unsigned t_sat = __reduce_add_sync(0xFFFFFFFFu, c_sat);
+            const unsigned t_clamp = __reduce_add_sync(0xFFFFFFFFu, c_clamp);
+            const unsigned t_ph = __reduce_add_sync(0xFFFFFFFFu, c_ph);
+            const unsigned t_drop = __reduce_add_sync(0xFFFFFFFFu, c_drop);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                e_sub += __shfl_xor_sync(0xFFFFFFFFu, e_sub, d);
+                e_drop += __shfl_xor_sync(0xFFFFFFFFu, e_drop, d);
+            }
+            if (lane == 0) {
+                DevStats &st = a.stats[S.slot_stats];
+                if (t_emit) atomicAdd(&st.n_emit, (unsigned long long)t_emit);
+                if (t_sub) atomicAdd(&st.n_subthreshold, (unsigned long long)t_sub);
+                if (t_cont) atomicAdd(&st.n_continuous, (unsigned long long)t_cont);
+                if (t_sat) atomicAdd(&st.n_saturated, (unsigned long long)t_sat);
+                if (t_clamp) {
+                    atomicAdd(&st.n_clamped, (unsigned long long)t_clamp);
+                    raise_status(a.status, QP_WARN_TABLE_CLAMPED);
+                }
+                if (t_ph) atomicAdd(&st.n_photon, (unsigned long long)t_ph);
+                if (t_drop) atomicAdd(&st.n_photon_drop, (unsigned long long)t_drop);
+                if (e_sub != 0.0) atomicAdd(&st.e_subthreshold, e_sub);
+                if (e_drop != 0.0) atomicAdd(&st.e_dropped, e_drop);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// The photons of the window moved ballistically: those that existed at its
+// start over its K steps (decayed ones, tau < 0, stay), those it added over
+// the steps left after the step that emitted them.  One thread a photon.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_fused_photons(const __grid_constant__ FusedArgs f)
+{
+    const Problem &P = f.a.single;
+    const SpeciesDev &Ph = P.sp[2];
+    const long long base = f.win[0];
+    long long n = base + f.win[1];
+    if (n > Ph.cap) n = Ph.cap;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int moves = i < base ? f.K : (int)f.moves[i - base];
+        if (moves == 0 || !(Ph.tau[i] >= 0.0)) continue;
+        double x = Ph.x[i], y = Ph.y[i], z = Ph.z ? Ph.z[i] : 0.0;
+        const double ux = Ph.ux[i], uy = Ph.uy[i], uz = Ph.uz[i];
+        if constexpr (PREC == kFP64) {
+            const double g = photon_speed64(ux, uy, uz);
+            if (!(g > 0.0)) continue;
+            for (int m = 0; m < moves; ++m) {
+                x = photon_move64(x, ux, g, P.dt);
+                y = photon_move64(y, uy, g, P.dt);
+                z = photon_move64(z, uz, g, P.dt);
+            }
+        } else {
+            const float fx = hi_d(ux), fy = hi_d(uy), fz = hi_d(uz);
+            const float g = photon_speed32(fx, fy, fz);
+            if (!(g > 0.0f)) continue;
+            const float c = P.mc.dt / g;
+            for (int m = 0; m < moves; ++m) {
+                x = photon_move32(x, fx, c);
+                y = photon_move32(y, fy, c);
+                z = photon_move32(z, fz, c);
+            }
+        }
+        Ph.x[i] = x;
+        Ph.y[i] = y;
+        if (Ph.z) Ph.z[i] = z;
+    }
+}
+
+// Exclusive scan of the per-step, per-tile photon counts in step-major
+// order from the photons at the window's start; the new live count (the
+// capacity bounds it, the rest is dropped in order) and the window's totals.
+__global__ void __launch_bounds__(1024) k_fused_scan(const __grid_constant__ FusedArgs f)
+{
+    __shared__ long long s[1024];
+    const Problem &P = f.a.single;
+    const SpeciesDev &Ph = P.sp[2];
+    long long base = 0;
+    if (Ph.present) {
+        base = *((volatile long long *)Ph.n_live);
+        if (base < 0 || base > Ph.cap) {
+            if (threadIdx.x == 0) raise_status(f.a.status, QP_ERR_INVALID_ARG);
+            base = base < 0 ? 0 : Ph.cap;
+        }
+    }
+    const long long m = (long long)f.K * f.tiles;
+    const int t = threadIdx.x;
+    const long long per = (m + 1023) / 1024;
+    const long long lo = t * per, hi = lo + per < m ? lo + per : m;
+    long long sum = 0;
+    for (long long k = lo; k < hi; ++k) sum += f.counts[k];
+    s[t] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const long long y = t >= d ? s[t - d] : 0;
+        __syncthreads();
+        s[t] += y;
+        __syncthreads();
+    }
+    long long run = base + s[t] - sum;
+    for (long long k = lo; k < hi; ++k) {
+        f.offs[k] = run;
+        run += f.counts[k];
+    }
+    if (t == 1023) {
+        const long long total = s[1023];
+        f.win[0] = base;
+        f.win[1] = total;
+        if (Ph.present) {
+            *Ph.n_live = base + total < Ph.cap ? base + total : Ph.cap;
+            if (base + total > Ph.cap) raise_status(f.a.status, QP_WARN_BUFFER_FULL);
+        } else if (total > 0) {
+            raise_status(f.a.status, QP_WARN_BUFFER_FULL);
+        }
+    }
+}
+
+template <int PREC>
+const void *fused_kernel_of(int fk, int pass)
+{
+#define QP_FUSED_CASE(F)                                                                     \
+    case F: return pass ? (const void *)k_fused<PREC, F, 1> : (const void *)k_fused<PREC, F, 0>;
+    switch (fk) {
+        QP_FUSED_CASE(QP_FIELD_NONE)
+        QP_FUSED_CASE(QP_FIELD_PLANE)
+        QP_FUSED_CASE(QP_FIELD_GAUSSIAN)
+        QP_FUSED_CASE(QP_FIELD_YEE2D)
+        QP_FUSED_CASE(QP_FIELD_UNIFORM_B)
+    default: return nullptr;
+    }
+#undef QP_FUSED_CASE
 }
 
 template <int PREC, bool BATCH>

@@ -126,7 +126,7 @@ EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
            "qp_batch_create", "qp_batch_destroy", "qp_batch_scratch_words", "qp_batch_set",
            "qp_batch_clear", "qp_batch_step", "qp_batch_progress", "qp_coalesce_photons",
-           "qp_compact_photons", "qp_fill_yee2d")
+           "qp_compact_photons", "qp_fill_yee2d", "qp_step_fused")
 
 
 def library_path() -> str:
@@ -172,6 +172,7 @@ def lib(build_if_missing: bool = False):
         L.qp_coalesce_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_params),
                                           C.POINTER(qp_coalesce_stats), vp]
         L.qp_compact_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_stats), vp]
+        L.qp_step_fused.argtypes = [vp, C.POINTER(qp_step_params), i32, vp]
         L.qp_fill_yee2d.argtypes = [vp, C.POINTER(qp_pulse2d), C.POINTER(qp_field), C.c_double,
                                     vp]
         L.qp_status_string.restype = C.c_char_p
@@ -367,3 +368,9 @@ def pulse2d(a0, w0, tau_fwhm, x_focus, t_focus, y_axis) -> qp_pulse2d:
 def qp_fill_yee2d(ctx, pulse: qp_pulse2d, grid: qp_field, t: float, stream=None) -> int:
     return _check("qp_fill_yee2d",
                   lib().qp_fill_yee2d(ctx, C.byref(pulse), C.byref(grid), float(t), stream))
+
+
+def qp_step_fused(ctx, params: qp_step_params, fuse: int, stream=None) -> int:
+    """params.n_steps steps, `fuse` per launch window (pairs off; the same
+    results as qp_step)."""
+    return _check("qp_step_fused", lib().qp_step_fused(ctx, C.byref(params), int(fuse), stream))

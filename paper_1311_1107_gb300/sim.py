@@ -180,6 +180,15 @@ class Simulation:
             Q.qp_reset_counters(self.ctx, sp.handle)
         self.step_index = int(self.workload["params"].get("step", 0))
 
+    def run_fused(self, n_steps: int, fuse: int, stream=None) -> int:
+        """n_steps steps in launch windows of `fuse` steps (qp_step_fused:
+        pairs off, fixed or analytic fields)."""
+        self.params.step = self.step_index
+        self.params.n_steps = int(n_steps)
+        st = Q.qp_step_fused(self.ctx, self.params, int(fuse), stream_handle(stream))
+        self.step_index += int(n_steps)
+        return st
+
     def run(self, n_steps: int, stream=None) -> int:
         if self.pulse is not None:
             # fields refilled from the pulse at each step's time, then the step

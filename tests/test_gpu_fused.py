@@ -1,0 +1,125 @@
+"""Fused steps (qp_step_fused: K steps per launch window, leptons held in
+registers; pairs off) against one launch per step (qp_step) and against the
+oracle (GPU only).
+
+Both run the same per-particle arithmetic and the same photon motion, and
+the fused windows keep the photons' slot order, so every array of every
+species must be the same bits, and every event counter the same number
+(the sub-threshold energy is a sum in another order: within 1e-12)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1311_1107_gb300 import qedpic as Q
+from paper_1311_1107_gb300 import workloads as W
+from paper_1311_1107_gb300.sim import Simulation
+from tests.parity import compare_species, oracle_arrays, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+COUNTERS = ("n_emit", "n_photon", "n_photon_drop", "n_subthreshold", "n_saturated",
+            "n_clamped", "n_continuous")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Q.qp_init_tables(W.LAMBDA_M, 0)
+    yield c
+    torch.cuda.synchronize()
+    Q.qp_destroy(c)
+
+
+def _no_pairs(w):
+    w["params"] = dict(w["params"], pairs=False)
+    return w
+
+
+def _cases():
+    return {
+        "plane wave": lambda: W.plane_wave_collision(n=1000, n_steps=200),
+        "beam": lambda: _no_pairs(W.beam_collision(n=1500, n_steps=200, buffer=300_000)),
+        "foil": lambda: _no_pairs(W.laser_on_foil(nx=256, ny=128, ppc=8, foil_cells=4,
+                                                  n_steps=200, photon_capacity=1 << 18,
+                                                  pair_capacity=1 << 10)),
+        "constant B": lambda: _no_pairs(W.uniform_b_cascade(n=700, n_steps=200, cap=1 << 18)),
+    }
+
+
+def _state(sim):
+    torch.cuda.synchronize()
+    out = {n: sp.host() for n, sp in sim.species.items()}
+    diag = {n: sim.diagnostics(n) for n in sim.species}
+    return out, diag
+
+
+def _same(label, a, b, da, db):
+    for name in a:
+        assert len(a[name]["x"]) == len(b[name]["x"]), (label, name)
+        for k, v in a[name].items():
+            if v is None:
+                continue
+            assert np.array_equal(v, b[name][k]), (label, name, k)
+    for name in da:
+        for c in COUNTERS:
+            assert getattr(da[name], c) == getattr(db[name], c), (label, name, c)
+        assert da[name].e_subthreshold == pytest.approx(db[name].e_subthreshold, rel=1e-12,
+                                                        abs=1e-300)
+        assert da[name].status == db[name].status
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", list(_cases()))
+def test_fused_windows_give_the_same_bits_as_single_steps(ctx, case, precision):
+    w = _cases()[case]()
+    n_steps = 200
+    ref = Simulation(w, precision=precision, ctx=ctx)
+    ref.run(n_steps)
+    a, da = _state(ref)
+    assert da["electron"].n_emit > 0
+    for fuse in (1, 7, 64, n_steps):
+        sim = Simulation(w, precision=precision, ctx=ctx)
+        sim.run_fused(n_steps, fuse)
+        b, db = _state(sim)
+        _same(f"{case} {precision} fuse {fuse}", a, b, da, db)
+        for sp in list(sim.species.values()):
+            Q.qp_destroy_species(ctx, sp.handle)
+    print(f"\n[{case} {precision}] {len(a['photon']['x'])} photons, "
+          f"{da['electron'].n_emit} emissions: fused = single steps")
+
+
+def test_fused_overflow_drops_the_same_photons(ctx):
+    w = W.plane_wave_collision(n=600, n_steps=120)
+    w["capacity"] = dict(w["capacity"], photon=3000)
+    ref = Simulation(w, precision="fp64", ctx=ctx)
+    ref.run(120)
+    a, da = _state(ref)
+    assert da["electron"].n_photon_drop > 0
+    sim = Simulation(w, precision="fp64", ctx=ctx)
+    sim.run_fused(120, 50)
+    b, db = _state(sim)
+    _same("overflow", a, b, da, db)
+    assert db["electron"].status == Q.QP_WARN_BUFFER_FULL
+
+
+def test_fused_plane_wave_against_the_oracle(ctx):
+    # the plane-wave case at full size: 4096 e- x 1000 steps, FP64, in
+    # windows of 100 steps; events exact, photons slot by slot
+    w = W.plane_wave_collision()
+    sim = Simulation(w, precision="fp64", ctx=ctx)
+    sim.run_fused(1000, 100)
+    g, d = _state(sim)
+    osim, osp = run_oracle(w, 1000)
+    assert d["electron"].n_emit == osim.stats.n_emit
+    assert d["electron"].n_photon == osim.stats.n_photon
+    compare_species(g["electron"], oracle_arrays(osp["electron"]), 1e-6, 1e-6, "electrons")
+    compare_species(g["photon"], oracle_arrays(osp["photon"]), 1e-6, 1e-4, "photons")
+
+
+def test_fused_rejects_pairs_on(ctx):
+    w = W.beam_collision(n=100, n_steps=10, buffer=10_000)
+    sim = Simulation(w, precision="fp64", ctx=ctx)
+    with pytest.raises(Q.QPError):
+        sim.run_fused(10, 5)
