@@ -12,6 +12,9 @@ The line also carries
       and pair buffers, the K steps from step 980, around the pulse peak),
       mixed and FP64, each with its roofline: the many-particle state in
       which the step's HBM bound can be approached;
+  `fused`: the plane-wave case (4096 e-, 1000 steps, no pairs) as one job,
+      one launch a step against one fused window of 1000 steps, FP64 and
+      mixed;
   `refill`: the same foil with its E_y and B_z refilled from the pulse
       before every step (qp_fill_yee2d), mixed and FP64;
   `serving`: the 256-request stream of beam-collision requests (n_e
@@ -248,6 +251,64 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
         "status": min(d.status for d in diag.values()),
     }
     return res
+
+
+def fused_leg(dev, flush, warmup: int):
+    """The plane-wave case (4096 e-, 1000 steps, no pairs) run as one job:
+    one launch a step (qp_step) against fused windows (qp_step_fused, the
+    whole job in one window of 1000 steps), FP64 and mixed.  L2 is flushed
+    before each timed job; the particle-steps are the live slots at each
+    step start (an untimed single-step run counts them; the fused run has
+    the same slots, bit for bit)."""
+    import torch
+
+    from paper_1311_1107_gb300 import qedpic as Q
+    from paper_1311_1107_gb300 import workloads as W
+    from paper_1311_1107_gb300.sim import Simulation
+
+    w = W.plane_wave_collision()
+    n_steps = int(w["params"]["n_steps"])
+    ctx = Q.qp_init_tables(W.LAMBDA_M, dev)
+    out = {"workload": w["name"], "fuse": n_steps}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "mixed"):
+        sim = Simulation(w, precision=prec, ctx=ctx, device=dev, track_chi=False)
+        names = ("electron", "positron", "photon")
+        counts = torch.zeros((n_steps, 3), dtype=torch.int64, device=f"cuda:{dev}")
+        live = [sim.species[n].n_live for n in names]
+        for k in range(n_steps):
+            torch.cat(live, out=counts[k])
+            sim.run(1)
+        slots = int(counts.sum().item())
+
+        def job(fused):
+            sim.load_initial()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if fused:
+                sim.run_fused(n_steps, n_steps)
+            else:
+                sim.run(n_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        for _ in range(max(1, warmup)):
+            job(False)
+            job(True)
+        t1, tf = job(False), job(True)
+        out[prec] = {"single_steps": {"value": round(slots / (t1 * 1e-3), 1), "unit": UNIT,
+                                      "ms_per_step": round(t1 / n_steps, 5)},
+                     "fused": {"value": round(slots / (tf * 1e-3), 1), "unit": UNIT,
+                               "ms_per_step": round(tf / n_steps, 5)},
+                     "speedup": round(t1 / tf, 3),
+                     "status": sim.diagnostics("electron").status}
+        sim.close()
+        del sim
+    torch.cuda.synchronize()
+    Q.qp_destroy(ctx)
+    return out
 
 
 def kernel_source_id() -> str:
@@ -666,6 +727,9 @@ def ours_arm(args):
                   "fp64": {k: r["fp64"][k] for k in ("value", "ms_per_step")},
                   "status": {"mixed": r["mixed"]["status"], "fp64": r["fp64"]["status"]}}
         del wr
+    fused = None
+    if world == 1 and args.workload == "foil" and not args.no_collision:
+        fused = fused_leg(dev, flush, args.warmup)
     serv = None
     if rank == 0 and world == 1 and not args.no_serving:
         serv = serving(dev, args.requests or 256, args.serving_nmax or 1e6)
@@ -701,7 +765,7 @@ def ours_arm(args):
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
                      "final_live": main_leg["fp64"]["final_live"]},
             "roofline": main_leg["mixed"]["roofline"],
-            "collision": coll, "refill": refill,
+            "collision": coll, "refill": refill, "fused": fused,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
             "clocks": clk,
             "status": {"mixed": main_leg["mixed"]["status"], "fp64": main_leg["fp64"]["status"]},

@@ -395,13 +395,13 @@ typedef struct {
  * across the target; the PIC context of the paper's section 3).  Writes E_y
  * at (x0 + i dx, y0 + (j + 1/2) dy) and B_z at (x0 + (i + 1/2) dx, y0 +
  * (j + 1/2) dy) of `grid` (kind QP_FIELD_YEE2D; its yee[1] and yee[5] are
- * written through, the other components are not touched).  The x-dependent
- * factors (amplitude, envelope, Gouy phase and curvature, the phase reduced
- * modulo 2 pi) are formed per column in FP64, the nodes in FP32: every node
- * is within ~1e-6 of a0 of the FP64 formula rounded to float.  Give the
- * step that follows t = n dt, as the particle step evaluates its fields at
- * that time.  Stream-ordered; the first call for a grid size allocates
- * context scratch (32 nx + 4 ny bytes).  QP_ERR_INVALID_ARG for a grid of
+ * written through, the other components are not touched).  One launch:
+ * each block forms the x-dependent factors of its 32 columns (amplitude,
+ * envelope, Gouy phase and curvature; the phase reduced modulo 2 pi in
+ * FP64) and the radii of its 64 rows, then its nodes in FP32: every node is
+ * within ~1e-6 of a0 of the FP64 formula rounded to float.  Give the step
+ * that follows t = n dt, as the particle step evaluates its fields at that
+ * time.  Stream-ordered, no allocation.  QP_ERR_INVALID_ARG for a grid of
  * another kind, missing E_y/B_z pointers or a non-positive size.
  */
 int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double t, void *stream);

@@ -61,8 +61,6 @@ struct qp_ctx {
     size_t stash_blocks = 0;          // blocks the stash is sized for
     void *d_fuse = nullptr;           // scratch of qp_step_fused
     size_t fuse_bytes = 0;
-    void *d_pulse = nullptr;          // scratch of qp_fill_yee2d
-    size_t pulse_bytes = 0;
     void *d_coal = nullptr;           // scratch of qp_coalesce_photons
     size_t coal_bytes = 0;
     long long *d_coal_stats = nullptr;  // [4] of the last coalescence
@@ -136,7 +134,6 @@ void release(qp_ctx *c)
     cudaFree(c->d_stash);
     cudaFree(c->d_coal);
     cudaFree(c->d_coal_stats);
-    cudaFree(c->d_pulse);
     cudaFree(c->d_fuse);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
@@ -1009,26 +1006,14 @@ int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double
         grid->nx <= 0 || grid->ny <= 0 || !(grid->dx > 0.0) || !(grid->dy > 0.0) ||
         !(p->w0 > 0.0) || !(p->tau_fwhm > 0.0) || !isfinite(t))
         return QP_ERR_INVALID_ARG;
+    if (grid->ny > (int64_t)64 * 65535)  // rows of 64 per block in grid.y
+        return QP_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return QP_ERR_CUDA;
-    const size_t bytes = (size_t)(2 * grid->nx) * sizeof(float4) + 256 +
-                         (size_t)grid->ny * sizeof(float);
-    if (bytes > ctx->pulse_bytes) {
-        void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes);
-        if (e != cudaSuccess) return cuda_status(e);
-        cudaFree(ctx->d_pulse);
-        ctx->d_pulse = q;
-        ctx->pulse_bytes = bytes;
-    }
-    float4 *cols = (float4 *)ctx->d_pulse;
-    float *rows = (float *)((char *)ctx->d_pulse +
-                            ((size_t)(2 * grid->nx) * sizeof(float4) + 255) / 256 * 256);
     const qp::Pulse2DDev pd{p->a0, p->w0, p->tau_fwhm, p->x_focus, p->t_focus, p->y_axis};
     return cuda_status(qp::launch_pulse_fill(pd, grid->nx, grid->ny, grid->dx, grid->dy,
                                              grid->x0, grid->y0, t, (float *)grid->yee[1],
-                                             (float *)grid->yee[5], cols, rows, ctx->num_sms,
-                                             (cudaStream_t)stream));
+                                             (float *)grid->yee[5], (cudaStream_t)stream));
 }
 
 static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }

@@ -209,66 +209,66 @@ cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, in
 
 // -------------------------------------------------------------------- pulse refill
 
-// Per-column factors of the 2D pulse (FP64, one thread per Ey column, Bz
-// column and row): E = A exp(-c r^2) cos(phi + kappa r^2) with
+// One launch: each block fills a tile of 32 columns x kPulseRows rows.  Its
+// column factors (for the E_y and the B_z staggering) and row radii go to
+// shared memory first: E = A exp(-c r^2) cos(phi + kappa r^2) with
 // A = a0 (1 + q^2)^(-1/4) exp(-2 ln2 eta^2/tau^2), c = 1/(w0^2 (1 + q^2)),
-// kappa = xi / (2 (xi^2 + zr^2)), phi = -eta - atan(q)/2 reduced to
-// [-pi, pi]; rows: r^2 = (y - y_axis)^2.  The nodes then need only FP32.
-__global__ void k_pulse_cols(Pulse2DDev p, int64_t nx, int64_t ny, double dx, double dy,
-                             double x0, double y0, double t, float4 *cols, float *rows)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < 2 * nx) {
-        const int s = k >= nx ? 1 : 0;
-        const int64_t i = k - s * nx;
-        const double x = x0 + ((double)i + 0.5 * s) * dx;
-        const double xi = x - p.x_focus;
-        const double eta = (t - p.t_focus) - xi;
-        const double zr = 0.5 * p.w0 * p.w0;
-        const double q = xi / zr;
-        const double wr2 = 1.0 + q * q;
-        const double A = p.a0 * pow(wr2, -0.25) *
-                         exp(-2.0 * 0.69314718055994530942 * eta * eta / (p.tau_fwhm * p.tau_fwhm));
-        double phi = -eta - 0.5 * atan(q);
-        phi -= 6.283185307179586477 * rint(phi * 0.15915494309189533577);
-        cols[k] = make_float4((float)A, (float)(1.0 / (p.w0 * p.w0 * wr2)),
-                              (float)(xi / (2.0 * (xi * xi + zr * zr))), (float)phi);
-    } else if (k < 2 * nx + ny) {
-        const int64_t j = k - 2 * nx;
-        const double r = y0 + ((double)j + 0.5) * dy - p.y_axis;
-        rows[j] = (float)(r * r);
-    }
-}
+// kappa = xi / (2 (xi^2 + zr^2)), phi = -eta - atan(q)/2.  Only eta and the
+// phase reduction modulo 2 pi are FP64 (the phase is hundreds of radians);
+// the factors and the nodes are FP32.
+constexpr int kPulseRows = 64;
 
-__global__ void __launch_bounds__(256) k_pulse_fill(const float4 *cols, const float *rows,
-                                                    int64_t nx, int64_t ny, float *ey,
-                                                    float *bz)
+__global__ void __launch_bounds__(256) k_pulse_fill(Pulse2DDev p, int64_t nx, int64_t ny,
+                                                    double dx, double dy, double x0, double y0,
+                                                    double t, float *ey, float *bz)
 {
-    const int64_t n = nx * ny;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const int64_t j = k / nx, i = k - j * nx;
-        const float r2 = rows[j];
-        const float4 e = cols[i], b = cols[nx + i];
+    __shared__ float4 s_col[64];
+    __shared__ float s_r2[kPulseRows];
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * kPulseRows;
+    if (tid < 64) {
+        const int s = tid >> 5;  // 0: E_y column, 1: B_z column (half a cell further)
+        const int64_t i = i0 + (tid & 31);
+        const double xi = x0 + ((double)i + 0.5 * s) * dx - p.x_focus;
+        const double eta = (t - p.t_focus) - xi;
+        const float zr = (float)(0.5 * p.w0 * p.w0);
+        const float xf = (float)xi, ef = (float)eta;
+        const float q = xf / zr, wr2 = 1.0f + q * q;
+        const float tau = (float)p.tau_fwhm;
+        const float A = (float)p.a0 * rsqrtf(sqrtf(wr2)) *
+                        expf(-1.3862943611198906f * ef * ef / (tau * tau));
+        // -eta reduced modulo 2 pi in FP64, then the Gouy phase
+        const double red = -eta - 6.283185307179586477 * rint(-eta * 0.15915494309189533577);
+        const float phi = (float)red - 0.5f * atanf(q);
+        s_col[tid] = make_float4(A, 1.0f / ((float)(p.w0 * p.w0) * wr2),
+                                 xf / (2.0f * (xf * xf + zr * zr)), phi);
+    } else if (tid < 64 + kPulseRows) {
+        const int64_t j = j0 + (tid - 64);
+        const double r = y0 + ((double)j + 0.5) * dy - p.y_axis;
+        s_r2[tid - 64] = (float)(r * r);
+    }
+    __syncthreads();
+    const int c = tid & 31;
+    const int64_t i = i0 + c;
+    if (i >= nx) return;
+    const float4 e = s_col[c], b = s_col[32 + c];
+    for (int r = tid >> 5; r < kPulseRows; r += 8) {
+        const int64_t j = j0 + r;
+        if (j >= ny) break;
+        const float r2 = s_r2[r];
+        const int64_t k = j * nx + i;
         ey[k] = e.x * expf(-e.y * r2) * cosf(fmaf(e.z, r2, e.w));
         bz[k] = b.x * expf(-b.y * r2) * cosf(fmaf(b.z, r2, b.w));
     }
 }
 
 cudaError_t launch_pulse_fill(const Pulse2DDev &p, int64_t nx, int64_t ny, double dx, double dy,
-                              double x0, double y0, double t, float *ey, float *bz, float4 *cols,
-                              float *rows, int num_sms, cudaStream_t st)
+                              double x0, double y0, double t, float *ey, float *bz,
+                              cudaStream_t st)
 {
     if (nx <= 0 || ny <= 0) return cudaSuccess;
-    const int64_t m = 2 * nx + ny;
-    k_pulse_cols<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(p, nx, ny, dx, dy, x0, y0, t, cols,
-                                                               rows);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int64_t blocks = (nx * ny + 255) / 256;
-    const int64_t cap = (int64_t)num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    k_pulse_fill<<<(unsigned)blocks, 256, 0, st>>>(cols, rows, nx, ny, ey, bz);
+    const dim3 grid((unsigned)((nx + 31) / 32), (unsigned)((ny + kPulseRows - 1) / kPulseRows));
+    k_pulse_fill<<<grid, 256, 0, st>>>(p, nx, ny, dx, dy, x0, y0, t, ey, bz);
     return cudaGetLastError();
 }
 

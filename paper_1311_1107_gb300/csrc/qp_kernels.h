@@ -44,13 +44,13 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
                             int grid, long long *stats, int *status, cudaStream_t st);
 
 // Refill of a 2D Yee grid's E_y and B_z with the 2D Gaussian pulse at time t
-// (qp_fill_yee2d): cols = 2 nx float4 and rows = ny floats of scratch.
+// (qp_fill_yee2d): one launch, no scratch.
 struct Pulse2DDev {
     double a0, w0, tau_fwhm, x_focus, t_focus, y_axis;
 };
 cudaError_t launch_pulse_fill(const Pulse2DDev &p, int64_t nx, int64_t ny, double dx, double dy,
-                              double x0, double y0, double t, float *ey, float *bz, float4 *cols,
-                              float *rows, int num_sms, cudaStream_t st);
+                              double x0, double y0, double t, float *ey, float *bz,
+                              cudaStream_t st);
 
 constexpr int kDiagBlocks = 256;
 constexpr int kDiagWords = 8 + QP_HIST_BINS;  // scalars + histogram per block
