@@ -145,6 +145,11 @@ def lib():
             "or_coalesce": (C.c_int, [C.POINTER(_Species), C.POINTER(CoalesceParams),
                                       C.POINTER(CoalesceStats)]),
             "or_pulse2d_eval": (d, [C.POINTER(Pulse2D), d, d, d]),
+            "or_yee_advance_b": (None, [C.POINTER(vp), i64, i64, d, d, d]),
+            "or_yee_advance_e": (None, [C.POINTER(vp), C.POINTER(vp), i64, i64, d, d, d]),
+            "or_deposit_current": (None, [C.POINTER(_Species), d, d, C.POINTER(vp), i64, i64, d,
+                                          d, d, d]),
+            "or_sort_by_cell": (C.c_int, [C.POINTER(_Species), i64, i64, d, d, d, d]),
             "or_fill_pulse2d": (None, [C.POINTER(Pulse2D), vp, vp, i64, i64, d, d, d, d, d]),
         }
         for name, (res, args) in sig.items():
@@ -483,3 +488,39 @@ def fill_pulse2d(p: Pulse2D, field: Field, t: float):
                           bz.ctypes.data_as(C.c_void_p), int(field.nx), int(field.ny),
                           float(field.dx), float(field.dy), float(field.x0), float(field.y0),
                           float(t))
+
+
+def _ptrs(arrays, dtype):
+    out = (C.c_void_p * len(arrays))()
+    for k, a in enumerate(arrays):
+        assert a.dtype == dtype and a.flags["C_CONTIGUOUS"]
+        out[k] = a.ctypes.data
+    return out
+
+
+def yee_advance_b(comps, dx, dy, dtb):
+    """B -= dtb curl E on six float32 (ny, nx) arrays (Ex Ey Ez Bx By Bz), in place."""
+    ny, nx = comps[0].shape
+    lib().or_yee_advance_b(_ptrs(comps, np.float32), nx, ny, float(dx), float(dy), float(dtb))
+
+
+def yee_advance_e(comps, J, dx, dy, dt):
+    """E += dt (curl B - J); J: three float32 (ny, nx) arrays or None."""
+    ny, nx = comps[0].shape
+    lib().or_yee_advance_e(_ptrs(comps, np.float32), None if J is None else _ptrs(J, np.float32),
+                           nx, ny, float(dx), float(dy), float(dt))
+
+
+def deposit_current(sp: Species, q, dt, J, dx, dy, x0=0.0, y0=0.0):
+    """Add the current of sp's live particles to J (three float64 (ny, nx) arrays)."""
+    ny, nx = J[0].shape
+    st = sp._struct()
+    lib().or_deposit_current(C.byref(st), float(q), float(dt), _ptrs(J, np.float64), nx, ny,
+                             float(dx), float(dy), float(x0), float(y0))
+
+
+def sort_by_cell(sp: Species, nx, ny, dx, dy, x0=0.0, y0=0.0):
+    st = sp._struct()
+    if lib().or_sort_by_cell(C.byref(st), int(nx), int(ny), float(dx), float(dy), float(x0),
+                             float(y0)) != 0:
+        raise MemoryError("or_sort_by_cell")

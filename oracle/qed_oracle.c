@@ -1404,3 +1404,174 @@ void or_fill_pulse2d(const or_pulse2d *p, float *ey, float *bz, int64_t nx, int6
         }
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* PIC coupling around the step: 2D Yee Maxwell solver, current deposition,  */
+/* particle sorting (section 3: the QED step runs inside a PIC code)          */
+/* ------------------------------------------------------------------------- */
+
+/* The six float components of a 2D Yee grid, ny rows of nx values, on the
+ * staggering of or_yee_component: Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j),
+ * Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2); values outside the grid
+ * are 0.  Normalised units (c = 1): dB/dt = -curl E, dE/dt = curl B - J,
+ * with J in units of e n_c c (the charge density of the reference density
+ * moving at c).  READING: the paper uses CALDER's solver and describes none;
+ * this is the standard leapfrog on Yee's lattice, d/dz = 0. */
+static float or_at(const float *a, int64_t nx, int64_t ny, int64_t i, int64_t j)
+{
+    if (i < 0 || j < 0 || i >= nx || j >= ny) return 0.0f;
+    return a[j * nx + i];
+}
+
+/* B -= dtb curl E (each new value rounded to float). */
+void or_yee_advance_b(float *const F[6], int64_t nx, int64_t ny, double dx, double dy, double dtb)
+{
+    float *Bx = F[3], *By = F[4], *Bz = F[5];
+    const float *Ex = F[0], *Ey = F[1], *Ez = F[2];
+    size_t n = (size_t)(nx * ny);
+    float *nbx = malloc(n * sizeof(float)), *nby = malloc(n * sizeof(float)),
+          *nbz = malloc(n * sizeof(float));
+    for (int64_t j = 0; j < ny; j++)
+        for (int64_t i = 0; i < nx; i++) {
+            int64_t k = j * nx + i;
+            /* Bx (i, j+1/2): d Ez/dy between (i, j+1) and (i, j) */
+            double dEz_dy = ((double)or_at(Ez, nx, ny, i, j + 1) - (double)Ez[k]) / dy;
+            /* By (i+1/2, j): -(-dEz/dx) = +dEz/dx */
+            double dEz_dx = ((double)or_at(Ez, nx, ny, i + 1, j) - (double)Ez[k]) / dx;
+            /* Bz (i+1/2, j+1/2): dEy/dx - dEx/dy */
+            double dEy_dx = ((double)or_at(Ey, nx, ny, i + 1, j) - (double)Ey[k]) / dx;
+            double dEx_dy = ((double)or_at(Ex, nx, ny, i, j + 1) - (double)Ex[k]) / dy;
+            nbx[k] = (float)((double)Bx[k] - dtb * dEz_dy);
+            nby[k] = (float)((double)By[k] + dtb * dEz_dx);
+            nbz[k] = (float)((double)Bz[k] - dtb * (dEy_dx - dEx_dy));
+        }
+    memcpy(Bx, nbx, n * sizeof(float));
+    memcpy(By, nby, n * sizeof(float));
+    memcpy(Bz, nbz, n * sizeof(float));
+    free(nbx);
+    free(nby);
+    free(nbz);
+}
+
+/* E += dt (curl B - J); J on E's staggering (NULL: no current). */
+void or_yee_advance_e(float *const F[6], const float *const J[3], int64_t nx, int64_t ny,
+                      double dx, double dy, double dt)
+{
+    float *Ex = F[0], *Ey = F[1], *Ez = F[2];
+    const float *Bx = F[3], *By = F[4], *Bz = F[5];
+    size_t n = (size_t)(nx * ny);
+    float *nex = malloc(n * sizeof(float)), *ney = malloc(n * sizeof(float)),
+          *nez = malloc(n * sizeof(float));
+    for (int64_t j = 0; j < ny; j++)
+        for (int64_t i = 0; i < nx; i++) {
+            int64_t k = j * nx + i;
+            /* Ex (i+1/2, j): dBz/dy between (i+1/2, j+1/2) and (i+1/2, j-1/2) */
+            double dBz_dy = ((double)Bz[k] - (double)or_at(Bz, nx, ny, i, j - 1)) / dy;
+            /* Ey (i, j+1/2): -dBz/dx between (i+1/2, j+1/2) and (i-1/2, j+1/2) */
+            double dBz_dx = ((double)Bz[k] - (double)or_at(Bz, nx, ny, i - 1, j)) / dx;
+            /* Ez (i, j): dBy/dx - dBx/dy */
+            double dBy_dx = ((double)By[k] - (double)or_at(By, nx, ny, i - 1, j)) / dx;
+            double dBx_dy = ((double)Bx[k] - (double)or_at(Bx, nx, ny, i, j - 1)) / dy;
+            double jx = J ? (double)J[0][k] : 0.0, jy = J ? (double)J[1][k] : 0.0,
+                   jz = J ? (double)J[2][k] : 0.0;
+            nex[k] = (float)((double)Ex[k] + dt * (dBz_dy - jx));
+            ney[k] = (float)((double)Ey[k] + dt * (-dBz_dx - jy));
+            nez[k] = (float)((double)Ez[k] + dt * (dBy_dx - dBx_dy - jz));
+        }
+    memcpy(Ex, nex, n * sizeof(float));
+    memcpy(Ey, ney, n * sizeof(float));
+    memcpy(Ez, nez, n * sizeof(float));
+    free(nex);
+    free(ney);
+    free(nez);
+}
+
+/* Current of the live slots of a lepton species, added to J (FP64 arrays on
+ * E's staggering, ny rows of nx): each particle deposits q w v / (dx dy)
+ * with the linear (cloud-in-cell) weights of each component's staggering at
+ * the mid-step position x - v dt/2 (x^(n+1) and v^(n+1/2) after a step).
+ * READING: direct (not charge-conserving) deposition. */
+void or_deposit_current(const or_species *S, double q, double dt, double *const J[3], int64_t nx,
+                        int64_t ny, double dx, double dy, double x0, double y0)
+{
+    static const double ox[3] = {0.5, 0.0, 0.0}, oy[3] = {0.0, 0.5, 0.0};
+    for (int64_t p = 0; p < S->n; p++) {
+        double u[3] = {S->ux[p], S->uy[p], S->uz[p]};
+        double g = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        double v[3] = {u[0] / g, u[1] / g, u[2] / g};
+        double xm = S->x[p] - 0.5 * dt * v[0], ym = S->y[p] - 0.5 * dt * v[1];
+        double a = q * S->w[p] / (dx * dy);
+        for (int c = 0; c < 3; c++) {
+            double gx = (xm - x0) / dx - ox[c], gy = (ym - y0) / dy - oy[c];
+            double fi = floor(gx), fj = floor(gy);
+            double fx = gx - fi, fy = gy - fj;
+            for (int b = 0; b < 2; b++)
+                for (int e = 0; e < 2; e++) {
+                    double ii = fi + e, jj = fj + b;
+                    if (!(ii >= 0.0 && jj >= 0.0 && ii < (double)nx && jj < (double)ny)) continue;
+                    double wgt = (e ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+                    J[c][(int64_t)jj * nx + (int64_t)ii] += a * v[c] * wgt;
+                }
+        }
+    }
+}
+
+/* Stable sort of the live slots of a species by the cell of the grid that
+ * holds them (row-major, floor((y - y0)/dy) nx + floor((x - x0)/dx));
+ * particles outside the grid after all others, in slot order.  Every array
+ * moves with its particle; slots are renumbered (later draws follow the new
+ * slots).  Returns 0, or -1 without memory. */
+int or_sort_by_cell(or_species *S, int64_t nx, int64_t ny, double dx, double dy, double x0,
+                    double y0)
+{
+    int64_t n = S->n;
+    or_keyslot *ks = malloc(sizeof(or_keyslot) * (size_t)(n > 0 ? n : 1));
+    double *buf = malloc(sizeof(double) * 11 * (size_t)(n > 0 ? n : 1));
+    if (!ks || !buf) {
+        free(ks);
+        free(buf);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        double gx = floor((S->x[i] - x0) / dx), gy = floor((S->y[i] - y0) / dy);
+        uint64_t key = (uint64_t)nx * (uint64_t)ny;  /* outside: after every cell */
+        if (gx >= 0.0 && gy >= 0.0 && gx < (double)nx && gy < (double)ny)
+            key = (uint64_t)gy * (uint64_t)nx + (uint64_t)gx;
+        ks[i].key = key;
+        ks[i].slot = i;
+    }
+    qsort(ks, (size_t)n, sizeof(or_keyslot), or_keyslot_cmp);
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = ks[k].slot;
+        double *o = buf + 11 * k;
+        o[0] = S->x[i];
+        o[1] = S->y[i];
+        o[2] = S->z ? S->z[i] : 0.0;
+        o[3] = S->ux[i];
+        o[4] = S->uy[i];
+        o[5] = S->uz[i];
+        o[6] = S->tau[i];
+        o[7] = S->w[i];
+        o[8] = S->chi ? S->chi[i] : 0.0;
+        o[9] = S->margin ? S->margin[i] : INFINITY;
+        o[10] = S->nemit ? (double)S->nemit[i] : 0.0;
+    }
+    for (int64_t k = 0; k < n; k++) {
+        const double *o = buf + 11 * k;
+        S->x[k] = o[0];
+        S->y[k] = o[1];
+        if (S->z) S->z[k] = o[2];
+        S->ux[k] = o[3];
+        S->uy[k] = o[4];
+        S->uz[k] = o[5];
+        S->tau[k] = o[6];
+        S->w[k] = o[7];
+        if (S->chi) S->chi[k] = o[8];
+        if (S->margin) S->margin[k] = o[9];
+        if (S->nemit) S->nemit[k] = (int32_t)o[10];
+        if (S->ids) S->ids[k] = or_slot_id(S, k);
+    }
+    free(ks);
+    free(buf);
+    return 0;
+}
