@@ -12,6 +12,8 @@ The line also carries
       and pair buffers, the K steps from step 980, around the pulse peak),
       mixed and FP64, each with its roofline: the many-particle state in
       which the step's HBM bound can be approached;
+  `pic`: the same foil as a PIC cycle (Yee solver and current deposition
+      around every QED step: qp_yee_advance_*, qp_deposit_current);
   `fused`: the plane-wave case (4096 e-, 1000 steps, no pairs) as one job,
       one launch a step against one fused window of 1000 steps, FP64 and
       mixed;
@@ -71,7 +73,8 @@ def parse():
     p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--workload", choices=("foil", "collision", "plane", "serving"),
+    p.add_argument("--workload", choices=("foil", "collision", "plane", "serving", "fused",
+                                          "coalesce"),
                    default="foil")
     p.add_argument("--requests", type=int, default=None,
                    help="serving: requests in the stream (default 256)")
@@ -727,6 +730,19 @@ def ours_arm(args):
                   "fp64": {k: r["fp64"][k] for k in ("value", "ms_per_step")},
                   "status": {"mixed": r["mixed"]["status"], "fp64": r["fp64"]["status"]}}
         del wr
+    # the same foil as a PIC cycle: the grid's own fields advanced by the
+    # Yee solver with the electrons' current around every QED step
+    pic = None
+    if world == 1 and args.workload == "foil" and not args.no_collision:
+        from paper_1311_1107_gb300 import workloads as W
+        wp = W.laser_on_foil(seed=0, pic=True)
+        r = leg(wp, args, dev, dist, flush, ids, "k_step_foil2d.md", hbm_peak, peak_kind)
+        pic = {"workload": wp["name"], "value": r["mixed"]["value"], "unit": UNIT,
+               "ms_per_step": r["mixed"]["ms_per_step"],
+               "roofline": dict(r["mixed"]["roofline"], traffic=None, traffic_read_write=None),
+               "fp64": {k: r["fp64"][k] for k in ("value", "ms_per_step")},
+               "status": {"mixed": r["mixed"]["status"], "fp64": r["fp64"]["status"]}}
+        del wp
     fused = None
     if world == 1 and args.workload == "foil" and not args.no_collision:
         fused = fused_leg(dev, flush, args.warmup)
@@ -765,7 +781,7 @@ def ours_arm(args):
                      "mixed_over_fp64": round(v_mixed / v_fp64, 3),
                      "final_live": main_leg["fp64"]["final_live"]},
             "roofline": main_leg["mixed"]["roofline"],
-            "collision": coll, "refill": refill, "fused": fused,
+            "collision": coll, "refill": refill, "pic": pic, "fused": fused,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches, "serving": serv,
             "clocks": clk,
             "status": {"mixed": main_leg["mixed"]["status"], "fp64": main_leg["fp64"]["status"]},
@@ -780,12 +796,87 @@ def wc_start(args) -> int:
     return 980 if args.start_step is None else args.start_step
 
 
+def fused_arm(args):
+    """--workload fused: the fused plane-wave leg alone (one JSON line)."""
+    import torch
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda:0")
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = fused_leg(0, flush, args.warmup)
+    clk = clocks.stop()
+    line = {"metric": "fused steps: particle-steps/s, one launch a step vs fused windows",
+            "value": res["mixed"]["fused"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1000,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (mixed path)", "data": "synthetic",
+            "config": {"workload": res["workload"]}, "fused": res, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+COALESCE_STEPS = 30
+
+
+def coalesce_arm(args):
+    """--workload coalesce: the photons of the beam collision after its
+    window (collision-n electrons, steps from start-step), compacted and
+    coalesced; K timed repetitions, each on a fresh copy of the photons."""
+    import torch
+
+    from paper_1311_1107_gb300 import qedpic as Q
+    from paper_1311_1107_gb300 import workloads as W
+    from paper_1311_1107_gb300.sim import Simulation
+
+    torch.cuda.set_device(0)
+    w = workload("collision", 0, args.start_step, args.collision_n or 2e6)
+    ctx = Q.qp_init_tables(W.LAMBDA_M, 0)
+    sim = Simulation(w, precision="mixed", ctx=ctx, track_chi=False)
+    sim.run(COALESCE_STEPS)
+    torch.cuda.synchronize()
+    ph = sim.species["photon"]
+    n = ph.count()
+    keep = ph.block[:, :n].clone()
+    sig = W.length(2e-6)
+    # a box over the beam's 4 sigma, 8 energy bins an octave, 8 direction bins
+    x0 = float(ph.t["x"][:n].min()) - 1.0
+    box = (x0, -4 * sig, -4 * sig, 8 * sig / 32, 8 * sig / 32, 8 * sig / 32)
+    p = Q.coalesce_params(box, (64, 32, 32), 8, 8, 3, seed=1, step=sim.step_index)
+    stream = torch.cuda.current_stream()
+    times, stats = [], None
+    for rep in range(args.warmup + args.steps):
+        ph.block[:, :n].copy_(keep)
+        ph.n_live.fill_(n)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Q.qp_coalesce_photons(ctx, ph.handle, p, None, stats=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append(a.elapsed_time(b))
+    stats = Q.qp_coalesce_photons(ctx, ph.handle, None)  # compaction of the result
+    ms = float(np.median(times))
+    line = {"metric": "super-photon coalescence: photons/s", "value": round(n / (ms * 1e-3), 1),
+            "unit": "photons/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"photons of {w['name']} after {COALESCE_STEPS} steps",
+                       "photons": n, "after": stats["n_after"], "grid": "64x32x32 cells",
+                       "bins": "8 energy bins an octave, 8 direction bins"}}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    Q.qp_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "serving":
         serving_arm(args)
+    elif args.workload == "fused":
+        fused_arm(args)
+    elif args.workload == "coalesce":
+        coalesce_arm(args)
     else:
         ours_arm(args)
 

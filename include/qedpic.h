@@ -406,6 +406,54 @@ typedef struct {
  */
 int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double t, void *stream);
 
+/* ---- PIC coupling: 2D Yee Maxwell solver, current deposition, sorting ----
+ *
+ * The paper's QED step runs inside a PIC code (section 3, CALDER); these
+ * calls are the rest of a 2D PIC cycle around qp_step on a QP_FIELD_YEE2D
+ * grid (the grid qp_step gathers from; all six component pointers must be
+ * set and are written through).  Staggering as for the gather: Ex (i+1/2,
+ * j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2,
+ * j+1/2); fields outside the grid are taken as 0.  Normalised units (c = 1):
+ * dB/dt = -curl E, dE/dt = curl B - J, J in units of e n_c c (n in units of
+ * the reference density n_c, the weights of the foil workload's electrons
+ * being n dx dy / ppc).  FP32 arithmetic on the FP32 grid; one thread a node
+ * or a particle; stream-ordered, no allocation (the sort excepted).  A cycle
+ * with E^n and B^(n-1/2) stored:
+ *   qp_yee_advance_b(dt/2)   B^(n-1/2) -> B^n
+ *   qp_step                  particles pushed in E^n, B^n
+ *   J = 0; qp_deposit_current for electrons and positrons: J^(n+1/2)
+ *   qp_yee_advance_b(dt/2)   B^n -> B^(n+1/2)
+ *   qp_yee_advance_e(dt, J)  E^n -> E^(n+1)
+ * QP_ERR_INVALID_ARG for a grid of another kind or with a missing component.
+ */
+
+/* B -= dtb curl E on the grid, in place. */
+int qp_yee_advance_b(qp_ctx *ctx, const qp_field *grid, double dtb, void *stream);
+
+/* E += dt (curl B - J) on the grid, in place; jx, jy, jz: device float
+ * arrays of ny rows of nx values on E's staggering, or NULL (no current). */
+int qp_yee_advance_e(qp_ctx *ctx, const qp_field *grid, const float *jx, const float *jy,
+                     const float *jz, double dt, void *stream);
+
+/* Adds the current of a lepton species' live slots to jx, jy, jz (device
+ * float arrays on E's staggering, ny rows of nx, caller-owned; the caller
+ * zeroes them): each particle gives q w v / (dx dy) (q = -1 for electrons,
+ * +1 for positrons) with the linear weights of each component's staggering
+ * at its mid-step position x - v dt/2 (after qp_step: x^(n+1), v^(n+1/2)).
+ * Direct deposition, not charge-conserving; float atomics, so the last bits
+ * of a sum vary from run to run.  QP_ERR_INVALID_ARG for a photon species. */
+int qp_deposit_current(qp_ctx *ctx, int32_t handle, const qp_field *grid, float *jx, float *jy,
+                       float *jz, double dt, void *stream);
+
+/* Stable sort of a species' live slots by the grid cell that holds them
+ * (row-major: floor((y - y0)/dy) nx + floor((x - x0)/dx); particles outside
+ * the grid after every cell, in slot order): every array moves with its
+ * particle, so the gather of the next steps reads the grid cell by cell.
+ * Slots are renumbered: later draws follow the new slots.  The first call
+ * for a capacity allocates the context's scratch (as qp_coalesce_photons;
+ * not during a stream capture).  Capacity below 2^32 slots. */
+int qp_sort_species(qp_ctx *ctx, int32_t handle, const qp_field *grid, void *stream);
+
 /* ---- super-photon compaction and coalescence ---------------------------- */
 
 /* Grid and bins of qp_coalesce_photons.  A live photon belongs to the group

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqedpic.so")
 
 SOURCES = ["qp_step_fp64.cu", "qp_step_mixed.cu", "qp_kernels.cu", "qp_abi.cu", "qp_noalloc.cu",
-           "qp_coalesce.cu", "qp_tables.cpp"]
+           "qp_coalesce.cu", "qp_pic.cu", "qp_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-unit flags.  The mixed-precision step divides in FP32 with the
 # hardware reciprocal (2 ulp): its tolerance is set by FP32 physics, and the

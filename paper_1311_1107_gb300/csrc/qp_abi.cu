@@ -1016,6 +1016,91 @@ int qp_fill_yee2d(qp_ctx *ctx, const qp_pulse2d *p, const qp_field *grid, double
                                              (float *)grid->yee[5], (cudaStream_t)stream));
 }
 
+// A full 2D Yee grid (all six components) as the PIC kernels take it.
+static bool yee_grid_of(const qp_field *f, qp::YeeGrid &g)
+{
+    if (!f || f->kind != QP_FIELD_YEE2D || f->nx <= 0 || f->ny <= 0 || !(f->dx > 0.0) ||
+        !(f->dy > 0.0) || !isfinite(f->x0) || !isfinite(f->y0))
+        return false;
+    for (int c = 0; c < 6; ++c) {
+        if (!f->yee[c]) return false;
+        g.f[c] = (float *)f->yee[c];
+    }
+    g.nx = f->nx;
+    g.ny = f->ny;
+    g.dx = f->dx;
+    g.dy = f->dy;
+    g.x0 = f->x0;
+    g.y0 = f->y0;
+    return true;
+}
+
+int qp_yee_advance_b(qp_ctx *ctx, const qp_field *grid, double dtb, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    qp::YeeGrid g{};
+    if (!yee_grid_of(grid, g) || !isfinite(dtb)) return QP_ERR_INVALID_ARG;
+    DeviceGuard d(ctx->device);
+    if (!d.ok) return QP_ERR_CUDA;
+    return cuda_status(qp::launch_yee_b(g, dtb, ctx->num_sms, (cudaStream_t)stream));
+}
+
+int qp_yee_advance_e(qp_ctx *ctx, const qp_field *grid, const float *jx, const float *jy,
+                     const float *jz, double dt, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    qp::YeeGrid g{};
+    if (!yee_grid_of(grid, g) || !isfinite(dt)) return QP_ERR_INVALID_ARG;
+    DeviceGuard d(ctx->device);
+    if (!d.ok) return QP_ERR_CUDA;
+    return cuda_status(qp::launch_yee_e(g, jx, jy, jz, dt, ctx->num_sms, (cudaStream_t)stream));
+}
+
+int qp_deposit_current(qp_ctx *ctx, int32_t handle, const qp_field *grid, float *jx, float *jy,
+                       float *jz, double dt, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &sd = ctx->species[handle].d;
+    qp::YeeGrid g{};
+    if (sd.kind == QP_PHOTON || !yee_grid_of(grid, g) || !jx || !jy || !jz || !isfinite(dt))
+        return QP_ERR_INVALID_ARG;
+    DeviceGuard d(ctx->device);
+    if (!d.ok) return QP_ERR_CUDA;
+    const double q = sd.kind == QP_ELECTRON ? -1.0 : 1.0;
+    return cuda_status(qp::launch_deposit(species_dev(ctx, handle), q, dt, g, jx, jy, jz,
+                                          ctx->d_status, ctx->num_sms, (cudaStream_t)stream));
+}
+
+int qp_sort_species(qp_ctx *ctx, int32_t handle, const qp_field *grid, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &sd = ctx->species[handle].d;
+    qp::YeeGrid g{};
+    if (!yee_grid_of(grid, g) || sd.capacity >= (int64_t)0xFFFFFFFFll) return QP_ERR_INVALID_ARG;
+    if ((double)g.nx * (double)g.ny > 9.0e18) return QP_ERR_INVALID_ARG;
+    DeviceGuard d(ctx->device);
+    if (!d.ok) return QP_ERR_CUDA;
+    const int grid_blocks = 2 * ctx->num_sms;
+    const size_t bytes = qp::coalesce_scratch_bytes(sd.capacity, grid_blocks);
+    if (bytes > ctx->coal_bytes) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(ctx->d_coal);
+        ctx->d_coal = p;
+        ctx->coal_bytes = bytes;
+    }
+    if (!ctx->d_coal_stats) {
+        cudaError_t e = cudaMalloc(&ctx->d_coal_stats, 4 * sizeof(long long));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(qp::launch_sort_cells(species_dev(ctx, handle), g, ctx->d_coal,
+                                             grid_blocks, ctx->d_coal_stats, ctx->d_status,
+                                             (cudaStream_t)stream));
+}
+
 static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
 int qp_coalesce_photons(qp_ctx *ctx, int32_t handle, const qp_coalesce_params *P,

@@ -1,5 +1,6 @@
 // Compaction and coalescence of super-photons (qp_compact_photons,
-// qp_coalesce_photons).
+// qp_coalesce_photons), and the stable sort of a species by cell
+// (qp_sort_species) on the same radix sort.
 //
 // The paper (section 3, last paragraph) names a coalescence of super-photons
 // that conserves energy and momentum on average, without an algorithm.
@@ -466,6 +467,52 @@ __global__ void __launch_bounds__(kCoThreads) k_co_copy_back(SpeciesDev S, Stage
     }
 }
 
+// ---------------------------------------------------------------- sort by cell
+
+// Cell keys of the live slots (row-major; outside the grid: nx ny, after
+// every cell) and the identity order.
+__global__ void __launch_bounds__(kCoThreads) k_sort_prepare(SpeciesDev S, YeeGrid g,
+                                                             unsigned long long *keys,
+                                                             unsigned *vals, long long *counts,
+                                                             int *status)
+{
+    const long long n = live_count(S, status);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counts[0] = n;
+        counts[1] = n;
+    }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double gx = floor((S.x[i] - g.x0) / g.dx), gy = floor((S.y[i] - g.y0) / g.dy);
+        unsigned long long key = (unsigned long long)g.nx * (unsigned long long)g.ny;
+        if (gx >= 0.0 && gy >= 0.0 && gx < (double)g.nx && gy < (double)g.ny)
+            key = (unsigned long long)gy * (unsigned long long)g.nx + (unsigned long long)gx;
+        keys[i] = key;
+        vals[i] = (unsigned)i;
+    }
+}
+
+// Every array of the sorted slot k from its source slot, into the staging arrays.
+__global__ void __launch_bounds__(kCoThreads) k_sort_gather(SpeciesDev S, const unsigned *vals,
+                                                            Stage st, const long long *counts)
+{
+    const long long n = counts[0];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const unsigned i = vals[k];
+        st.f[0][k] = S.x[i];
+        st.f[1][k] = S.y[i];
+        st.f[2][k] = S.z ? S.z[i] : 0.0;
+        st.f[3][k] = S.ux[i];
+        st.f[4][k] = S.uy[i];
+        st.f[5][k] = S.uz[i];
+        st.f[6][k] = S.tau[i];
+        st.f[7][k] = S.w[i];
+        st.f[8][k] = S.chi ? S.chi[i] : 0.0;
+        st.nemit[k] = S.nemit ? S.nemit[i] : 0;
+    }
+}
+
 }  // namespace
 
 size_t coalesce_scratch_bytes(int64_t cap, int grid)
@@ -552,6 +599,47 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
         k_co_pairs<<<grid, kCoThreads, 0, st>>>(S, C, keys[cur], vals[cur], role, off, stg,
                                                  counts);
     }
+    k_co_copy_back<<<grid, kCoThreads, 0, st>>>(S, stg, counts, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_cells(const SpeciesDev &S, const YeeGrid &g, void *scratch, int grid,
+                              long long *stats, int *status, cudaStream_t st)
+{
+    const size_t c = (size_t)(S.cap > 0 ? S.cap : 1);
+    unsigned char *p = (unsigned char *)scratch;
+    auto take = [&](size_t bytes) {
+        unsigned char *q = p;
+        p += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    unsigned long long *keys[2] = {(unsigned long long *)take(c * 8),
+                                   (unsigned long long *)take(c * 8)};
+    unsigned *vals[2] = {(unsigned *)take(c * 4), (unsigned *)take(c * 4)};
+    (void)take(c);      // roles (unused here)
+    (void)take(c * 4);  // offsets (unused here)
+    Stage stg;
+    for (int f = 0; f < 9; ++f) stg.f[f] = (double *)take(c * 8);
+    stg.nemit = (int *)take(c * 4);
+    unsigned *hist = (unsigned *)take((size_t)kRadix * grid * 4);
+    (void)take((size_t)grid * 4 + 64);
+    long long *counts = (long long *)take(16 * 8);
+    const unsigned long long top = (unsigned long long)g.nx * (unsigned long long)g.ny;
+    int bits = 0;
+    while (bits < 64 && (top >> bits) != 0ull) ++bits;
+    const int passes = (bits + 7) / 8;
+    cudaError_t e = cudaMemsetAsync(stats, 0, 4 * 8, st);
+    if (e != cudaSuccess) return e;
+    k_sort_prepare<<<grid, kCoThreads, 0, st>>>(S, g, keys[0], vals[0], counts, status);
+    int cur = 0;
+    for (int ps = 0; ps < passes; ++ps) {
+        k_co_hist<<<grid, kCoThreads, 0, st>>>(keys[cur], 8 * ps, hist, counts);
+        k_co_scan<<<1, 1024, 0, st>>>(hist, kRadix * grid, nullptr);
+        k_co_scatter<<<grid, kCoThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1],
+                                                   vals[cur ^ 1], 8 * ps, hist, counts);
+        cur ^= 1;
+    }
+    k_sort_gather<<<grid, kCoThreads, 0, st>>>(S, vals[cur], stg, counts);
     k_co_copy_back<<<grid, kCoThreads, 0, st>>>(S, stg, counts, stats);
     return cudaGetLastError();
 }

@@ -35,6 +35,22 @@ cudaError_t launch_diag(const SpeciesDev &S, int is_photon, double *partials, in
 cudaError_t launch_wait_selftest(unsigned long long *words, unsigned spin_limit, int *status,
                                  cudaStream_t st);
 
+// A 2D Yee grid (qp_pic.cu): six float components, ny rows of nx values.
+struct YeeGrid {
+    float *f[6];  // Ex Ey Ez Bx By Bz
+    int64_t nx, ny;
+    double dx, dy, x0, y0;
+};
+cudaError_t launch_yee_b(const YeeGrid &g, double dtb, int num_sms, cudaStream_t st);
+cudaError_t launch_yee_e(const YeeGrid &g, const float *jx, const float *jy, const float *jz,
+                         double dt, int num_sms, cudaStream_t st);
+cudaError_t launch_deposit(const SpeciesDev &S, double q, double dt, const YeeGrid &g, float *jx,
+                           float *jy, float *jz, int *status, int num_sms, cudaStream_t st);
+// Stable sort of a species' live slots by cell of g (qp_coalesce.cu; the
+// coalescence scratch, stats as there).
+cudaError_t launch_sort_cells(const SpeciesDev &S, const YeeGrid &g, void *scratch, int grid,
+                              long long *stats, int *status, cudaStream_t st);
+
 // Compaction / coalescence of a photon species (qp_coalesce.cu): scratch
 // bytes for `cap` slots and `grid` blocks, and the stream-ordered pipeline
 // (P = NULL: compaction only).  stats: 4 device int64 (groups merged,

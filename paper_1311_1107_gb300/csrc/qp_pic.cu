@@ -1,0 +1,141 @@
+// PIC coupling around the QED step on a 2D Yee grid (qp_yee_advance_b,
+// qp_yee_advance_e, qp_deposit_current): the paper's QED step runs inside
+// a PIC code (section 3); these are the field solver and the current
+// deposition a 2D PIC cycle needs around it.
+//
+// Grid: six float components, ny rows of nx values, staggered as the
+// step's field gather reads them: Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j),
+// Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2); values outside the grid
+// are 0.  Normalised units (c = 1): dB/dt = -curl E, dE/dt = curl B - J, J in
+// units of e n_c c.  One thread a node; every node's update reads its own
+// value and neighbours of the other field only, so both updates run in
+// place.  FP32 arithmetic (the grid is FP32).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qp_kernels.h"
+
+namespace qp {
+namespace {
+
+constexpr int kPicBlock = 256;
+
+__device__ __forceinline__ float at(const float *a, int64_t nx, int64_t ny, int64_t i, int64_t j)
+{
+    return (i < 0 || j < 0 || i >= nx || j >= ny) ? 0.0f : a[j * nx + i];
+}
+
+__global__ void __launch_bounds__(kPicBlock) k_yee_b(YeeGrid g, float dtb)
+{
+    const int64_t n = g.nx * g.ny;
+    const float idx = 1.0f / g.dx, idy = 1.0f / g.dy;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const int64_t j = k / g.nx, i = k - j * g.nx;
+        const float ez = g.f[2][k];
+        const float dEz_dy = (at(g.f[2], g.nx, g.ny, i, j + 1) - ez) * idy;
+        const float dEz_dx = (at(g.f[2], g.nx, g.ny, i + 1, j) - ez) * idx;
+        const float dEy_dx = (at(g.f[1], g.nx, g.ny, i + 1, j) - g.f[1][k]) * idx;
+        const float dEx_dy = (at(g.f[0], g.nx, g.ny, i, j + 1) - g.f[0][k]) * idy;
+        g.f[3][k] -= dtb * dEz_dy;
+        g.f[4][k] += dtb * dEz_dx;
+        g.f[5][k] -= dtb * (dEy_dx - dEx_dy);
+    }
+}
+
+__global__ void __launch_bounds__(kPicBlock) k_yee_e(YeeGrid g, const float *jx, const float *jy,
+                                                     const float *jz, float dt)
+{
+    const int64_t n = g.nx * g.ny;
+    const float idx = 1.0f / g.dx, idy = 1.0f / g.dy;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const int64_t j = k / g.nx, i = k - j * g.nx;
+        const float bz = g.f[5][k];
+        const float dBz_dy = (bz - at(g.f[5], g.nx, g.ny, i, j - 1)) * idy;
+        const float dBz_dx = (bz - at(g.f[5], g.nx, g.ny, i - 1, j)) * idx;
+        const float dBy_dx = (g.f[4][k] - at(g.f[4], g.nx, g.ny, i - 1, j)) * idx;
+        const float dBx_dy = (g.f[3][k] - at(g.f[3], g.nx, g.ny, i, j - 1)) * idy;
+        g.f[0][k] += dt * (dBz_dy - (jx ? jx[k] : 0.0f));
+        g.f[1][k] += dt * (-dBz_dx - (jy ? jy[k] : 0.0f));
+        g.f[2][k] += dt * (dBy_dx - dBx_dy - (jz ? jz[k] : 0.0f));
+    }
+}
+
+// One thread a particle: q w v / (dx dy) spread with the linear weights of
+// each component's staggering at the mid-step position x - v dt/2 (after a
+// step: x^(n+1) and v^(n+1/2)).  FP32 atomic sums (their order varies).
+__global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, float q, double dt, YeeGrid g,
+                                                       float *jx, float *jy, float *jz,
+                                                       int *status)
+{
+    long long n = *((volatile long long *)S.n_live);
+    if (n < 0 || n > S.cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, QP_ERR_INVALID_ARG);
+        n = n < 0 ? 0 : S.cap;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float *J[3] = {jx, jy, jz};
+    const float ox[3] = {0.5f, 0.0f, 0.0f}, oy[3] = {0.0f, 0.5f, 0.0f};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const float ux = (float)S.ux[p], uy = (float)S.uy[p], uz = (float)S.uz[p];
+        const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+        const float v[3] = {ux * ig, uy * ig, uz * ig};
+        // mid-step position in cells (the subtraction in FP64: positions are large)
+        const float gx0 = (float)((S.x[p] - 0.5 * dt * (double)v[0] - g.x0) / g.dx);
+        const float gy0 = (float)((S.y[p] - 0.5 * dt * (double)v[1] - g.y0) / g.dy);
+        const float a = q * (float)S.w[p] / (float)(g.dx * g.dy);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float gx = gx0 - ox[c], gy = gy0 - oy[c];
+            const float fi = floorf(gx), fj = floorf(gy);
+            const float fx = gx - fi, fy = gy - fj;
+            if (!(fi >= -1.0f && fj >= -1.0f && fi < (float)g.nx && fj < (float)g.ny)) continue;
+            const int64_t i = (int64_t)fi, j = (int64_t)fj;
+            const float av = a * v[c];
+            if (av == 0.0f) continue;
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int64_t ii = i + e, jj = j + b;
+                    if (ii < 0 || jj < 0 || ii >= g.nx || jj >= g.ny) continue;
+                    const float wgt = (e ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy);
+                    atomicAdd(&J[c][jj * g.nx + ii], av * wgt);
+                }
+        }
+    }
+}
+
+int grid_blocks(int64_t n, int num_sms)
+{
+    int64_t b = (n + kPicBlock - 1) / kPicBlock;
+    const int64_t cap = (int64_t)num_sms * 8;
+    if (b > cap) b = cap;
+    return (int)(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_yee_b(const YeeGrid &g, double dtb, int num_sms, cudaStream_t st)
+{
+    k_yee_b<<<grid_blocks(g.nx * g.ny, num_sms), kPicBlock, 0, st>>>(g, (float)dtb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_e(const YeeGrid &g, const float *jx, const float *jy, const float *jz,
+                         double dt, int num_sms, cudaStream_t st)
+{
+    k_yee_e<<<grid_blocks(g.nx * g.ny, num_sms), kPicBlock, 0, st>>>(g, jx, jy, jz, (float)dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(const SpeciesDev &S, double q, double dt, const YeeGrid &g, float *jx,
+                           float *jy, float *jz, int *status, int num_sms, cudaStream_t st)
+{
+    k_deposit<<<grid_blocks(S.cap, num_sms), kPicBlock, 0, st>>>(S, (float)q, dt, g, jx, jy, jz,
+                                                                 status);
+    return cudaGetLastError();
+}
+
+}  // namespace qp

@@ -126,7 +126,8 @@ EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
            "qp_batch_create", "qp_batch_destroy", "qp_batch_scratch_words", "qp_batch_set",
            "qp_batch_clear", "qp_batch_step", "qp_batch_progress", "qp_coalesce_photons",
-           "qp_compact_photons", "qp_fill_yee2d", "qp_step_fused")
+           "qp_compact_photons", "qp_fill_yee2d", "qp_step_fused", "qp_yee_advance_b",
+           "qp_yee_advance_e", "qp_deposit_current", "qp_sort_species")
 
 
 def library_path() -> str:
@@ -173,6 +174,11 @@ def lib(build_if_missing: bool = False):
                                           C.POINTER(qp_coalesce_stats), vp]
         L.qp_compact_photons.argtypes = [vp, i32, C.POINTER(qp_coalesce_stats), vp]
         L.qp_step_fused.argtypes = [vp, C.POINTER(qp_step_params), i32, vp]
+        L.qp_yee_advance_b.argtypes = [vp, C.POINTER(qp_field), C.c_double, vp]
+        L.qp_yee_advance_e.argtypes = [vp, C.POINTER(qp_field), vp, vp, vp, C.c_double, vp]
+        L.qp_deposit_current.argtypes = [vp, i32, C.POINTER(qp_field), vp, vp, vp, C.c_double,
+                                         vp]
+        L.qp_sort_species.argtypes = [vp, i32, C.POINTER(qp_field), vp]
         L.qp_fill_yee2d.argtypes = [vp, C.POINTER(qp_pulse2d), C.POINTER(qp_field), C.c_double,
                                     vp]
         L.qp_status_string.restype = C.c_char_p
@@ -374,3 +380,25 @@ def qp_step_fused(ctx, params: qp_step_params, fuse: int, stream=None) -> int:
     """params.n_steps steps, `fuse` per launch window (pairs off; the same
     results as qp_step)."""
     return _check("qp_step_fused", lib().qp_step_fused(ctx, C.byref(params), int(fuse), stream))
+
+
+def qp_yee_advance_b(ctx, grid: qp_field, dtb: float, stream=None) -> int:
+    return _check("qp_yee_advance_b", lib().qp_yee_advance_b(ctx, C.byref(grid), float(dtb),
+                                                             stream))
+
+
+def qp_yee_advance_e(ctx, grid: qp_field, jx_ptr, jy_ptr, jz_ptr, dt: float, stream=None) -> int:
+    """j*_ptr: device addresses (int) of the current arrays, or None."""
+    return _check("qp_yee_advance_e", lib().qp_yee_advance_e(ctx, C.byref(grid), jx_ptr, jy_ptr,
+                                                             jz_ptr, float(dt), stream))
+
+
+def qp_deposit_current(ctx, handle: int, grid: qp_field, jx_ptr, jy_ptr, jz_ptr, dt: float,
+                       stream=None) -> int:
+    return _check("qp_deposit_current",
+                  lib().qp_deposit_current(ctx, handle, C.byref(grid), jx_ptr, jy_ptr, jz_ptr,
+                                           float(dt), stream))
+
+
+def qp_sort_species(ctx, handle: int, grid: qp_field, stream=None) -> int:
+    return _check("qp_sort_species", lib().qp_sort_species(ctx, handle, C.byref(grid), stream))

@@ -149,6 +149,13 @@ class Simulation:
         rf = workload["field"].get("refill")
         self.pulse = (Q.pulse2d(rf["a0"], rf["w0"], rf["tau_fwhm"], rf["x_focus"],
                                 rf["t_focus"], rf["y_axis"]) if rf else None)
+        pc = workload["field"].get("pic")
+        self.pic_pulse = (Q.pulse2d(pc["a0"], pc["w0"], pc["tau_fwhm"], pc["x_focus"],
+                                    pc["t_focus"], pc["y_axis"]) if pc else None)
+        self.J = None
+        if pc:
+            ny, nx = workload["field"]["comps"][0].shape
+            self.J = torch.zeros((3, ny, nx), dtype=torch.float32, device=self.dev)
         p = workload["params"]
         s = Q.qp_step_params()
         s.field = self.field
@@ -168,6 +175,13 @@ class Simulation:
             self.load_initial(init_tau)
 
     def load_initial(self, init_tau: bool = True, stream=None):
+        if self.pic_pulse is not None:
+            # the grid starts with the pulse at the first step's time (E and
+            # B at that time); the solver advances it from there
+            for c in self._keep:
+                c.zero_()
+            t0 = int(self.workload["params"].get("step", 0)) * self.workload["params"]["dt"]
+            Q.qp_fill_yee2d(self.ctx, self.pic_pulse, self.field, t0, stream_handle(stream))
         el = self.species["electron"]
         el.load(self.workload["electrons"])
         for sp in ("positron", "photon"):
@@ -189,7 +203,32 @@ class Simulation:
         self.step_index += int(n_steps)
         return st
 
+    def _pic_step(self, sh) -> int:
+        """One PIC cycle: B half step, the QED step, the current, B half
+        step, E full step (E^n and B^(n-1/2) stored between cycles)."""
+        dt = self.params.dt
+        Q.qp_yee_advance_b(self.ctx, self.field, 0.5 * dt, sh)
+        self.params.step = self.step_index
+        self.params.n_steps = 1
+        st = Q.qp_step(self.ctx, self.params, sh)
+        self.J.zero_()
+        j = [self.J[k].data_ptr() for k in range(3)]
+        for name in ("electron", "positron"):
+            sp = self.species[name]
+            if sp.cap > 0:
+                Q.qp_deposit_current(self.ctx, sp.handle, self.field, j[0], j[1], j[2], dt, sh)
+        Q.qp_yee_advance_b(self.ctx, self.field, 0.5 * dt, sh)
+        Q.qp_yee_advance_e(self.ctx, self.field, j[0], j[1], j[2], dt, sh)
+        self.step_index += 1
+        return st
+
     def run(self, n_steps: int, stream=None) -> int:
+        if self.pic_pulse is not None:
+            sh = stream_handle(stream)
+            st = 0
+            for _ in range(int(n_steps)):
+                st = max(st, self._pic_step(sh))
+            return st
         if self.pulse is not None:
             # fields refilled from the pulse at each step's time, then the step
             st = 0

@@ -99,14 +99,18 @@ def gaussian_2d_snapshot(nx: int, ny: int, dx: float, dy: float, a0: float, w0: 
 def laser_on_foil(nx: int = 2048, ny: int = 512, ppc: int = 8, a0: float = 200.0,
                   n_steps: int = 500, seed: int = 0, foil_cells: int = 32,
                   photon_capacity: int = 1 << 25, pair_capacity: int = 1 << 20,
-                  refill: bool = False):
+                  refill: bool = False, pic: bool = False):
     """2048x512 grid, dx = lambda/32, a 1-lambda foil of electrons at
     n = 100 n_c, 8 per cell, Maxwellian 1 keV, in the fixed fields of a
     Gaussian pulse (a0 200, waist 3 lambda, 30 fs FWHM) whose peak sits at the
     foil front.  Sokolov damping below chi 1e-3, Monte-Carlo above.
     refill: the grid's E_y and B_z are refilled from the pulse before every
     step instead (qp_fill_yee2d); the pulse's peak reaches the foil front at
-    mid-run; the grid starts empty."""
+    mid-run; the grid starts empty.
+    pic: the fields are the grid's own, advanced by the Yee solver with the
+    electrons' current (qp_yee_advance_*, qp_deposit_current): the grid
+    starts with the pulse of `refill` at the first step's time and the pulse
+    then propagates, diffracts and meets the foil on the grid."""
     rng = np.random.default_rng(seed)
     dx = dy = T_PERIOD / 32.0
     i0 = nx // 2
@@ -123,16 +127,18 @@ def laser_on_foil(nx: int = 2048, ny: int = 512, ppc: int = 8, a0: float = 200.0
     w0, tau = length(3 * LAMBDA_M), duration(30e-15)
     dt = 0.95 * dx / math.sqrt(2.0)
     field = {"kind": "yee2d", "dx": dx, "dy": dy, "x0": 0.0, "y0": 0.0}
-    if refill:
+    if refill or pic:
         field["comps"] = [np.zeros((ny, nx), dtype=np.float32) for _ in range(6)]
-        field["refill"] = {"a0": a0, "w0": w0, "tau_fwhm": tau, "x_focus": i0 * dx,
-                           "t_focus": (n_steps // 2) * dt, "y_axis": 0.5 * ny * dy}
+        field["refill" if refill else "pic"] = {
+            "a0": a0, "w0": w0, "tau_fwhm": tau, "x_focus": i0 * dx,
+            "t_focus": (n_steps // 2) * dt, "y_axis": 0.5 * ny * dy}
     else:
         field["comps"] = gaussian_2d_snapshot(nx, ny, dx, dy, a0=a0, w0=w0, tau_fwhm=tau,
                                               x_focus=i0 * dx, y_axis=0.5 * ny * dy)
     return {
         "name": (f"2D laser-on-foil: {nx}x{ny} Yee grid, {n} e-, a0 {a0:g}, {n_steps} steps"
-                 + (", fields refilled from the pulse every step" if refill else "")),
+                 + (", fields refilled from the pulse every step" if refill else "")
+                 + (", PIC fields (Yee solver and current deposition)" if pic else "")),
         "dims": 2,
         "electrons": el,
         "field": field,

@@ -36,10 +36,40 @@ def oracle_pulse(desc):
                      rf["y_axis"])
 
 
+def oracle_pic_start(sim, workload):
+    """The oracle's grid of a PIC workload at its first step: the pulse at
+    that time (E and B), the other components zero."""
+    pc = workload["field"]["pic"]
+    p = O.pulse2d(pc["a0"], pc["w0"], pc["tau_fwhm"], pc["x_focus"], pc["t_focus"], pc["y_axis"])
+    for c in sim.field._keep:
+        c[:] = 0.0
+    O.fill_pulse2d(p, sim.field, sim.P.step * sim.P.dt)
+
+
+def oracle_pic_steps(sim, n_steps):
+    """PIC cycles of the oracle: B half step, the QED step, the leptons'
+    current (FP64, rounded to the grid's float), B half step, E full step."""
+    f = sim.field
+    comps = f._keep
+    dt = sim.P.dt
+    for _ in range(n_steps):
+        O.yee_advance_b(comps, f.dx, f.dy, 0.5 * dt)
+        sim.run(1)
+        J = [np.zeros(comps[0].shape) for _ in range(3)]
+        for q, sp in ((-1.0, sim.sp[0]), (1.0, sim.sp[1])):
+            if sp is not None and sp.n:
+                O.deposit_current(sp, q, dt, J, f.dx, f.dy, f.x0, f.y0)
+        O.yee_advance_b(comps, f.dx, f.dy, 0.5 * dt)
+        O.yee_advance_e(comps, [j.astype(np.float32) for j in J], f.dx, f.dy, dt)
+
+
 def oracle_steps(sim, workload, n_steps):
     """n_steps of an oracle run; a workload with a refilled grid gets the
     oracle's own refill (from the pulse, FP64 rounded to float) before each
-    step."""
+    step, a PIC workload the oracle's own solver and deposition."""
+    if workload["field"].get("pic"):
+        oracle_pic_steps(sim, n_steps)
+        return
     pulse = oracle_pulse(workload["field"])
     if pulse is None:
         sim.run(n_steps)
@@ -100,6 +130,8 @@ def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, 
         params["noise_key"] = noise_key
     sim = O.Sim(oracle_field(workload["field"]), params, electrons=el, positrons=po,
                 photons=ph)
+    if workload["field"].get("pic"):
+        oracle_pic_start(sim, workload)
     oracle_steps(sim, workload, n_steps)
     return sim, {"electron": el, "positron": po, "photon": ph}
 

@@ -1,0 +1,145 @@
+"""PIC coupling on the GPU (qp_yee_advance_b/e, qp_deposit_current,
+qp_sort_species) against the oracle's solver, deposition and sort, and the
+2D foil run as a PIC cycle (its fields advanced with the electrons' current)
+against the oracle running the same cycle (GPU only).
+
+Bars: the solver and the deposition run in FP32 on the device (float
+atomics for the current) and in FP64 rounded to float in the oracle, so
+fields and currents are compared within 2e-5 of their largest value; the
+sort is exact (its keys are exact FP64 operations on both sides); the PIC
+foil, whose fields differ at FP32 level between the two sides, is held to
+the FP32 (mixed-path) bar on both paths."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1311_1107_gb300 import qedpic as Q
+from paper_1311_1107_gb300 import workloads as W
+from paper_1311_1107_gb300.sim import DeviceSpecies, Simulation, make_field
+from tests.parity import (chaos_aware_compare, distribution_check, head, oracle_arrays,
+                          run_oracle)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Q.qp_init_tables(W.LAMBDA_M, 0)
+    yield c
+    torch.cuda.synchronize()
+    Q.qp_destroy(c)
+
+
+def _grid(nx, ny, dx, dy, seed):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) - nx / 2)[None, :] * dx
+    y = (np.arange(ny) - ny / 2)[:, None] * dy
+    env = np.exp(-(x ** 2 + y ** 2) / (0.1 * (nx * dx) ** 2))
+    comps = [(env * np.cos(rng.uniform(0.5, 2.0) * x + rng.uniform(0.5, 2.0) * y)
+              * rng.uniform(-3, 3)).astype(np.float32) for _ in range(6)]
+    return {"kind": "yee2d", "comps": comps, "dx": dx, "dy": dy, "x0": 0.0, "y0": 0.0}
+
+
+def test_yee_solver_matches_the_oracle(ctx):
+    nx, ny, dx, dy = 300, 200, 0.2, 0.25
+    dt = 0.5 * min(dx, dy)
+    desc = _grid(nx, ny, dx, dy, 1)
+    f, keep = make_field(desc)
+    of = [c.copy() for c in desc["comps"]]
+    rng = np.random.default_rng(2)
+    J = [(rng.uniform(-1, 1, (ny, nx))).astype(np.float32) for _ in range(3)]
+    Jd = [torch.as_tensor(j).cuda() for j in J]
+    for step in range(10):
+        Q.qp_yee_advance_b(ctx, f, 0.5 * dt)
+        O.yee_advance_b(of, dx, dy, 0.5 * dt)
+        use = step % 2 == 0
+        Q.qp_yee_advance_e(ctx, f, *([j.data_ptr() for j in Jd] if use else [None] * 3), dt)
+        O.yee_advance_e(of, J if use else None, dx, dy, dt)
+    torch.cuda.synchronize()
+    scale = max(np.abs(c).max() for c in of)
+    worst = max(np.abs(keep[k].cpu().numpy() - of[k]).max() for k in range(6)) / scale
+    print(f"\n[yee solver] largest difference {worst:.3g} of the largest field")
+    assert worst <= 2e-5
+
+
+def test_current_deposition_matches_the_oracle(ctx):
+    nx, ny, dx, dy, dt = 160, 96, 0.3, 0.25, 0.1
+    rng = np.random.default_rng(3)
+    n = 50_000
+    arr = {"x": rng.uniform(-1, nx * dx + 1, n), "y": rng.uniform(-1, ny * dy + 1, n),
+           "ux": rng.normal(0, 2, n), "uy": rng.normal(0, 2, n), "uz": rng.normal(0, 2, n),
+           "w": rng.uniform(0.5, 1.5, n)}
+    f, keep = make_field(_grid(nx, ny, dx, dy, 4))
+    for kind, q in ((Q.QP_ELECTRON, -1.0), (Q.QP_POSITRON, 1.0)):
+        sp = DeviceSpecies(ctx, kind, n, 2)
+        sp.load(arr)
+        Jg = torch.zeros((3, ny, nx), dtype=torch.float32, device="cuda")
+        Q.qp_deposit_current(ctx, sp.handle, f, *(Jg[k].data_ptr() for k in range(3)), dt)
+        torch.cuda.synchronize()
+        osp = O.Species.from_arrays(arr, n, 2)
+        Jo = [np.zeros((ny, nx)) for _ in range(3)]
+        O.deposit_current(osp, q, dt, Jo, dx, dy)
+        for c in range(3):
+            g = Jg[c].cpu().numpy().astype(np.float64)
+            err = np.abs(g - Jo[c]).max() / np.abs(Jo[c]).max()
+            assert err <= 2e-5, (kind, c, err)
+            assert g.sum() == pytest.approx(Jo[c].sum(), rel=1e-4)
+        Q.qp_destroy_species(ctx, sp.handle)
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 300_001])
+def test_sort_by_cell_matches_the_oracle(ctx, n):
+    nx, ny, dx, dy = 64, 48, 0.5, 0.5
+    rng = np.random.default_rng(5 + n)
+    arr = {"x": rng.uniform(-2, nx * dx + 2, n), "y": rng.uniform(-2, ny * dy + 2, n),
+           "z": rng.normal(size=n), "ux": rng.normal(size=n), "uy": rng.normal(size=n),
+           "uz": rng.normal(size=n), "w": rng.uniform(size=n), "tau": rng.normal(size=n)}
+    f, keep = make_field(_grid(nx, ny, dx, dy, 6))
+    sp = DeviceSpecies(ctx, Q.QP_ELECTRON, n + 7, 3)
+    sp.load(arr)
+    if n:
+        sp.nemit[:n].copy_(torch.arange(n, dtype=torch.int32))
+    Q.qp_sort_species(ctx, sp.handle, f)
+    torch.cuda.synchronize()
+    o = O.Species.from_arrays(arr, n + 7, 3)
+    o.tau[:n] = arr["tau"]
+    o.nemit[:n] = np.arange(n)
+    O.sort_by_cell(o, nx, ny, dx, dy)
+    g = sp.host()
+    assert sp.count() == n
+    for k in ("x", "y", "z", "ux", "uy", "uz", "tau", "w", "nemit"):
+        np.testing.assert_array_equal(g[k], getattr(o, k)[:n], err_msg=k)
+    Q.qp_destroy_species(ctx, sp.handle)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pic_foil_matches_the_oracle(ctx, precision):
+    n_steps = 120
+    w = W.laser_on_foil(nx=256, ny=128, ppc=8, foil_cells=4, n_steps=2 * n_steps,
+                        photon_capacity=1 << 18, pair_capacity=1 << 12, pic=True)
+    sim = Simulation(w, precision=precision, ctx=ctx)
+    sim.run(n_steps)
+    torch.cuda.synchronize()
+    g = sim.species["electron"].host()
+    n = len(w["electrons"]["x"])
+    osim, osp = run_oracle(w, n_steps)
+    o = head(oracle_arrays(osp["electron"]), n)
+    twins = [head(oracle_arrays(run_oracle(w, n_steps, noise=2e-7, noise_key=k)[1]["electron"]),
+                  n) for k in (0, 1)]
+    rep = chaos_aware_compare(head(g, n), o, twins, 1e-4, f"PIC foil {precision}",
+                              margin=osp["electron"].margin[:n],
+                              margin_min=1e-4 if precision == "mixed" else 1e-10,
+                              min_comparable=0.05)
+    distribution_check(head(g, n), o, f"PIC foil {precision}")
+    # the fields: the pulse on the grid, within FP32-level differences
+    ey_g = sim._keep[1].cpu().numpy()
+    ey_o = osim.field._keep[1]
+    err = np.abs(ey_g - ey_o).max() / np.abs(ey_o).max()
+    print(f"[PIC foil {precision}] E_y largest difference {err:.3g} of the largest")
+    assert err <= 1e-3 and np.abs(ey_o).max() > 50.0
+    assert np.abs(o["uy"]).max() > 5.0 and rep["comparable"] > 0
+    sim.close()
