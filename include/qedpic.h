@@ -476,7 +476,9 @@ typedef struct {
     int32_t energy_bins_per_octave; /* E: a power of two, 1..64                  */
     int32_t direction_bins; /* D: a power of two, 1..64                          */
     int32_t min_group;      /* groups of at least this many photons merge (>= 3) */
-    int32_t reserved;       /* 0                                                 */
+    int32_t max_group;      /* a larger group merges in runs of max_group photons
+                               (slot order; a last run below min_group is kept);
+                               0: 256; else >= min_group                         */
     uint64_t seed;          /* key of the merged photons' optical-depth draws    */
     int64_t step;           /* step counter of those draws                       */
 } qp_coalesce_params;
@@ -500,7 +502,9 @@ typedef struct {
  * axis least aligned with P); both sit at the group's weighted mean
  * position and draw fresh optical depths -log(xi) from the Philox stream
  * (seed; photon species, purpose 5, the first photon's particle id, step,
- * k = 0, 1).  A group whose momentum vanishes is kept as it is.  W, E and P
+ * k = 0, 1).  A group of more than max_group photons merges in runs of
+ * max_group (its members in slot order), each run as a group of its own;
+ * a run whose momentum vanishes is kept as it is.  W, E and P
  * of every group are conserved to rounding and both photons are massless.
  * Decayed photons (tau < 0) are removed.  The survivors keep their slot
  * order, a merged pair taking its group's first slot; their chi and nemit

@@ -82,7 +82,8 @@ class CoalesceParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("x0", "y0", "z0", "dx", "dy", "dz")] + [
         ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
         ("ebins_per_octave", C.c_int32), ("dir_bins", C.c_int32), ("min_group", C.c_int32),
-        ("dims", C.c_int32), ("seed", C.c_uint64), ("step", C.c_int64)]
+        ("dims", C.c_int32), ("max_group", C.c_int32), ("pad", C.c_int32),
+        ("seed", C.c_uint64), ("step", C.c_int64)]
 
 
 class CoalesceStats(C.Structure):
@@ -444,13 +445,14 @@ class Sim:
 
 
 def coalesce_params(box, cells, ebins_per_octave=8, dir_bins=8, min_group=3, dims=3, seed=0,
-                    step=0) -> CoalesceParams:
-    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz)."""
+                    step=0, max_group=0) -> CoalesceParams:
+    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz); max_group 0: 256."""
     c = CoalesceParams()
     c.x0, c.y0, c.z0, c.dx, c.dy, c.dz = (float(v) for v in box)
     c.nx, c.ny, c.nz = (int(v) for v in cells)
     c.ebins_per_octave, c.dir_bins, c.min_group = ebins_per_octave, dir_bins, min_group
     c.dims, c.seed, c.step = dims, seed, step
+    c.max_group = max_group
     return c
 
 

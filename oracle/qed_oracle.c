@@ -1086,7 +1086,10 @@ int or_run(const or_units *U, const or_tables *T, const or_field *F, const or_pa
  * remaining optical depth of a photon is memoryless).  Decayed photons
  * (tau < 0) are removed; what remains keeps its slot order, a merged pair
  * taking the place of its group's first photon.  Slots are renumbered, so a
- * photon's later draws follow its new slot. */
+ * photon's later draws follow its new slot.  A group of more than max_group
+ * photons is merged in runs of max_group (its members in slot order, the
+ * last run the rest; a run of fewer than min_group is kept as it is), which
+ * bounds the work of one merge. */
 
 typedef struct {
     double x0, y0, z0, dx, dy, dz;
@@ -1095,6 +1098,8 @@ typedef struct {
     int32_t dir_bins;         /* power of two, 1 .. 64, per face axis        */
     int32_t min_group;        /* >= 3                                        */
     int32_t dims;
+    int32_t max_group;        /* >= min_group; 0: 256                        */
+    int32_t pad;
     uint64_t seed;
     int64_t step;
 } or_coalesce_params;
@@ -1236,7 +1241,8 @@ int or_coalesce(or_species *Ph, const or_coalesce_params *C, or_coalesce_stats *
     memset(st, 0, sizeof(*st));
     st->n_before = n;
     int merge = C && C->min_group > 0;
-    if (merge && (C->min_group < 3 || C->ebins_per_octave < 1 || C->ebins_per_octave > 64 ||
+    if (merge && (C->min_group < 3 || (C->max_group != 0 && C->max_group < C->min_group) ||
+                  C->ebins_per_octave < 1 || C->ebins_per_octave > 64 ||
                   C->dir_bins < 1 || C->dir_bins > 64 || !(C->dx > 0.0) || !(C->dy > 0.0) ||
                   (C->dims == 3 && !(C->dz > 0.0)) || C->nx < 1 || C->ny < 1 || C->nz < 1))
         return -1;
@@ -1271,35 +1277,39 @@ int or_coalesce(or_species *Ph, const or_coalesce_params *C, or_coalesce_stats *
     double (*pairs)[2][8] = NULL;
     int64_t n_pairs = 0;
     int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk > 0 ? nk : 1));
-    for (int64_t a = 0; a < nk;) {
-        int64_t b = a;
-        while (b < nk && ks[b].key == ks[a].key) b++;
-        if (b - a >= C->min_group) {
-            for (int64_t k = a; k < b; k++) members[k - a] = ks[k].slot;
-            double c2 = 0.0;
-            {
-                double P[3] = {0.0, 0.0, 0.0};
-                for (int64_t k = a; k < b; k++) {
-                    int64_t i = ks[k].slot;
-                    P[0] = P[0] + Ph->w[i] * Ph->ux[i];
-                    P[1] = P[1] + Ph->w[i] * Ph->uy[i];
-                    P[2] = P[2] + Ph->w[i] * Ph->uz[i];
+    const int64_t M = merge ? (C->max_group > 0 ? C->max_group : 256) : 1;
+    for (int64_t g0 = 0; g0 < nk;) {
+        int64_t g1 = g0;
+        while (g1 < nk && ks[g1].key == ks[g0].key) g1++;
+        for (int64_t a = g0; a < g1; a += M) {
+            const int64_t b = a + M < g1 ? a + M : g1;
+            if (b - a >= C->min_group) {
+                for (int64_t k = a; k < b; k++) members[k - a] = ks[k].slot;
+                double c2 = 0.0;
+                {
+                    double P[3] = {0.0, 0.0, 0.0};
+                    for (int64_t k = a; k < b; k++) {
+                        int64_t i = ks[k].slot;
+                        P[0] = P[0] + Ph->w[i] * Ph->ux[i];
+                        P[1] = P[1] + Ph->w[i] * Ph->uy[i];
+                        P[2] = P[2] + Ph->w[i] * Ph->uz[i];
+                    }
+                    c2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
                 }
-                c2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
-            }
-            if (c2 > 0.0) {
-                pairs = realloc(pairs, sizeof(*pairs) * (size_t)(n_pairs + 1));
-                int64_t anchor = members[0];
-                or_merge_group(Ph, members, b - a, C, or_id(Ph, anchor), pairs[n_pairs]);
-                grp[anchor] = n_pairs;
-                for (int64_t k = a; k < b; k++) role[ks[k].slot] = 0;
-                role[anchor] = 2;
-                n_pairs++;
-                st->groups_merged++;
-                st->photons_merged += b - a;
+                if (c2 > 0.0) {
+                    pairs = realloc(pairs, sizeof(*pairs) * (size_t)(n_pairs + 1));
+                    int64_t anchor = members[0];
+                    or_merge_group(Ph, members, b - a, C, or_id(Ph, anchor), pairs[n_pairs]);
+                    grp[anchor] = n_pairs;
+                    for (int64_t k = a; k < b; k++) role[ks[k].slot] = 0;
+                    role[anchor] = 2;
+                    n_pairs++;
+                    st->groups_merged++;
+                    st->photons_merged += b - a;
+                }
             }
         }
-        a = b;
+        g0 = g1;
     }
     /* the survivors in slot order, into fresh arrays, then back */
     int64_t out = 0;

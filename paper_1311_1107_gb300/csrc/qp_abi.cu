@@ -1111,7 +1111,8 @@ int qp_coalesce_photons(qp_ctx *ctx, int32_t handle, const qp_coalesce_params *P
     const qp_species_desc &d = ctx->species[handle].d;
     if (d.kind != QP_PHOTON || d.capacity >= (int64_t)0xFFFFFFFFll) return QP_ERR_INVALID_ARG;
     if (P) {
-        if (P->min_group < 3 || !pow2_in(P->energy_bins_per_octave, 1, 64) ||
+        if (P->min_group < 3 || (P->max_group != 0 && P->max_group < P->min_group) ||
+            !pow2_in(P->energy_bins_per_octave, 1, 64) ||
             !pow2_in(P->direction_bins, 1, 64) || !(P->dx > 0.0) || !(P->dy > 0.0) ||
             (d.dims == 3 && !(P->dz > 0.0)) || P->nx < 1 || P->ny < 1 || P->nz < 1 ||
             (d.dims == 2 && P->nz != 1) || !isfinite(P->x0) || !isfinite(P->y0) ||

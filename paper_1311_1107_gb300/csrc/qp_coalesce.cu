@@ -19,14 +19,17 @@
 //   k_co_prepare   roles (1 alive, 0 decayed) and group keys;
 //   radix passes   stable LSD sort of (key, slot), 8 bits a pass:
 //                  k_co_hist, k_co_scan_hist, k_co_scatter;
-//   k_co_groups    runs of one key: groups of >= min_group members become
-//                  pairs (role 2 at the first member, 0 at the others);
+//   k_co_groups    groups (runs of one key) cut into runs of at most
+//                  max_group members in slot order; runs of >= min_group
+//                  listed;
+//   k_co_runs      one thread a run: its momentum checked, roles set (2 at
+//                  the first member, 0 at the others);
 //   role scan      k_co_chunk_sums, k_co_scan_chunks, k_co_offsets: the
 //                  output slot of every survivor in slot order;
 //   k_co_kept      survivors copied to the staging arrays;
 //   k_co_pairs     merged pairs computed and written to the staging arrays;
 //   k_co_copy_back staging -> species, new live count.
-// Group sums run in slot order in one thread per group, with the oracle's
+// Group sums run in slot order in one thread per run, with the oracle's
 // operations in the oracle's order; this unit is compiled without FMA
 // contraction, so keys, sums and merged momenta are the oracle's bit for
 // bit (the fresh optical depths -log(xi) differ by the last bit at most).
@@ -50,6 +53,7 @@ struct CoParams {
     int lb;            // log2 of energy bins per octave
     int D;             // direction bins per face axis
     int min_group;
+    int max_group;     // longest run of one group merged into one pair
     int dims;
     unsigned long long seed;
     long long step;
@@ -272,31 +276,50 @@ __device__ __forceinline__ bool group_start(const unsigned long long *keys, long
     return true;
 }
 
-__global__ void __launch_bounds__(kCoThreads) k_co_groups(SpeciesDev S, CoParams C,
+// Runs of the sorted keys: every group (one key) is cut into runs of at
+// most max_group members in slot order; the runs of at least min_group go to
+// the run list (one thread a group: it only walks the group's keys).
+__global__ void __launch_bounds__(kCoThreads) k_co_groups(CoParams C,
                                                           const unsigned long long *keys,
-                                                          const unsigned *vals,
-                                                          unsigned char *role,
-                                                          const long long *counts,
-                                                          long long *stats)
+                                                          long long *counts, uint2 *runs)
 {
     const long long n = counts[0];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         long long end;
-        if (!group_start(keys, j, n, C.nomerge, &end) || end - j < C.min_group) continue;
-        // a group whose momentum vanishes is left as it is
+        if (!group_start(keys, j, n, C.nomerge, &end)) continue;
+        for (long long a = j; a < end; a += C.max_group) {
+            const long long b = a + C.max_group < end ? a + C.max_group : end;
+            if (b - a < C.min_group) continue;
+            const unsigned long long r = atomicAdd((unsigned long long *)&counts[2], 1ull);
+            runs[r] = make_uint2((unsigned)a, (unsigned)b);
+        }
+    }
+}
+
+// One thread a run: a run whose momentum vanishes is kept as it is, the
+// others become pairs (role 2 at the first member, 0 at the others).
+__global__ void __launch_bounds__(kCoThreads) k_co_runs(SpeciesDev S, const unsigned *vals,
+                                                        const uint2 *runs, unsigned char *role,
+                                                        const long long *counts,
+                                                        long long *stats)
+{
+    const long long nr = counts[2];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += stride) {
+        const uint2 run = runs[r];
         double P[3] = {0.0, 0.0, 0.0};
-        for (long long k = j; k < end; ++k) {
+        for (unsigned k = run.x; k < run.y; ++k) {
             const unsigned i = vals[k];
             P[0] = P[0] + S.w[i] * S.ux[i];
             P[1] = P[1] + S.w[i] * S.uy[i];
             P[2] = P[2] + S.w[i] * S.uz[i];
         }
         if (!(P[0] * P[0] + P[1] * P[1] + P[2] * P[2] > 0.0)) continue;
-        for (long long k = j; k < end; ++k) role[vals[k]] = 0;
-        role[vals[j]] = 2;  // the sorted run is in slot order: j is the first
+        for (unsigned k = run.x; k < run.y; ++k) role[vals[k]] = 0;
+        role[vals[run.x]] = 2;  // the sorted run is in slot order: its first
         atomicAdd((unsigned long long *)&stats[0], 1ull);
-        atomicAdd((unsigned long long *)&stats[1], (unsigned long long)(end - j));
+        atomicAdd((unsigned long long *)&stats[1], (unsigned long long)(run.y - run.x));
     }
 }
 
@@ -383,20 +406,18 @@ __global__ void __launch_bounds__(kCoThreads) k_co_kept(SpeciesDev S, const unsi
 }
 
 __global__ void __launch_bounds__(kCoThreads) k_co_pairs(SpeciesDev S, CoParams C,
-                                                         const unsigned long long *keys,
-                                                         const unsigned *vals,
+                                                         const unsigned *vals, const uint2 *runs,
                                                          const unsigned char *role,
                                                          const unsigned *off, Stage st,
                                                          const long long *counts)
 {
-    const long long n = counts[0];
+    const long long nr = counts[2];
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        long long end;
-        if (!group_start(keys, j, n, C.nomerge, &end)) continue;
-        const unsigned anchor = vals[j];
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nr; q += stride) {
+        const uint2 run = runs[q];
+        const unsigned anchor = vals[run.x];
         if (role[anchor] != 2) continue;
-        const GroupSums g = group_sums(S, vals, j, end);
+        const GroupSums g = group_sums(S, vals, run.x, run.y);
         const double W = g.W;
         const double eps = g.E / W;
         const double c[3] = {g.P[0] / W, g.P[1] / W, g.P[2] / W};
@@ -519,7 +540,7 @@ size_t coalesce_scratch_bytes(int64_t cap, int grid)
 {
     const size_t c = (size_t)(cap > 0 ? cap : 1);
     return 2 * c * 8 + 2 * c * 4 + c + c * 4 + c * 9 * 8 + c * 4 +
-           ((size_t)kRadix * grid + grid + 64) * 4 + 16 * 8 + 32 * 256;
+           ((size_t)kRadix * grid + grid + 64) * 4 + 16 * 8 + (c / 3 + 1) * 8 + 32 * 256;
 }
 
 cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, void *scratch,
@@ -544,6 +565,7 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
     unsigned *hist = (unsigned *)take((size_t)kRadix * grid * 4);
     unsigned *chunk = (unsigned *)take((size_t)grid * 4 + 64);
     long long *counts = (long long *)take(16 * 8);
+    uint2 *runs = (uint2 *)take((c / 3 + 1) * sizeof(uint2));
 
     CoParams C{};
     int passes = 0;
@@ -562,6 +584,7 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
         C.lb = lb;
         C.D = P->direction_bins;
         C.min_group = P->min_group;
+        C.max_group = P->max_group > 0 ? P->max_group : 256;
         C.dims = S.z ? 3 : 2;
         C.seed = P->seed;
         C.step = P->step;
@@ -588,16 +611,15 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
         cur ^= 1;
     }
     if (passes) {
-        k_co_groups<<<grid, kCoThreads, 0, st>>>(S, C, keys[cur], vals[cur], role, counts,
-                                                  stats);
+        k_co_groups<<<grid, kCoThreads, 0, st>>>(C, keys[cur], counts, runs);
+        k_co_runs<<<grid, kCoThreads, 0, st>>>(S, vals[cur], runs, role, counts, stats);
     }
     k_co_chunk_sums<<<grid, kCoThreads, 0, st>>>(role, chunk, counts);
     k_co_scan<<<1, 1024, 0, st>>>(chunk, grid, counts + 1);
     k_co_offsets<<<grid, kCoThreads, 0, st>>>(role, chunk, off, counts);
     k_co_kept<<<grid, kCoThreads, 0, st>>>(S, role, off, stg, counts);
     if (passes) {
-        k_co_pairs<<<grid, kCoThreads, 0, st>>>(S, C, keys[cur], vals[cur], role, off, stg,
-                                                 counts);
+        k_co_pairs<<<grid, kCoThreads, 0, st>>>(S, C, vals[cur], runs, role, off, stg, counts);
     }
     k_co_copy_back<<<grid, kCoThreads, 0, st>>>(S, stg, counts, stats);
     return cudaGetLastError();

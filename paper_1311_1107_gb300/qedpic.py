@@ -107,7 +107,7 @@ class qp_coalesce_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("x0", "y0", "z0", "dx", "dy", "dz")] + [
         ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
         ("energy_bins_per_octave", C.c_int32), ("direction_bins", C.c_int32),
-        ("min_group", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+        ("min_group", C.c_int32), ("max_group", C.c_int32), ("seed", C.c_uint64),
         ("step", C.c_int64)]
 
 
@@ -336,13 +336,14 @@ def qp_batch_progress(batch, steps_left_ptr: int, next_step_ptr: int | None = No
 
 
 def coalesce_params(box, cells, energy_bins_per_octave=8, direction_bins=8, min_group=3,
-                    seed=0, step=0) -> qp_coalesce_params:
-    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz)."""
+                    seed=0, step=0, max_group=0) -> qp_coalesce_params:
+    """box: (x0, y0, z0, dx, dy, dz); cells: (nx, ny, nz); max_group 0: 256."""
     p = qp_coalesce_params()
     p.x0, p.y0, p.z0, p.dx, p.dy, p.dz = (float(v) for v in box)
     p.nx, p.ny, p.nz = (int(v) for v in cells)
     p.energy_bins_per_octave, p.direction_bins = energy_bins_per_octave, direction_bins
     p.min_group, p.seed, p.step = min_group, seed, step
+    p.max_group = max_group
     return p
 
 

@@ -86,18 +86,19 @@ PARAMS = dict(box=(0.0, 0.0, 0.0, 2.0, 2.0, 2.0), cells=(4, 4, 4))
 
 
 @pytest.mark.parametrize("dims", [3, 2])
-@pytest.mark.parametrize("n,eb,db,m", [(0, 8, 8, 3), (1, 8, 8, 3), (777, 2, 2, 3),
-                                       (200_003, 4, 4, 3), (200_003, 1, 1, 50)])
-def test_coalescence_matches_the_oracle(ctx, dims, n, eb, db, m):
+@pytest.mark.parametrize("n,eb,db,m,mg", [(0, 8, 8, 3, 0), (1, 8, 8, 3, 0), (777, 2, 2, 3, 0),
+                                          (200_003, 4, 4, 3, 0), (200_003, 1, 1, 50, 0),
+                                          (200_003, 1, 1, 3, 7), (50_000, 1, 1, 3, 100_000)])
+def test_coalescence_matches_the_oracle(ctx, dims, n, eb, db, m, mg):
     arr = _random(n, n + dims, dims)
     cap = n + 5
     cells = PARAMS["cells"] if dims == 3 else (4, 4, 1)
     g = _gpu(ctx, arr, cap, dims)
     o = _oracle(arr, cap, dims)
-    p = Q.coalesce_params(PARAMS["box"], cells, eb, db, m, seed=3, step=17)
+    p = Q.coalesce_params(PARAMS["box"], cells, eb, db, m, seed=3, step=17, max_group=mg)
     st = Q.qp_coalesce_photons(ctx, g.handle, p)
     so = O.coalesce(o, O.coalesce_params(PARAMS["box"], cells, eb, db, m, dims=dims, seed=3,
-                                         step=17))
+                                         step=17, max_group=mg))
     print(f"\n[coalesce dims {dims} n {n}] gpu {st} oracle {so}")
     assert st["groups_merged"] == so["groups_merged"]
     assert st["photons_merged"] == so["photons_merged"]
@@ -129,6 +130,7 @@ def test_arguments_are_checked(ctx):
     bad = [Q.coalesce_params(PARAMS["box"], PARAMS["cells"], 3, 8, 3),   # not a power of 2
            Q.coalesce_params(PARAMS["box"], PARAMS["cells"], 8, 128, 3),
            Q.coalesce_params(PARAMS["box"], PARAMS["cells"], 8, 8, 2),
+           Q.coalesce_params(PARAMS["box"], PARAMS["cells"], 8, 8, 5, max_group=4),
            Q.coalesce_params((0, 0, 0, 0.0, 1, 1), PARAMS["cells"], 8, 8, 3)]
     for p in bad:
         with pytest.raises(Q.QPError):

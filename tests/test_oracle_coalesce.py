@@ -222,3 +222,28 @@ def test_bad_parameters_are_rejected():
                                              "min_group": 3, **kw})
         with pytest.raises(ValueError):
             O.coalesce(sp, p)
+
+
+def test_large_groups_merge_in_runs_of_max_group():
+    # one group of 1000 photons (one cell, energy bin and direction bin),
+    # max_group 256: runs of 256, 256, 256 and 232 slots in slot order, each
+    # replaced by its own conserving pair
+    arr, gid = _grouped_input([1000], 8)
+    order = np.argsort(np.arange(1000))  # slot order = input order
+    sp = _photons(arr)
+    stats = O.coalesce(sp, O.coalesce_params(BOX, CELLS, 8, 8, 3, max_group=256))
+    assert stats["groups_merged"] == 4 and stats["photons_merged"] == 1000 and sp.n == 8
+    for r, (a, b) in enumerate(((0, 256), (256, 512), (512, 768), (768, 1000))):
+        m = order[a:b]
+        w, u = arr["w"][m], np.stack([arr["ux"][m], arr["uy"][m], arr["uz"][m]], 1)
+        W, P = w.sum(), (w[:, None] * u).sum(0)
+        k = 2 * r
+        np.testing.assert_allclose(sp.w[k] * (np.array([sp.ux[k], sp.uy[k], sp.uz[k]])
+                                              + np.array([sp.ux[k + 1], sp.uy[k + 1],
+                                                          sp.uz[k + 1]])), P, rtol=1e-13)
+        assert sp.w[k] == pytest.approx(W / 2, rel=1e-15)
+    # a tail run shorter than min_group is kept as it is
+    arr2, _ = _grouped_input([258], 9)
+    sp2 = _photons(arr2)
+    st2 = O.coalesce(sp2, O.coalesce_params(BOX, CELLS, 8, 8, 3, max_group=256))
+    assert st2["groups_merged"] == 1 and sp2.n == 2 + 2
