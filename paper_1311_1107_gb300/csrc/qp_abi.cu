@@ -966,10 +966,13 @@ int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stre
     const long long tiles_e = (n[0] + 31) / 32, tiles = tiles_e + (n[1] + 31) / 32;
     const int K = fuse < s->n_steps ? fuse : s->n_steps;
     if (K > 65535) return QP_ERR_INVALID_ARG;
-    const size_t entries = (size_t)K * (size_t)(tiles > 0 ? tiles : 1);
     const int64_t cap_g = s->photon == -1 ? 0 : ctx->species[s->photon].d.capacity;
-    const size_t bytes = entries * sizeof(int) + 256 + entries * sizeof(long long) + 256 + 16 +
-                         256 + (size_t)(cap_g > 0 ? cap_g : 1) * sizeof(unsigned short);
+    // the photon order sorts 32-bit indices on keys of at most 64 bits
+    if (cap_g >= (int64_t)0xFFFFFFFFll || qp::fused_key_bits(K, tiles, nullptr) > 64)
+        return QP_ERR_INVALID_ARG;
+    const int order_grid = 2 * ctx->num_sms;
+    const size_t sort_bytes = (qp::coalesce_scratch_bytes(cap_g, order_grid) + 255) / 256 * 256;
+    const size_t bytes = sort_bytes + 256;
     if (bytes > ctx->fuse_bytes) {
         void *p = nullptr;
         e = cudaMalloc(&p, bytes);
@@ -978,10 +981,8 @@ int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stre
         ctx->d_fuse = p;
         ctx->fuse_bytes = bytes;
     }
-    int *counts = (int *)ctx->d_fuse;
-    long long *offs = (long long *)((char *)ctx->d_fuse + (entries * sizeof(int) + 255) / 256 * 256);
-    long long *win = offs + (entries + 31) / 32 * 32;
-    unsigned short *moves = (unsigned short *)(win + 32);
+    // the window counts after the sort scratch
+    long long *win = (long long *)((char *)ctx->d_fuse + sort_bytes);
     fill_globals(ctx, a);
     a.ctl = ctx->d_ctl;
     qp::Problem &P = a.single;
@@ -991,8 +992,8 @@ int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stre
         const int Kw = s->n_steps - w0 < K ? s->n_steps - w0 : K;
         set_time_host(P, s->step + w0);
         e = timed(ctx, 0, cs, [&] {
-            return qp::launch_fused(a, s->precision, s->field.kind, Kw, tiles_e, tiles, counts,
-                                    offs, win, moves, ctx->num_sms, cs);
+            return qp::launch_fused(a, s->precision, s->field.kind, Kw, tiles_e, tiles,
+                                    ctx->d_fuse, order_grid, win, ctx->num_sms, cs);
         });
         if (e != cudaSuccess) return cuda_status(e);
     }

@@ -543,29 +543,61 @@ size_t coalesce_scratch_bytes(int64_t cap, int grid)
            ((size_t)kRadix * grid + grid + 64) * 4 + 16 * 8 + (c / 3 + 1) * 8 + 32 * 256;
 }
 
-cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, void *scratch,
-                            int grid, long long *stats, int *status, cudaStream_t st)
+namespace {
+
+// The scratch of qp_coalesce_photons, qp_sort_species and the fused steps'
+// photon order, carved in one layout (every piece 256-byte aligned).
+struct CoScratch {
+    unsigned long long *keys[2];
+    unsigned *vals[2];
+    unsigned char *role;
+    unsigned *off;
+    Stage stg;
+    unsigned *hist, *chunk;
+    long long *counts;
+    uint2 *runs;
+};
+
+CoScratch carve(void *scratch, int64_t cap, int grid)
 {
-    const size_t c = (size_t)(S.cap > 0 ? S.cap : 1);
-    // carve the scratch (every piece 256-byte aligned)
+    const size_t c = (size_t)(cap > 0 ? cap : 1);
     unsigned char *p = (unsigned char *)scratch;
     auto take = [&](size_t bytes) {
         unsigned char *q = p;
         p += (bytes + 255) / 256 * 256;
         return q;
     };
-    unsigned long long *keys[2] = {(unsigned long long *)take(c * 8),
-                                   (unsigned long long *)take(c * 8)};
-    unsigned *vals[2] = {(unsigned *)take(c * 4), (unsigned *)take(c * 4)};
-    unsigned char *role = take(c);
-    unsigned *off = (unsigned *)take(c * 4);
-    Stage stg;
-    for (int f = 0; f < 9; ++f) stg.f[f] = (double *)take(c * 8);
-    stg.nemit = (int *)take(c * 4);
-    unsigned *hist = (unsigned *)take((size_t)kRadix * grid * 4);
-    unsigned *chunk = (unsigned *)take((size_t)grid * 4 + 64);
-    long long *counts = (long long *)take(16 * 8);
-    uint2 *runs = (uint2 *)take((c / 3 + 1) * sizeof(uint2));
+    CoScratch s;
+    s.keys[0] = (unsigned long long *)take(c * 8);
+    s.keys[1] = (unsigned long long *)take(c * 8);
+    s.vals[0] = (unsigned *)take(c * 4);
+    s.vals[1] = (unsigned *)take(c * 4);
+    s.role = take(c);
+    s.off = (unsigned *)take(c * 4);
+    for (int f = 0; f < 9; ++f) s.stg.f[f] = (double *)take(c * 8);
+    s.stg.nemit = (int *)take(c * 4);
+    s.hist = (unsigned *)take((size_t)kRadix * grid * 4);
+    s.chunk = (unsigned *)take((size_t)grid * 4 + 64);
+    s.counts = (long long *)take(16 * 8);
+    s.runs = (uint2 *)take((c / 3 + 1) * sizeof(uint2));
+    return s;
+}
+
+}  // namespace
+
+cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, void *scratch,
+                            int grid, long long *stats, int *status, cudaStream_t st)
+{
+    const CoScratch cs = carve(scratch, S.cap, grid);
+    unsigned long long *const *keys = cs.keys;
+    unsigned *const *vals = cs.vals;
+    unsigned char *role = cs.role;
+    unsigned *off = cs.off;
+    const Stage stg = cs.stg;
+    unsigned *hist = cs.hist;
+    unsigned *chunk = cs.chunk;
+    long long *counts = cs.counts;
+    uint2 *runs = cs.runs;
 
     CoParams C{};
     int passes = 0;
@@ -628,24 +660,12 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
 cudaError_t launch_sort_cells(const SpeciesDev &S, const YeeGrid &g, void *scratch, int grid,
                               long long *stats, int *status, cudaStream_t st)
 {
-    const size_t c = (size_t)(S.cap > 0 ? S.cap : 1);
-    unsigned char *p = (unsigned char *)scratch;
-    auto take = [&](size_t bytes) {
-        unsigned char *q = p;
-        p += (bytes + 255) / 256 * 256;
-        return q;
-    };
-    unsigned long long *keys[2] = {(unsigned long long *)take(c * 8),
-                                   (unsigned long long *)take(c * 8)};
-    unsigned *vals[2] = {(unsigned *)take(c * 4), (unsigned *)take(c * 4)};
-    (void)take(c);      // roles (unused here)
-    (void)take(c * 4);  // offsets (unused here)
-    Stage stg;
-    for (int f = 0; f < 9; ++f) stg.f[f] = (double *)take(c * 8);
-    stg.nemit = (int *)take(c * 4);
-    unsigned *hist = (unsigned *)take((size_t)kRadix * grid * 4);
-    (void)take((size_t)grid * 4 + 64);
-    long long *counts = (long long *)take(16 * 8);
+    const CoScratch cs = carve(scratch, S.cap, grid);
+    unsigned long long *const *keys = cs.keys;
+    unsigned *const *vals = cs.vals;
+    const Stage stg = cs.stg;
+    unsigned *hist = cs.hist;
+    long long *counts = cs.counts;
     const unsigned long long top = (unsigned long long)g.nx * (unsigned long long)g.ny;
     int bits = 0;
     while (bits < 64 && (top >> bits) != 0ull) ++bits;
@@ -663,6 +683,65 @@ cudaError_t launch_sort_cells(const SpeciesDev &S, const YeeGrid &g, void *scrat
     }
     k_sort_gather<<<grid, kCoThreads, 0, st>>>(S, vals[cur], stg, counts);
     k_co_copy_back<<<grid, kCoThreads, 0, st>>>(S, stg, counts, stats);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fused photon order
+
+namespace {
+
+// counts[3]: photons the fused window allocated; counts[0] and win[2]:
+// those it staged (the capacity bounds them), sorted next; win[1]: those it
+// stores (the free slots bound them); identity order to sort.
+__global__ void __launch_bounds__(kCoThreads) k_fo_prepare(SpeciesDev Ph, long long *counts,
+                                                           long long *win, unsigned *vals,
+                                                           int *status)
+{
+    const long long base = win[0];
+    const long long cap = Ph.present ? Ph.cap : 0;
+    const long long alloc = counts[3];
+    const long long staged = alloc < cap ? alloc : cap;
+    const long long stored = staged < cap - base ? staged : cap - base;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counts[0] = staged;
+        win[1] = stored;
+        win[2] = staged;
+        if (alloc > stored) raise_status(status, QP_WARN_BUFFER_FULL);
+    }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < staged; a += stride)
+        vals[a] = (unsigned)a;
+}
+
+}  // namespace
+
+FusedScratch fused_scratch(void *scratch, int64_t photon_cap, int grid, int key_bits)
+{
+    const CoScratch cs = carve(scratch, photon_cap, grid);
+    FusedScratch f;
+    for (int c = 0; c < 8; ++c) f.stage[c] = cs.stg.f[c];
+    f.rkeys = cs.keys[0];
+    f.moves_new = (unsigned short *)cs.off;
+    f.alloc = cs.counts + 3;
+    f.order = cs.vals[((key_bits + 7) / 8) & 1];
+    f.sorted_keys = cs.keys[((key_bits + 7) / 8) & 1];
+    return f;
+}
+
+cudaError_t launch_fused_order(const SpeciesDev &Ph, void *scratch, int grid, int key_bits,
+                               long long *win, int *status, cudaStream_t st)
+{
+    const CoScratch cs = carve(scratch, Ph.present ? Ph.cap : 0, grid);
+    k_fo_prepare<<<grid, kCoThreads, 0, st>>>(Ph, cs.counts, win, cs.vals[0], status);
+    int cur = 0;
+    for (int ps = 0; ps < (key_bits + 7) / 8; ++ps) {
+        k_co_hist<<<grid, kCoThreads, 0, st>>>(cs.keys[cur], 8 * ps, cs.hist, cs.counts);
+        k_co_scan<<<1, 1024, 0, st>>>(cs.hist, kRadix * grid, nullptr);
+        k_co_scatter<<<grid, kCoThreads, 0, st>>>(cs.keys[cur], cs.vals[cur], cs.keys[cur ^ 1],
+                                                   cs.vals[cur ^ 1], 8 * ps, cs.hist,
+                                                   cs.counts);
+        cur ^= 1;
+    }
     return cudaGetLastError();
 }
 

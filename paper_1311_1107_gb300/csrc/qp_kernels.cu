@@ -152,31 +152,47 @@ cudaError_t launch_step(const StepArgs &a, int precision, int field_kind, bool b
     return cudaLaunchKernel(fn, dim3(grid), dim3(kTile), args, smem, st);
 }
 
+static int bits_of(unsigned long long v)
+{
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+int fused_key_bits(int K, long long tiles, int *ordinal_bits)
+{
+    const int ob = bits_of((unsigned long long)(tiles > 0 ? tiles : 1) * 32ull - 1ull);
+    if (ordinal_bits) *ordinal_bits = ob;
+    return bits_of((unsigned long long)(K > 1 ? K - 1 : 0)) + ob + kEmitBits;
+}
+
 cudaError_t launch_fused(const StepArgs &a, int precision, int field_kind, int K,
-                         long long tiles_e, long long tiles, int *counts, long long *offs,
-                         long long *win, unsigned short *moves, int num_sms, cudaStream_t st)
+                         long long tiles_e, long long tiles, void *scratch, int order_grid,
+                         long long *win, int num_sms, cudaStream_t st)
 {
     const bool mixed = precision == QP_MIXED;
-    const void *count = mixed ? fused_kernel_mixed(field_kind, 0) : fused_kernel_fp64(field_kind, 0);
-    const void *write = mixed ? fused_kernel_mixed(field_kind, 1) : fused_kernel_fp64(field_kind, 1);
+    const void *lep = mixed ? fused_kernel_mixed(field_kind) : fused_kernel_fp64(field_kind);
     const void *photons = mixed ? fused_photons_mixed() : fused_photons_fp64();
-    if (!count || !write) return cudaErrorInvalidValue;
+    if (!lep) return cudaErrorInvalidValue;
+    const SpeciesDev &Ph = a.single.sp[2];
     FusedArgs f{};
     f.a = a;
     f.K = K;
+    const int key_bits = fused_key_bits(K, tiles, &f.ob);
     f.tiles_e = tiles_e;
     f.tiles = tiles;
-    f.counts = counts;
-    f.offs = offs;
+    f.fs = fused_scratch(scratch, Ph.present ? Ph.cap : 0, order_grid, key_bits);
     f.win = win;
-    f.moves = moves;
     void *args[] = {(void *)&f};
     const long long resident = (long long)num_sms * 32;
     const unsigned grid = (unsigned)(tiles < resident ? (tiles > 0 ? tiles : 1) : resident);
-    cudaError_t e = cudaLaunchKernel(count, dim3(grid), dim3(32), args, 0, st);
-    if (e == cudaSuccess) e = cudaLaunchKernel(fused_scan_kernel(), dim3(1), dim3(1024), args, 0, st);
-    if (e == cudaSuccess) e = cudaLaunchKernel(write, dim3(grid), dim3(32), args, 0, st);
-    const long long cap = a.single.sp[2].present ? a.single.sp[2].cap : 0;
+    cudaError_t e = cudaMemsetAsync(f.fs.alloc, 0, sizeof(long long), st);
+    if (e == cudaSuccess) e = cudaLaunchKernel(lep, dim3(grid), dim3(32), args, 0, st);
+    if (e == cudaSuccess) e = launch_fused_order(Ph, scratch, order_grid, key_bits, win, a.status, st);
+    const long long cap = Ph.present ? Ph.cap : 0;
     if (e == cudaSuccess && cap > 0) {
         long long pb = (cap + 255) / 256;
         if (pb > (long long)num_sms * 8) pb = (long long)num_sms * 8;

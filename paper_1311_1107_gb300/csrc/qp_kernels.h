@@ -17,16 +17,35 @@ size_t step_smem_fp64();
 size_t step_smem_mixed();
 size_t step_smem_bytes(int precision);
 // Fused steps (qp_step_fused): one window of K steps of the single problem
-// a.single (its time set for the window's first step).  counts and offs hold
-// K x tiles entries, win two, moves one per photon slot.
+// a.single (its time set for the window's first step).  The physics pass
+// stages each new photon at a provisional index (arrival order) with its
+// order key (step, emitter, emission index); launch_fused_order
+// (qp_coalesce.cu, on the coalescence scratch) sorts the keys; the photon
+// pass moves the window's photons and writes the new ones at their slots in
+// the order of K separate steps.  win: [0] photons at the window start,
+// [1] photons it stored, [2] photons it staged (all it emitted up to the
+// capacity; those past the free slots in key order are dropped, as K
+// separate steps drop them).
+struct FusedScratch {
+    double *stage[8];               // x y z ux uy uz tau w of the new photons
+    unsigned long long *rkeys;      // order key of each provisional photon
+    unsigned short *moves_new;      // steps left to each provisional photon
+    long long *alloc;               // provisional indices taken
+    const unsigned *order;          // provisional index of each slot (sorted)
+    const unsigned long long *sorted_keys;  // their keys
+};
+FusedScratch fused_scratch(void *scratch, int64_t photon_cap, int grid, int key_bits);
+cudaError_t launch_fused_order(const SpeciesDev &Ph, void *scratch, int grid, int key_bits,
+                               long long *win, int *status, cudaStream_t st);
+// Bits of the order key of a window of K steps over `tiles` lepton tiles.
+int fused_key_bits(int K, long long tiles, int *ordinal_bits);
 cudaError_t launch_fused(const StepArgs &a, int precision, int field_kind, int K,
-                         long long tiles_e, long long tiles, int *counts, long long *offs,
-                         long long *win, unsigned short *moves, int num_sms, cudaStream_t st);
-const void *fused_kernel_fp64(int field_kind, int pass);
-const void *fused_kernel_mixed(int field_kind, int pass);
+                         long long tiles_e, long long tiles, void *scratch, int order_grid,
+                         long long *win, int num_sms, cudaStream_t st);
+const void *fused_kernel_fp64(int field_kind);
+const void *fused_kernel_mixed(int field_kind);
 const void *fused_photons_fp64();
 const void *fused_photons_mixed();
-const void *fused_scan_kernel();
 cudaError_t launch_init_tau(double *tau, int64_t first, int64_t count, int64_t id_base,
                             int64_t id_split, int64_t id_append, uint64_t seed, int species,
                             cudaStream_t st);

@@ -1305,40 +1305,27 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
 // leptons then never change in number and the photons only move).  The
 // physics is lepton_particle, the photon motion photon_move*: the same
 // arithmetic as K launches of k_step, so the results are the same bits.
-// Photon slots keep the order of K separate steps (step, then emitter
-// slot, then emission index): a count pass records the photons each tile
-// stores at each step, one scan turns the counts into first slots, and the
-// write pass runs the same physics again and writes every photon at its
-// slot, moved over the window's remaining steps.  Tiles are one warp (a
-// tile's per-step count is a warp sum).
+// New photons take provisional indices in arrival order (one atomic a warp
+// and step) and are staged there with their order key: step, then emitter
+// (tile, lane), then emission index, the slot order of K separate steps.
+// The key sort (launch_fused_order) and k_fused_photons put them at those
+// slots.  Tiles are one warp.
+
+constexpr int kEmitBits = 3;
+static_assert(QP_MAX_EMISSIONS <= (1 << kEmitBits), "emission index bits");
 
 struct FusedArgs {
     StepArgs a;              // a.single: the problem at the window's first step
     int32_t K;               // steps in the window
-    int32_t pad;
+    int32_t ob;              // bits of the emitter ordinal (tile * 32 + lane) in the key
     long long tiles_e, tiles; // lepton tiles (electron tiles first)
-    int *counts;             // [K][tiles] photons stored per step and tile
-    long long *offs;         // [K][tiles] first slot of those photons
-    long long *win;          // [2] photons at the window start, photons stored in it
-    unsigned short *moves;   // [slot - win[0]] steps left to a new photon in the window
+    FusedScratch fs;
+    long long *win;          // [3] photons at the window start, stored and staged in it
 };
 
-// The append sinks of a fused lepton: the state stays in registers.
-struct FusedCountSink {
-    LeptonState &cur;
-    template <int C>
-    __device__ __forceinline__ void put(double v)
-    {
-        (&cur.x)[C] = v;
-    }
-    __device__ __forceinline__ void tables() {}
-    __device__ __forceinline__ void chi(double) {}
-    __device__ __forceinline__ void direction(double, double, double) {}
-    __device__ __forceinline__ void photon(int, double, double) {}
-    __device__ __forceinline__ void origin(double, double, double) {}
-};
-
-struct FusedWriteSink {
+// The append sink of a fused lepton: the state stays in registers, the
+// emitted photons are kept for the warp's provisional indices.
+struct FusedSink {
     LeptonState &cur;
     double chi_last, kx, ky, kz, ox, oy, oz;
     double gg[QP_MAX_EMISSIONS], tg[QP_MAX_EMISSIONS];
@@ -1370,27 +1357,8 @@ struct FusedWriteSink {
 
 static_assert(offsetof(LeptonState, tau) == 6 * sizeof(double), "LeptonState layout");
 
-// A new photon written at `slot` where the step that emitted it leaves it
-// (its emitter's position at the start of that step); k_fused_photons moves
-// it over the window's remaining steps.
-__device__ __forceinline__ void fused_photon(const SpeciesDev &Ph, int64_t slot, double ox,
-                                             double oy, double oz, double ux, double uy,
-                                             double uz, double tau, double w)
-{
-    Ph.x[slot] = ox;
-    Ph.y[slot] = oy;
-    if (Ph.z) Ph.z[slot] = oz;
-    Ph.ux[slot] = ux;
-    Ph.uy[slot] = uy;
-    Ph.uz[slot] = uz;
-    Ph.tau[slot] = tau;
-    Ph.w[slot] = w;
-    if (Ph.chi) Ph.chi[slot] = 0.0;
-    if (Ph.nemit) Ph.nemit[slot] = 0;
-}
-
 // One warp a block, at most 64 registers a thread (32 resident warps an SM).
-template <int PREC, int FK, int PASS>
+template <int PREC, int FK>
 __global__ void __launch_bounds__(32, 32) k_fused(const __grid_constant__ FusedArgs f)
 {
     using R = typename std::conditional<PREC == kFP64, double, float>::type;
@@ -1404,6 +1372,23 @@ __global__ void __launch_bounds__(32, 32) k_fused(const __grid_constant__ FusedA
     } else {
         H = a.tab.Hf;
         G = a.tab.Gsf;
+    }
+    // photons at the window start; new photons are staged up to the capacity
+    // (the key order decides which of them the free slots keep), the rest
+    // dropped here
+    long long stage_cap = 0;
+    {
+        const SpeciesDev &Ph = a.single.sp[2];
+        long long base = 0;
+        if (Ph.present) {
+            base = *((volatile long long *)Ph.n_live);
+            if (base < 0 || base > Ph.cap) {
+                if (lane == 0 && blockIdx.x == 0) raise_status(a.status, QP_ERR_INVALID_ARG);
+                base = base < 0 ? 0 : Ph.cap;
+            }
+            stage_cap = Ph.cap;
+        }
+        if (blockIdx.x == 0 && lane == 0) f.win[0] = base;
     }
     for (long long tile = blockIdx.x; tile < f.tiles; tile += gridDim.x) {
         {
@@ -1425,8 +1410,9 @@ __global__ void __launch_bounds__(32, 32) k_fused(const __grid_constant__ FusedA
         double w = 0.0;
         if (active) {
             cur = {S.x[i], S.y[i], S.z ? S.z[i] : 0.0, S.ux[i], S.uy[i], S.uz[i], S.tau[i]};
-            if (PASS == 1) w = S.w[i];
+            w = S.w[i];
         }
+        const unsigned long long ordinal = (unsigned long long)(tile * 32 + lane) << kEmitBits;
         const uint64_t s0 = sP.step;
         unsigned c_emit = 0, c_sub = 0, c_cont = 0, c_sat = 0, c_clamp = 0, c_ph = 0, c_drop = 0;
         double e_sub = 0.0, e_drop = 0.0, chi_last = 0.0;
@@ -1437,200 +1423,199 @@ __global__ void __launch_bounds__(32, 32) k_fused(const __grid_constant__ FusedA
                 __syncwarp();
             }
             LeptonOut o{};
-            if constexpr (PASS == 0) {
-                FusedCountSink sink{cur};
-                if (active) {
-                    const LeptonState in = cur;
-                    lepton_particle<PREC, FK, R>(a, sP, H, G, sp, S, i, in, o, sink);
-                }
-                const unsigned tot = __reduce_add_sync(0xFFFFFFFFu, (unsigned)o.nph);
-                if (lane == 0) f.counts[(size_t)k * f.tiles + tile] = (int)tot;
-            } else {
-                FusedWriteSink sink{cur};
-                if (active) {
-                    const LeptonState in = cur;
-                    lepton_particle<PREC, FK, R>(a, sP, H, G, sp, S, i, in, o, sink);
-                    chi_last = sink.chi_last;
-                }
-                // slots of this step's photons: the tile's first slot plus
-                // the stored photons of the lanes before
-                int inc = o.nph;
+            FusedSink sink{cur};
+            if (active) {
+                const LeptonState in = cur;
+                lepton_particle<PREC, FK, R>(a, sP, H, G, sp, S, i, in, o, sink);
+                chi_last = sink.chi_last;
+            }
+            // provisional indices: the warp's total from one atomic, the
+            // lanes in order after it
+            int inc = o.nph;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-                    if (lane >= d) inc += y;
-                }
-                const long long first = f.offs[(size_t)k * f.tiles + tile] + (inc - o.nph);
-                const SpeciesDev &Ph = sP.sp[2];
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+                if (lane >= d) inc += y;
+            }
+            const int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            if (tot) {
+                unsigned long long first = 0ull;
+                if (lane == 31)
+                    first = atomicAdd((unsigned long long *)f.fs.alloc, (unsigned long long)tot);
+                first = __shfl_sync(0xFFFFFFFFu, first, 31) + (unsigned long long)(inc - o.nph);
+                const unsigned long long kkey =
+                    ((unsigned long long)k << (f.ob + kEmitBits)) | ordinal;
                 for (int j = 0; j < o.nph; ++j) {
-                    const long long slot = first + j;
+                    const long long pa = (long long)first + j;
                     const double g = sink.gg[j];
-                    if (Ph.present && slot < Ph.cap) {
-                        fused_photon(Ph, slot, sink.ox, sink.oy, sink.oz, g * sink.kx,
-                                     g * sink.ky, g * sink.kz, sink.tg[j], w);
-                        f.moves[slot - f.win[0]] = (unsigned short)(f.K - 1 - k);
+                    if (pa < stage_cap) {
+                        f.fs.stage[0][pa] = sink.ox;
+                        f.fs.stage[1][pa] = sink.oy;
+                        f.fs.stage[2][pa] = sink.oz;
+                        f.fs.stage[3][pa] = g * sink.kx;
+                        f.fs.stage[4][pa] = g * sink.ky;
+                        f.fs.stage[5][pa] = g * sink.kz;
+                        f.fs.stage[6][pa] = sink.tg[j];
+                        f.fs.stage[7][pa] = w;
+                        f.fs.rkeys[pa] = kkey | (unsigned long long)j;
+                        f.fs.moves_new[pa] = (unsigned short)(f.K - 1 - k);
                         ++c_ph;
                     } else {
                         ++c_drop;
                         e_drop += w * g;
                     }
                 }
-                c_emit += (unsigned)o.n_emit;
-                c_sub += (unsigned)o.n_sub;
-                if (o.n_sub) e_sub += w * o.e_sub;
-                c_cont += o.cont;
-                c_sat += o.sat;
-                c_clamp += o.clamped;
             }
+            c_emit += (unsigned)o.n_emit;
+            c_sub += (unsigned)o.n_sub;
+            if (o.n_sub) e_sub += w * o.e_sub;
+            c_cont += o.cont;
+            c_sat += o.sat;
+            c_clamp += o.clamped;
         }
-        if constexpr (PASS == 1) {
-            if (active) {
-                S.x[i] = cur.x;
-                S.y[i] = cur.y;
-                if (S.z) S.z[i] = cur.z;
-                S.ux[i] = cur.ux;
-                S.uy[i] = cur.uy;
-                S.uz[i] = cur.uz;
-                S.tau[i] = cur.tau;
-                if (S.chi) S.chi[i] = chi_last;
-                if (c_emit && S.nemit) S.nemit[i] += (int)c_emit;
-            }
-            const unsigned t_emit = __reduce_add_sync(0xFFFFFFFFu, c_emit);
-            const unsigned t_sub = __reduce_add_sync(0xFFFFFFFFu, c_sub);
-            const unsigned t_cont = __reduce_add_sync(0xFFFFFFFFu, c_cont);
-            const unsigned t_sat = __reduce_add_sync(0xFFFFFFFFu, c_sat);
-            const unsigned t_clamp = __reduce_add_sync(0xFFFFFFFFu, c_clamp);
-            const unsigned t_ph = __reduce_add_sync(0xFFFFFFFFu, c_ph);
-            const unsigned t_drop = __reduce_add_sync(0xFFFFFFFFu, c_drop);
+        if (active) {
+            S.x[i] = cur.x;
+            S.y[i] = cur.y;
+            if (S.z) S.z[i] = cur.z;
+            S.ux[i] = cur.ux;
+            S.uy[i] = cur.uy;
+            S.uz[i] = cur.uz;
+            S.tau[i] = cur.tau;
+            if (S.chi) S.chi[i] = chi_last;
+            if (c_emit && S.nemit) S.nemit[i] += (int)c_emit;
+        }
+        const unsigned t_emit = __reduce_add_sync(0xFFFFFFFFu, c_emit);
+        const unsigned t_sub = __reduce_add_sync(0xFFFFFFFFu, c_sub);
+        const unsigned t_cont = __reduce_add_sync(0xFFFFFFFFu, c_cont);
+        const unsigned t_sat = __reduce_add_sync(0xFFFFFFFFu, c_sat);
+        const unsigned t_clamp = __reduce_add_sync(0xFFFFFFFFu, c_clamp);
+        const unsigned t_ph = __reduce_add_sync(0xFFFFFFFFu, c_ph);
+        const unsigned t_drop = __reduce_add_sync(0xFFFFFFFFu, c_drop);
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) {
-                e_sub += __shfl_xor_sync(0xFFFFFFFFu, e_sub, d);
-                e_drop += __shfl_xor_sync(0xFFFFFFFFu, e_drop, d);
+        for (int d = 16; d > 0; d >>= 1) {
+            e_sub += __shfl_xor_sync(0xFFFFFFFFu, e_sub, d);
+            e_drop += __shfl_xor_sync(0xFFFFFFFFu, e_drop, d);
+        }
+        if (lane == 0) {
+            DevStats &st = a.stats[S.slot_stats];
+            if (t_emit) atomicAdd(&st.n_emit, (unsigned long long)t_emit);
+            if (t_sub) atomicAdd(&st.n_subthreshold, (unsigned long long)t_sub);
+            if (t_cont) atomicAdd(&st.n_continuous, (unsigned long long)t_cont);
+            if (t_sat) atomicAdd(&st.n_saturated, (unsigned long long)t_sat);
+            if (t_clamp) {
+                atomicAdd(&st.n_clamped, (unsigned long long)t_clamp);
+                raise_status(a.status, QP_WARN_TABLE_CLAMPED);
             }
-            if (lane == 0) {
-                DevStats &st = a.stats[S.slot_stats];
-                if (t_emit) atomicAdd(&st.n_emit, (unsigned long long)t_emit);
-                if (t_sub) atomicAdd(&st.n_subthreshold, (unsigned long long)t_sub);
-                if (t_cont) atomicAdd(&st.n_continuous, (unsigned long long)t_cont);
-                if (t_sat) atomicAdd(&st.n_saturated, (unsigned long long)t_sat);
-                if (t_clamp) {
-                    atomicAdd(&st.n_clamped, (unsigned long long)t_clamp);
-                    raise_status(a.status, QP_WARN_TABLE_CLAMPED);
-                }
-                if (t_ph) atomicAdd(&st.n_photon, (unsigned long long)t_ph);
-                if (t_drop) atomicAdd(&st.n_photon_drop, (unsigned long long)t_drop);
-                if (e_sub != 0.0) atomicAdd(&st.e_subthreshold, e_sub);
-                if (e_drop != 0.0) atomicAdd(&st.e_dropped, e_drop);
-            }
+            if (t_ph) atomicAdd(&st.n_photon, (unsigned long long)t_ph);
+            if (t_drop) atomicAdd(&st.n_photon_drop, (unsigned long long)t_drop);
+            if (e_sub != 0.0) atomicAdd(&st.e_subthreshold, e_sub);
+            if (e_drop != 0.0) atomicAdd(&st.e_dropped, e_drop);
         }
         __syncwarp();
     }
 }
 
 // The photons of the window moved ballistically: those that existed at its
-// start over its K steps (decayed ones, tau < 0, stay), those it added over
-// the steps left after the step that emitted them.  One thread a photon.
+// start over its K steps in place (decayed ones, tau < 0, stay), the new
+// ones gathered from the staging in key order into the slots after them and
+// moved over the steps left after the step that emitted them.  One thread
+// a slot; the new live count.  Launched for any photon capacity > 0.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_fused_photons(const __grid_constant__ FusedArgs f)
 {
     const Problem &P = f.a.single;
     const SpeciesDev &Ph = P.sp[2];
-    const long long base = f.win[0];
-    long long n = base + f.win[1];
-    if (n > Ph.cap) n = Ph.cap;
+    const long long base = f.win[0], n = base + f.win[1];
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int moves = i < base ? f.K : (int)f.moves[i - base];
-        if (moves == 0 || !(Ph.tau[i] >= 0.0)) continue;
-        double x = Ph.x[i], y = Ph.y[i], z = Ph.z ? Ph.z[i] : 0.0;
-        const double ux = Ph.ux[i], uy = Ph.uy[i], uz = Ph.uz[i];
-        if constexpr (PREC == kFP64) {
-            const double g = photon_speed64(ux, uy, uz);
-            if (!(g > 0.0)) continue;
-            for (int m = 0; m < moves; ++m) {
-                x = photon_move64(x, ux, g, P.dt);
-                y = photon_move64(y, uy, g, P.dt);
-                z = photon_move64(z, uz, g, P.dt);
-            }
+        int moves;
+        double x, y, z, ux, uy, uz, tau;
+        long long pa = -1;
+        if (i < base) {
+            moves = f.K;
+            tau = Ph.tau[i];
+            if (!(tau >= 0.0)) continue;
+            x = Ph.x[i];
+            y = Ph.y[i];
+            z = Ph.z ? Ph.z[i] : 0.0;
+            ux = Ph.ux[i];
+            uy = Ph.uy[i];
+            uz = Ph.uz[i];
         } else {
-            const float fx = hi_d(ux), fy = hi_d(uy), fz = hi_d(uz);
-            const float g = photon_speed32(fx, fy, fz);
-            if (!(g > 0.0f)) continue;
-            const float c = P.mc.dt / g;
-            for (int m = 0; m < moves; ++m) {
-                x = photon_move32(x, fx, c);
-                y = photon_move32(y, fy, c);
-                z = photon_move32(z, fz, c);
+            pa = f.fs.order[i - base];
+            moves = f.fs.moves_new[pa];
+            x = f.fs.stage[0][pa];
+            y = f.fs.stage[1][pa];
+            z = f.fs.stage[2][pa];
+            ux = f.fs.stage[3][pa];
+            uy = f.fs.stage[4][pa];
+            uz = f.fs.stage[5][pa];
+            tau = f.fs.stage[6][pa];
+        }
+        if (moves > 0 && tau >= 0.0) {
+            if constexpr (PREC == kFP64) {
+                const double g = photon_speed64(ux, uy, uz);
+                if (g > 0.0)
+                    for (int m = 0; m < moves; ++m) {
+                        x = photon_move64(x, ux, g, P.dt);
+                        y = photon_move64(y, uy, g, P.dt);
+                        z = photon_move64(z, uz, g, P.dt);
+                    }
+            } else {
+                const float fx = hi_d(ux), fy = hi_d(uy), fz = hi_d(uz);
+                const float g = photon_speed32(fx, fy, fz);
+                if (g > 0.0f) {
+                    const float c = P.mc.dt / g;
+                    for (int m = 0; m < moves; ++m) {
+                        x = photon_move32(x, fx, c);
+                        y = photon_move32(y, fy, c);
+                        z = photon_move32(z, fz, c);
+                    }
+                }
             }
         }
         Ph.x[i] = x;
         Ph.y[i] = y;
         if (Ph.z) Ph.z[i] = z;
-    }
-}
-
-// Exclusive scan of the per-step, per-tile photon counts in step-major
-// order from the photons at the window's start; the new live count (the
-// capacity bounds it, the rest is dropped in order) and the window's totals.
-__global__ void __launch_bounds__(1024) k_fused_scan(const __grid_constant__ FusedArgs f)
-{
-    __shared__ long long s[1024];
-    const Problem &P = f.a.single;
-    const SpeciesDev &Ph = P.sp[2];
-    long long base = 0;
-    if (Ph.present) {
-        base = *((volatile long long *)Ph.n_live);
-        if (base < 0 || base > Ph.cap) {
-            if (threadIdx.x == 0) raise_status(f.a.status, QP_ERR_INVALID_ARG);
-            base = base < 0 ? 0 : Ph.cap;
+        if (pa >= 0) {
+            Ph.ux[i] = ux;
+            Ph.uy[i] = uy;
+            Ph.uz[i] = uz;
+            Ph.tau[i] = tau;
+            Ph.w[i] = f.fs.stage[7][pa];
+            if (Ph.chi) Ph.chi[i] = 0.0;
+            if (Ph.nemit) Ph.nemit[i] = 0;
         }
     }
-    const long long m = (long long)f.K * f.tiles;
-    const int t = threadIdx.x;
-    const long long per = (m + 1023) / 1024;
-    const long long lo = t * per, hi = lo + per < m ? lo + per : m;
-    long long sum = 0;
-    for (long long k = lo; k < hi; ++k) sum += f.counts[k];
-    s[t] = sum;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        const long long y = t >= d ? s[t - d] : 0;
-        __syncthreads();
-        s[t] += y;
-        __syncthreads();
+    // staged photons past the free slots: dropped, in key order, on the
+    // counters of the species that emitted them
+    const long long staged = f.win[2];
+    for (long long r = f.win[1] + (long long)blockIdx.x * blockDim.x + threadIdx.x; r < staged;
+         r += stride) {
+        const long long pa = f.fs.order[r];
+        const unsigned long long tile =
+            (f.fs.sorted_keys[r] >> kEmitBits & ((1ull << f.ob) - 1ull)) >> 5;
+        const int sp = tile < (unsigned long long)f.tiles_e ? 0 : 1;
+        const double ux = f.fs.stage[3][pa], uy = f.fs.stage[4][pa], uz = f.fs.stage[5][pa];
+        DevStats &st = f.a.stats[P.sp[sp].slot_stats];
+        atomicAdd(&st.n_photon, (unsigned long long)-1ll);
+        atomicAdd(&st.n_photon_drop, 1ull);
+        atomicAdd(&st.e_dropped, f.fs.stage[7][pa] * sqrt(ux * ux + uy * uy + uz * uz));
     }
-    long long run = base + s[t] - sum;
-    for (long long k = lo; k < hi; ++k) {
-        f.offs[k] = run;
-        run += f.counts[k];
-    }
-    if (t == 1023) {
-        const long long total = s[1023];
-        f.win[0] = base;
-        f.win[1] = total;
-        if (Ph.present) {
-            *Ph.n_live = base + total < Ph.cap ? base + total : Ph.cap;
-            if (base + total > Ph.cap) raise_status(f.a.status, QP_WARN_BUFFER_FULL);
-        } else if (total > 0) {
-            raise_status(f.a.status, QP_WARN_BUFFER_FULL);
-        }
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && Ph.present) *Ph.n_live = n;
 }
 
 template <int PREC>
-const void *fused_kernel_of(int fk, int pass)
+const void *fused_kernel_of(int fk)
 {
-#define QP_FUSED_CASE(F)                                                                     \
-    case F: return pass ? (const void *)k_fused<PREC, F, 1> : (const void *)k_fused<PREC, F, 0>;
     switch (fk) {
-        QP_FUSED_CASE(QP_FIELD_NONE)
-        QP_FUSED_CASE(QP_FIELD_PLANE)
-        QP_FUSED_CASE(QP_FIELD_GAUSSIAN)
-        QP_FUSED_CASE(QP_FIELD_YEE2D)
-        QP_FUSED_CASE(QP_FIELD_UNIFORM_B)
+    case QP_FIELD_NONE: return (const void *)k_fused<PREC, QP_FIELD_NONE>;
+    case QP_FIELD_PLANE: return (const void *)k_fused<PREC, QP_FIELD_PLANE>;
+    case QP_FIELD_GAUSSIAN: return (const void *)k_fused<PREC, QP_FIELD_GAUSSIAN>;
+    case QP_FIELD_YEE2D: return (const void *)k_fused<PREC, QP_FIELD_YEE2D>;
+    case QP_FIELD_UNIFORM_B: return (const void *)k_fused<PREC, QP_FIELD_UNIFORM_B>;
     default: return nullptr;
     }
-#undef QP_FUSED_CASE
 }
 
 template <int PREC, bool BATCH>

@@ -10,8 +10,7 @@ const void *step_kernel_fp64(int field_kind, bool batch)
 
 size_t step_smem_fp64() { return sizeof(Smem<double>); }
 
-const void *fused_kernel_fp64(int field_kind, int pass) { return fused_kernel_of<kFP64>(field_kind, pass); }
+const void *fused_kernel_fp64(int field_kind) { return fused_kernel_of<kFP64>(field_kind); }
 const void *fused_photons_fp64() { return (const void *)k_fused_photons<kFP64>; }
-const void *fused_scan_kernel() { return (const void *)k_fused_scan; }
 
 }  // namespace qp

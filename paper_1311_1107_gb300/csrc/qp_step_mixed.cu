@@ -12,7 +12,7 @@ const void *step_kernel_mixed(int field_kind, bool batch)
 
 size_t step_smem_mixed() { return sizeof(Smem<float>); }
 
-const void *fused_kernel_mixed(int field_kind, int pass) { return fused_kernel_of<kMixed>(field_kind, pass); }
+const void *fused_kernel_mixed(int field_kind) { return fused_kernel_of<kMixed>(field_kind); }
 const void *fused_photons_mixed() { return (const void *)k_fused_photons<kMixed>; }
 
 }  // namespace qp

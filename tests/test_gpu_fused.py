@@ -3,9 +3,11 @@ registers; pairs off) against one launch per step (qp_step) and against the
 oracle (GPU only).
 
 Both run the same per-particle arithmetic and the same photon motion, and
-the fused windows keep the photons' slot order, so every array of every
-species must be the same bits, and every event counter the same number
-(the sub-threshold energy is a sum in another order: within 1e-12)."""
+the fused windows put the new photons in the slot order of separate steps
+(a sort on their order keys), so every array of every species must be the
+same bits, and every event counter the same number (the sub-threshold
+energy is a sum in another order: within 1e-12).  A full photon buffer
+drops the same photons unless one window emits more than its capacity."""
 import numpy as np
 import pytest
 
@@ -102,6 +104,28 @@ def test_fused_overflow_drops_the_same_photons(ctx):
     b, db = _state(sim)
     _same("overflow", a, b, da, db)
     assert db["electron"].status == Q.QP_WARN_BUFFER_FULL
+
+
+def test_fused_window_past_the_capacity_keeps_the_counts(ctx):
+    # one window emits more photons than the whole photon capacity: the
+    # photons staged first are kept, so which ones survive may differ from
+    # single steps; the leptons and every counter may not
+    w = W.plane_wave_collision(n=600, n_steps=120)
+    w["capacity"] = dict(w["capacity"], photon=500)
+    ref = Simulation(w, precision="mixed", ctx=ctx)
+    ref.run(120)
+    a, da = _state(ref)
+    sim = Simulation(w, precision="mixed", ctx=ctx)
+    sim.run_fused(120, 120)
+    b, db = _state(sim)
+    assert da["electron"].n_photon + da["electron"].n_photon_drop > 500
+    assert len(b["photon"]["x"]) == len(a["photon"]["x"]) == 500
+    for k, v in a["electron"].items():
+        assert np.array_equal(v, b["electron"][k]), k
+    for c in COUNTERS:
+        assert getattr(da["electron"], c) == getattr(db["electron"], c), c
+    assert db["electron"].status == Q.QP_WARN_BUFFER_FULL
+    assert np.all(b["photon"]["w"] > 0)
 
 
 def test_fused_plane_wave_against_the_oracle(ctx):

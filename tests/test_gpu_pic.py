@@ -128,18 +128,28 @@ def test_pic_foil_matches_the_oracle(ctx, precision):
     n = len(w["electrons"]["x"])
     osim, osp = run_oracle(w, n_steps)
     o = head(oracle_arrays(osp["electron"]), n)
-    twins = [head(oracle_arrays(run_oracle(w, n_steps, noise=2e-7, noise_key=k)[1]["electron"]),
-                  n) for k in (0, 1)]
+    twin_runs = [run_oracle(w, n_steps, noise=2e-7, noise_key=k) for k in (0, 1)]
+    twins = [head(oracle_arrays(t[1]["electron"]), n) for t in twin_runs]
     rep = chaos_aware_compare(head(g, n), o, twins, 1e-4, f"PIC foil {precision}",
                               margin=osp["electron"].margin[:n],
                               margin_min=1e-4 if precision == "mixed" else 1e-10,
                               min_comparable=0.05)
     distribution_check(head(g, n), o, f"PIC foil {precision}")
-    # the fields: the pulse on the grid, within FP32-level differences
+    # the fields: the pulse on the grid plus the plasma's current.  The
+    # current follows the particles, whose orbits are chaotic, and a particle
+    # whose emissions differ (a discrete event decided at a rounding-level
+    # margin) deposits a different current from then on.  The GPU run is
+    # another sample of that sensitivity, which the oracle's noise-kicked
+    # twins measure: the bar is 1e-3 of the largest field or four times the
+    # twins' spread (a margin for sample-to-sample variation), whichever is
+    # larger
     ey_g = sim._keep[1].cpu().numpy()
     ey_o = osim.field._keep[1]
-    err = np.abs(ey_g - ey_o).max() / np.abs(ey_o).max()
-    print(f"[PIC foil {precision}] E_y largest difference {err:.3g} of the largest")
-    assert err <= 1e-3 and np.abs(ey_o).max() > 50.0
+    scale = np.abs(ey_o).max()
+    err = np.abs(ey_g - ey_o).max() / scale
+    spread = max(np.abs(t[0].field._keep[1] - ey_o).max() / scale for t in twin_runs)
+    print(f"[PIC foil {precision}] E_y largest difference {err:.3g} of the largest "
+          f"(oracle twins {spread:.3g})")
+    assert err <= max(1e-3, 4.0 * spread) and scale > 50.0
     assert np.abs(o["uy"]).max() > 5.0 and rep["comparable"] > 0
     sim.close()
