@@ -239,16 +239,20 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream);
  * change in number and photons only move.  The results are those of
  * qp_step with the same parameters, bit for bit: the same per-particle
  * arithmetic, photons in the same slots (step, then emitter slot, then
- * emission index), the same counters.  A window is a count pass (photons
- * stored per step and 32-lepton tile), a scan of the counts into first
- * slots, a write pass (the same physics again; photons written at their
- * slots) and the motion of the window's photons, one thread a photon (those
- * that existed at its start over K steps, the new ones over the steps left
- * after their birth).  The call reads the live lepton counts to the host
- * once (it synchronises `stream`) and grows the context's scratch (12 bytes
- * per step and tile, 2 per photon slot; an allocation): not during a stream
- * capture.  Windows hold at most 65535 steps.  QP_ERR_INVALID_ARG (nothing
- * enqueued) for pairs on, fuse < 1, or what qp_step rejects.
+ * emission index), the same counters.  A window is one physics pass (each
+ * new photon staged at a provisional index with its order key: step,
+ * emitter, emission index), a radix sort of those keys, and the motion of
+ * the window's photons, one thread a slot (those that existed at its start
+ * over K steps, the new ones gathered into key order and moved over the
+ * steps left after their birth).  Photons past the free slots are dropped
+ * in key order, as separate steps drop them, while one window emits no more
+ * photons than the photon capacity; beyond that the counters and leptons
+ * still agree but the surviving photons may differ (QP_WARN_BUFFER_FULL in
+ * both cases).  The call reads the live lepton counts to the host once (it
+ * synchronises `stream`) and grows the context's scratch (about 110 bytes
+ * per photon slot; an allocation).  Windows hold at most 65535 steps; the
+ * photon capacity stays below 2^32.  QP_ERR_INVALID_ARG (nothing enqueued)
+ * for pairs on, fuse < 1, a stream being captured, or what qp_step rejects.
  */
 int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stream);
 
@@ -548,7 +552,8 @@ int qp_compact_photons(qp_ctx *ctx, int32_t handle, qp_coalesce_stats *out, void
  * the array it reads, but all calls share it: calls that overlap on the GPU
  * (other streams, no ordering between them) race and return wrong results.
  * The result is copied to host memory and `stream` is synchronised before
- * the call returns.
+ * the call returns: a stream being captured is refused with
+ * QP_ERR_INVALID_ARG (nothing enqueued).
  * The paper has no counterpart: this is plumbing of the library.
  */
 #define QP_NOALLOC_MAX_TILES 4096

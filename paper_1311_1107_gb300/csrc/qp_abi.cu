@@ -947,6 +947,9 @@ int qp_step_fused(qp_ctx *ctx, const qp_step_params *s, int32_t fuse, void *stre
     DeviceGuard g(ctx->device);
     if (!g.ok) return QP_ERR_CUDA;
     cudaStream_t cs = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) return QP_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return QP_ERR_INVALID_ARG;  // it synchronises
     // the lepton counts (they do not change without pairs): read once
     long long n[2] = {0, 0};
     const int32_t hs[2] = {s->electron, s->positron};

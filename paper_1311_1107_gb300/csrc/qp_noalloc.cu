@@ -80,6 +80,9 @@ extern "C" int qp_diagnostics_noalloc(const qp_species_desc *d, qp_diag *out, vo
     const int dev = owning_device(d, current);
     DeviceSwitch guard(dev, current);
     if (!guard.ok) return QP_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return QP_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return QP_ERR_INVALID_ARG;  // it synchronises
     double *scratch = nullptr;
     int st = scratch_for_device(dev, &scratch);
     if (st != QP_OK) return st;

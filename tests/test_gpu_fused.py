@@ -147,3 +147,20 @@ def test_fused_rejects_pairs_on(ctx):
     sim = Simulation(w, precision="fp64", ctx=ctx)
     with pytest.raises(Q.QPError):
         sim.run_fused(10, 5)
+
+
+def test_fused_refuses_a_stream_being_captured(ctx):
+    # a window reads the lepton counts to the host: during a capture the
+    # call returns QP_ERR_INVALID_ARG before anything is enqueued
+    w = W.plane_wave_collision(n=100, n_steps=10)
+    sim = Simulation(w, precision="mixed", ctx=ctx)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=s):
+        with pytest.raises(Q.QPError) as e:
+            sim.run_fused(10, 5, stream=s)
+    assert e.value.status == Q.QP_ERR_INVALID_ARG
+    assert sim.run_fused(10, 5) >= 0
+    torch.cuda.synchronize()
+    assert sim.step_index == 10

@@ -90,3 +90,18 @@ def test_noalloc_at_the_largest_capacity(sim, n_live):
     for _ in range(2):
         _same(Q.qp_diagnostics_noalloc(sp._desc), ref)
     Q.qp_destroy_species(sim.ctx, sp.handle)
+
+
+def test_noalloc_refuses_a_stream_being_captured(sim):
+    # the call synchronises its stream: during a capture it returns
+    # QP_ERR_INVALID_ARG before anything is enqueued, and the capture stays
+    # valid (it ends with an empty graph)
+    sp = sim.species["electron"]
+    Q.qp_diagnostics_noalloc(sp._desc)  # the scratch array looked up first
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=s):
+        with pytest.raises(Q.QPError) as e:
+            Q.qp_diagnostics_noalloc(sp._desc, C.c_void_p(s.cuda_stream))
+    assert e.value.status == Q.QP_ERR_INVALID_ARG
+    _same(Q.qp_diagnostics_noalloc(sp._desc), sim.diagnostics("electron"))
