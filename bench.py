@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--workload", choices=("foil", "collision", "plane", "serving", "fused",
-                                          "coalesce"),
+                                          "coalesce", "refill", "pic"),
                    default="foil")
     p.add_argument("--requests", type=int, default=None,
                    help="serving: requests in the stream (default 256)")
@@ -91,6 +91,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--ref-cores", type=int, default=None,
+                   help="reference arm: host cores (processes) to time the oracle on "
+                        "(default: every core of the host)")
     return p.parse_args()
 
 
@@ -98,6 +101,10 @@ def workload(name: str, seed: int, start_step: int | None = None, collision_n=No
     from paper_1311_1107_gb300 import workloads as W
     if name == "foil":
         return W.laser_on_foil(seed=seed)
+    if name == "refill":  # the foil, its fields refilled from the pulse before every step
+        return W.laser_on_foil(seed=seed, refill=True)
+    if name == "pic":  # the foil as a PIC cycle (Yee solver and current around each step)
+        return W.laser_on_foil(seed=seed, pic=True)
     if name == "collision":
         # the 1e7-electron collision, timed from `start` (default 980: the
         # window around the pulse peak at step 1000), the beam placed where
@@ -314,13 +321,17 @@ def fused_leg(dev, flush, warmup: int):
     return out
 
 
+STEP_SOURCES = ("qp_step.cuh", "qp_device.cuh", "qp_mixed.cuh", "qp_df.h", "qp_internal.h",
+                "qp_kernels.h", "qp_step_fp64.cu", "qp_step_mixed.cu")
+
+
 def kernel_source_id() -> str:
     """Hash of the sources and build flags the step kernel is compiled from
     (the ncu summaries under profiles/ name the one they were taken on)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_1107_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in STEP_SOURCES:
         h.update(f.encode())
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
@@ -331,21 +342,27 @@ def kernel_source_id() -> str:
 
 
 def measured_traffic(profile: str, precision: str):
-    """DRAM bytes (read, write) per k_step launch from the committed ncu
-    summary of the workload, when it was taken on the current kernel
-    sources; None otherwise (the counters no longer describe the kernel)."""
+    """DRAM bytes per k_step launch from the committed ncu summary of the
+    workload, when it was taken on the current kernel sources; None
+    otherwise (the counters no longer describe the kernel).  Returns
+    (read, write, algorithmic): `algorithmic` is the model's bytes per
+    launch of the captured launches when the summary states them (a capture
+    of a smaller case of the workload), else None."""
     import re
+    if profile is None:
+        return None
     path = os.path.join(PROFILES, profile)
     if not os.path.exists(path):
         return None
     sid = kernel_source_id()
-    pat = re.compile(r"^traffic, (\w+): read (\d+) B, write (\d+) B per launch, "
-                     r"kernel source ([0-9a-f]{12})")
+    pat = re.compile(r"^traffic, (\w+): read (\d+) B, write (\d+) B per launch"
+                     r"(?:, algorithmic (\d+) B per launch)?, kernel source ([0-9a-f]{12})")
     with open(path) as f:
         for line in f:
             m = pat.match(line.strip())
-            if m and m.group(1) == precision and m.group(4) == sid:
-                return int(m.group(2)), int(m.group(3))
+            if m and m.group(1) == precision and m.group(5) == sid:
+                alg = int(m.group(4)) if m.group(4) else None
+                return int(m.group(2)), int(m.group(3)), alg
     return None
 
 
@@ -353,8 +370,12 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
     """Roofline of k_step (the only kernel of a step): algorithmic bytes of
     all lepton and photon slot-steps and appended particles in the timed
     steps, over the summed k_step device time (CUDA events on its stream).
-    traffic: (read, write) DRAM bytes per launch from an ncu capture of the
-    same command, or None."""
+    traffic: (read, write, algorithmic) DRAM bytes per launch from an ncu
+    capture (measured_traffic), or None.  A capture of a smaller case of the
+    workload states the algorithmic bytes of its launches; its traffic is
+    scaled to these launches by the ratio of algorithmic bytes (the traffic
+    of a launch grows with the slots it steps and the particles it
+    appends)."""
     lep_b, pho_b, new_b = species_bytes(dims, pairs)
     nbytes = (res["lep_slots"] * lep_b + res["pho_slots"] * pho_b
               + res.get("dead_slots", 0) * DEAD_B
@@ -362,16 +383,25 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
     t_ms = res["kernel_ms"][0]
     n = max(res["launches"][0], 1)
     achieved = nbytes / (t_ms * 1e-3) / 1e9
-    return {"kernel": "k_step", "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
-            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-            "traffic": sum(traffic) if traffic else None,
-            "traffic_read_write": list(traffic) if traffic else None,
-            "bytes_per_launch": round(nbytes / n), "avg_launch_us": round(t_ms * 1e3 / n, 3),
+    rw, scale = None, None
+    if traffic:
+        rd, wr, alg = traffic
+        scale = (nbytes / n) / alg if alg else 1.0
+        rw = [round(rd * scale), round(wr * scale)]
+    out = {"kernel": "k_step", "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+           "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+           "traffic": sum(rw) if rw else None,
+           "traffic_read_write": rw,
+           "bytes_per_launch": round(nbytes / n), "avg_launch_us": round(t_ms * 1e3 / n, 3),
             "bytes_model": f"{lep_b} B per lepton slot-step, {pho_b} B per photon slot-step, "
                            f"{DEAD_B} B per decayed-photon slot (tau read), "
                            f"{new_b} B per appended particle",
             "peak_source": ("measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
                             else "fallback 6.8 TB/s")}
+    if traffic and traffic[2]:
+        out["traffic_scaled"] = (f"from a smaller capture of the workload: x{scale:.3f}, "
+                                 "the ratio of algorithmic bytes per launch")
+    return out
 
 
 def e2e(w, precision, steps, dev):
@@ -573,8 +603,9 @@ def cpu_baseline(w, spec, args):
     target = seconds * slots_c / max(dt_c, 1e-6)  # particle-steps
     n_all = len(w["electrons"]["x"])
     n = int(min(n_all, max(1024, target / steps)))
-    if n == n_all:  # every electron: more steps, up to the timed count
-        steps = int(min(args.steps, max(steps, target / n_all)))
+    job_steps = max(args.steps, int(w["params"].get("n_steps", args.steps)))
+    if n == n_all:  # every electron: more steps, up to the workload's own
+        steps = int(min(job_steps, max(steps, target / n_all)))
     slots, dt, n1 = oracle_sample(w, n, steps, ppe)
     cores = host_cores()
     one = {"value": round(slots / dt, 1), "unit": UNIT, "cores": 1,
@@ -587,8 +618,7 @@ def cpu_baseline(w, spec, args):
     steps_a = steps
     if n_all_cores == n_all:
         total = cores * slots / max(dt, 1e-6) * seconds
-        steps_a = int(min(max(args.steps, int(w["params"].get("n_steps", args.steps))),
-                          max(steps, total / n_all)))
+        steps_a = int(min(job_steps, max(steps, total / n_all)))
     slots_a, dt_a, na = oracle_all_cores(spec, n_all_cores, steps_a, ppe, cores)
     return {"value": round(slots_a / dt_a, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{na} electrons (evenly spaced slots) split over {cores} processes "
@@ -619,9 +649,16 @@ def reference_arm(args):
         if dist:
             dist.destroy_process_group()
         return
+    if args.workload in ("refill", "pic", "coalesce"):
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the oracle arm times the foil, collision, plane and "
+                                         "fused (plane-wave) workloads"}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     spec = (args.workload, 0, args.start_step, args.collision_n)
     w = workload(*spec)
-    cores = host_cores()
+    cores = args.ref_cores or host_cores()
     per_core = 2048 if args.workload != "collision" else 512
     n_sample = per_core * cores
     ppe = 256 if args.workload == "collision" else 16
@@ -695,6 +732,8 @@ def ours_arm(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     profile = {"foil": "k_step_foil2d.md", "collision": "k_step_collision.md"}.get(
         args.workload, "k_step_" + args.workload + ".md")
+    if args.workload in ("refill", "pic"):
+        profile = None  # more kernels than k_step a step: no k_step traffic line
 
     clocks = ClockSampler(dev)
     clocks.start()

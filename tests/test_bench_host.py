@@ -18,20 +18,45 @@ def test_traffic_is_read_only_for_the_current_kernel_sources(tmp_path, monkeypat
     (tmp_path / "k_step_x.md").write_text(
         "# summary\n\n"
         f"traffic, mixed: read 1000 B, write 24 B per launch, kernel source {sid}\n"
-        "traffic, fp64: read 2000 B, write 8 B per launch, kernel source 000000000000\n")
+        "traffic, fp64: read 2000 B, write 8 B per launch, kernel source 000000000000\n"
+        f"traffic, fp32: read 300 B, write 100 B per launch, algorithmic 200 B per launch, "
+        f"kernel source {sid}\n")
     monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
-    assert bench.measured_traffic("k_step_x.md", "mixed") == (1000, 24)
+    assert bench.measured_traffic("k_step_x.md", "mixed") == (1000, 24, None)
     assert bench.measured_traffic("k_step_x.md", "fp64") is None   # other sources
+    assert bench.measured_traffic("k_step_x.md", "fp32") == (300, 100, 200)
     assert bench.measured_traffic("absent.md", "mixed") is None
+
+
+def test_kernel_source_id_follows_the_step_sources_only(tmp_path, monkeypatch):
+    # a copy of the sources: the id changes with a step source, not with
+    # another unit of the library
+    import shutil
+    root = tmp_path / "r"
+    for d in ("paper_1311_1107_gb300", "include"):
+        shutil.copytree(bench.ROOT + "/" + d, root / d,
+                        ignore=shutil.ignore_patterns("_build", "*.so", "__pycache__"))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    sid = bench.kernel_source_id()
+    csrc = root / "paper_1311_1107_gb300" / "csrc"
+    (csrc / "qp_pic.cu").write_text((csrc / "qp_pic.cu").read_text() + "// x\n")
+    assert bench.kernel_source_id() == sid
+    (csrc / "qp_step.cuh").write_text((csrc / "qp_step.cuh").read_text() + "// x\n")
+    assert bench.kernel_source_id() != sid
 
 
 def test_roofline_reports_traffic_and_fraction():
     res = {"lep_slots": 1000, "pho_slots": 0, "photons_added": 0, "pairs_added": 0,
            "kernel_ms": [1e-3, 0.0, 0.0], "launches": [1, 0, 0]}
-    r = bench.roofline(res, 3, True, 100.0, "measured", (50, 10))
+    r = bench.roofline(res, 3, True, 100.0, "measured", (50, 10, None))
     assert r["achieved"] == 112.0 and r["frac"] == 1.12  # 112 kB in 1 us
     assert r["traffic"] == 60 and r["traffic_read_write"] == [50, 10]
+    assert "traffic_scaled" not in r
     assert bench.roofline(res, 3, True, 100.0, "measured")["traffic"] is None
+    # a capture of a smaller case (algorithmic 56 kB a launch): scaled by 2
+    s = bench.roofline(res, 3, True, 100.0, "measured", (50_000, 10_000, 56_000))
+    assert s["traffic_read_write"] == [100_000, 20_000] and s["traffic"] == 120_000
+    assert "x2.000" in s["traffic_scaled"]
 
 
 def test_roofline_counts_decayed_photons_as_their_tau_read_only():
