@@ -157,31 +157,73 @@ __global__ void __launch_bounds__(kCoThreads) k_co_hist(const unsigned long long
     hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m entries in place (one block of 1024 threads, each
-// owning a contiguous segment).
-__global__ void __launch_bounds__(1024) k_co_scan(unsigned *v, int m, long long *total)
+// Exclusive scan of m entries in place, one block of 1024 threads, in tiles
+// of 8192 entries: a tile is loaded with coalesced reads into shared memory
+// (one pad word per 32, so that a thread's 8 contiguous entries fall in
+// distinct banks across the warp), each thread scans its 8 entries, the
+// thread sums are scanned across the block, and the tile is written back
+// coalesced with the running total of the earlier tiles added.  total: the
+// sum of all entries, or nullptr.
+constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) k_co_scan(unsigned *v, int m, long long *total)
 {
-    __shared__ unsigned s[1024];
-    const int t = threadIdx.x;
-    const int per = (m + 1023) / 1024;
-    const int a = t * per, b = min(m, a + per);
-    unsigned sum = 0u;
-    for (int i = a; i < b; ++i) sum += v[i];
-    s[t] = sum;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        const unsigned y = t >= d ? s[t - d] : 0u;
+    __shared__ unsigned s[kScanTile + kScanTile / 32];
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned s_tile;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned carry = 0u;
+    for (int base = 0; base < m; base += kScanTile) {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = k * kScanThreads + t;
+            s[i + (i >> 5)] = base + i < m ? v[base + i] : 0u;
+        }
         __syncthreads();
-        s[t] += y;
+        unsigned loc[kScanPer], sum = 0u;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = t * kScanPer + k;
+            loc[k] = s[i + (i >> 5)];
+            sum += loc[k];
+        }
+        unsigned inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) s_warp[w] = inc;
         __syncthreads();
+        if (w == 0) {
+            const unsigned x = s_warp[lane];
+            unsigned xi = x;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned y = __shfl_up_sync(0xFFFFFFFFu, xi, d);
+                if (lane >= d) xi += y;
+            }
+            s_warp[lane] = xi - x;
+            if (lane == 31) s_tile = xi;
+        }
+        __syncthreads();
+        unsigned run = carry + s_warp[w] + (inc - sum);
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = t * kScanPer + k;
+            s[i + (i >> 5)] = run;
+            run += loc[k];
+        }
+        carry += s_tile;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int i = k * kScanThreads + t;
+            if (base + i < m) v[base + i] = s[i + (i >> 5)];
+        }
+        __syncthreads();  // s, s_warp and s_tile are reused by the next tile
     }
-    unsigned run = s[t] - sum;
-    for (int i = a; i < b; ++i) {
-        const unsigned x = v[i];
-        v[i] = run;
-        run += x;
-    }
-    if (total && t == 1023) *total = (long long)s[1023];
+    if (total && t == 0) *total = (long long)carry;
 }
 
 // Stable scatter: the block walks its chunk tile by tile; within a tile an

@@ -25,41 +25,42 @@ __device__ __forceinline__ float at(const float *a, int64_t nx, int64_t ny, int6
     return (i < 0 || j < 0 || i >= nx || j >= ny) ? 0.0f : a[j * nx + i];
 }
 
-__global__ void __launch_bounds__(kPicBlock) k_yee_b(YeeGrid g, float dtb)
+// Nodes by rows: blockIdx.y strides over the rows, the threads of blockIdx.x
+// over the columns (no index division).
+__global__ void __launch_bounds__(kPicBlock) k_yee_b(YeeGrid g, float idx, float idy, float dtb)
 {
-    const int64_t n = g.nx * g.ny;
-    const float idx = 1.0f / g.dx, idy = 1.0f / g.dy;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const int64_t j = k / g.nx, i = k - j * g.nx;
-        const float ez = g.f[2][k];
-        const float dEz_dy = (at(g.f[2], g.nx, g.ny, i, j + 1) - ez) * idy;
-        const float dEz_dx = (at(g.f[2], g.nx, g.ny, i + 1, j) - ez) * idx;
-        const float dEy_dx = (at(g.f[1], g.nx, g.ny, i + 1, j) - g.f[1][k]) * idx;
-        const float dEx_dy = (at(g.f[0], g.nx, g.ny, i, j + 1) - g.f[0][k]) * idy;
-        g.f[3][k] -= dtb * dEz_dy;
-        g.f[4][k] += dtb * dEz_dx;
-        g.f[5][k] -= dtb * (dEy_dx - dEx_dy);
-    }
+    for (int64_t j = blockIdx.y; j < g.ny; j += gridDim.y)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nx;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t k = j * g.nx + i;
+            const float ez = g.f[2][k];
+            const float dEz_dy = (at(g.f[2], g.nx, g.ny, i, j + 1) - ez) * idy;
+            const float dEz_dx = (at(g.f[2], g.nx, g.ny, i + 1, j) - ez) * idx;
+            const float dEy_dx = (at(g.f[1], g.nx, g.ny, i + 1, j) - g.f[1][k]) * idx;
+            const float dEx_dy = (at(g.f[0], g.nx, g.ny, i, j + 1) - g.f[0][k]) * idy;
+            g.f[3][k] -= dtb * dEz_dy;
+            g.f[4][k] += dtb * dEz_dx;
+            g.f[5][k] -= dtb * (dEy_dx - dEx_dy);
+        }
 }
 
-__global__ void __launch_bounds__(kPicBlock) k_yee_e(YeeGrid g, const float *jx, const float *jy,
+__global__ void __launch_bounds__(kPicBlock) k_yee_e(YeeGrid g, float idx, float idy,
+                                                     const float *jx, const float *jy,
                                                      const float *jz, float dt)
 {
-    const int64_t n = g.nx * g.ny;
-    const float idx = 1.0f / g.dx, idy = 1.0f / g.dy;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const int64_t j = k / g.nx, i = k - j * g.nx;
-        const float bz = g.f[5][k];
-        const float dBz_dy = (bz - at(g.f[5], g.nx, g.ny, i, j - 1)) * idy;
-        const float dBz_dx = (bz - at(g.f[5], g.nx, g.ny, i - 1, j)) * idx;
-        const float dBy_dx = (g.f[4][k] - at(g.f[4], g.nx, g.ny, i - 1, j)) * idx;
-        const float dBx_dy = (g.f[3][k] - at(g.f[3], g.nx, g.ny, i, j - 1)) * idy;
-        g.f[0][k] += dt * (dBz_dy - (jx ? jx[k] : 0.0f));
-        g.f[1][k] += dt * (-dBz_dx - (jy ? jy[k] : 0.0f));
-        g.f[2][k] += dt * (dBy_dx - dBx_dy - (jz ? jz[k] : 0.0f));
-    }
+    for (int64_t j = blockIdx.y; j < g.ny; j += gridDim.y)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.nx;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t k = j * g.nx + i;
+            const float bz = g.f[5][k];
+            const float dBz_dy = (bz - at(g.f[5], g.nx, g.ny, i, j - 1)) * idy;
+            const float dBz_dx = (bz - at(g.f[5], g.nx, g.ny, i - 1, j)) * idx;
+            const float dBy_dx = (g.f[4][k] - at(g.f[4], g.nx, g.ny, i - 1, j)) * idx;
+            const float dBx_dy = (g.f[3][k] - at(g.f[3], g.nx, g.ny, i, j - 1)) * idy;
+            g.f[0][k] += dt * (dBz_dy - (jx ? jx[k] : 0.0f));
+            g.f[1][k] += dt * (-dBz_dx - (jy ? jy[k] : 0.0f));
+            g.f[2][k] += dt * (dBy_dx - dBx_dy - (jz ? jz[k] : 0.0f));
+        }
 }
 
 // One thread a particle: q w v / (dx dy) spread with the linear weights of
@@ -107,6 +108,19 @@ __global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, float q, do
     }
 }
 
+// Blocks of the node kernels: enough column blocks for a row, rows over
+// blockIdx.y (a grid of about 8 blocks an SM; each block strides over rows).
+dim3 node_grid(const YeeGrid &g, int num_sms)
+{
+    int64_t bx = (g.nx + kPicBlock - 1) / kPicBlock;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    int64_t by = (int64_t)num_sms * 8 / bx;
+    if (by > g.ny) by = g.ny;
+    if (by > 65535) by = 65535;
+    return dim3((unsigned)bx, (unsigned)(by > 0 ? by : 1));
+}
+
 int grid_blocks(int64_t n, int num_sms)
 {
     int64_t b = (n + kPicBlock - 1) / kPicBlock;
@@ -119,14 +133,18 @@ int grid_blocks(int64_t n, int num_sms)
 
 cudaError_t launch_yee_b(const YeeGrid &g, double dtb, int num_sms, cudaStream_t st)
 {
-    k_yee_b<<<grid_blocks(g.nx * g.ny, num_sms), kPicBlock, 0, st>>>(g, (float)dtb);
+    // 1/dx and 1/dy once, as each node would form them (FP64 quotient to float)
+    k_yee_b<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, (float)(1.0 / g.dx),
+                                                         (float)(1.0 / g.dy), (float)dtb);
     return cudaGetLastError();
 }
 
 cudaError_t launch_yee_e(const YeeGrid &g, const float *jx, const float *jy, const float *jz,
                          double dt, int num_sms, cudaStream_t st)
 {
-    k_yee_e<<<grid_blocks(g.nx * g.ny, num_sms), kPicBlock, 0, st>>>(g, jx, jy, jz, (float)dt);
+    k_yee_e<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, (float)(1.0 / g.dx),
+                                                         (float)(1.0 / g.dy), jx, jy, jz,
+                                                         (float)dt);
     return cudaGetLastError();
 }
 
