@@ -307,12 +307,19 @@ def fused_leg(dev, flush, warmup: int):
         for _ in range(max(1, warmup)):
             job(False)
             job(True)
-        t1, tf = job(False), job(True)
+        t1 = job(False)
+        Q.qp_profile_enable(ctx, True)
+        tf = job(True)
+        win_ms, wins = Q.qp_profile_read(ctx)
+        Q.qp_profile_enable(ctx, False)
         out[prec] = {"single_steps": {"value": round(slots / (t1 * 1e-3), 1), "unit": UNIT,
                                       "ms_per_step": round(t1 / n_steps, 5)},
                      "fused": {"value": round(slots / (tf * 1e-3), 1), "unit": UNIT,
                                "ms_per_step": round(tf / n_steps, 5)},
                      "speedup": round(t1 / tf, 3),
+                     "roofline": issue_roofline(
+                         measured_instructions("k_fused_plane_wave.md", prec), win_ms[0],
+                         int(wins[0]), torch.cuda.get_device_properties(dev).multi_processor_count),
                      "status": sim.diagnostics("electron").status}
         sim.close()
         del sim
@@ -364,6 +371,47 @@ def measured_traffic(profile: str, precision: str):
                 alg = int(m.group(4)) if m.group(4) else None
                 return int(m.group(2)), int(m.group(3)), alg
     return None
+
+
+SM_MAX_MHZ = 2070.0     # GB300's maximum SM clock
+ISSUE_PER_SM_CYCLE = 4  # warp instructions an SM issues a cycle (4 schedulers)
+
+
+def measured_instructions(profile: str, precision: str):
+    """Warp instructions of one fused window from the committed ncu summary,
+    when it was taken on the current step-kernel sources; else None."""
+    import re
+    path = os.path.join(PROFILES, profile)
+    if not os.path.exists(path):
+        return None
+    sid = kernel_source_id()
+    pat = re.compile(r"^instructions, (\w+): (\d+) warp instructions per window, "
+                     r"kernel source ([0-9a-f]{12})")
+    with open(path) as f:
+        for line in f:
+            m = pat.match(line.strip())
+            if m and m.group(1) == precision and m.group(3) == sid:
+                return int(m.group(2))
+    return None
+
+
+def issue_roofline(instructions, window_ms, windows, sms):
+    """The fused window's bound: instruction issue (it keeps the particles in
+    registers; its DRAM traffic is negligible).  achieved = warp instructions
+    of k_fused in one window (ncu) / the window's device time (CUDA events
+    around its launches); peak = SMs x 4 schedulers x the maximum SM clock."""
+    peak = sms * ISSUE_PER_SM_CYCLE * SM_MAX_MHZ * 1e6 / 1e9
+    out = {"kernel": "k_fused", "bound": "alu", "unit": "G warp-instructions/s",
+           "peak": round(peak, 1),
+           "peak_source": f"{sms} SMs x {ISSUE_PER_SM_CYCLE} warp instructions a cycle x "
+                          f"{SM_MAX_MHZ:.0f} MHz",
+           "window_us": round(window_ms * 1e3 / max(windows, 1), 2), "achieved": None,
+           "frac": None, "instructions_per_window": instructions}
+    if instructions and window_ms > 0:
+        achieved = instructions / (window_ms / max(windows, 1) * 1e-3) / 1e9
+        out["achieved"] = round(achieved, 2)
+        out["frac"] = round(achieved / peak, 4)
+    return out
 
 
 def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):

@@ -74,3 +74,19 @@ def test_all_core_oracle_steps_the_same_particles_as_one_core():
     slots1, _, n1 = bench.oracle_sample(w, 96, 3, 16)
     slots2, _, n2 = bench.oracle_all_cores(spec, 96, 3, 16, 2)
     assert n1 == n2 == 96 and slots1 == slots2
+
+
+def test_fused_window_issue_roofline(tmp_path, monkeypatch):
+    sid = bench.kernel_source_id()
+    (tmp_path / "k_fused_x.md").write_text(
+        f"instructions, mixed: 1000000 warp instructions per window, kernel source {sid}\n"
+        "instructions, fp64: 5 warp instructions per window, kernel source 000000000000\n")
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    assert bench.measured_instructions("k_fused_x.md", "mixed") == 1_000_000
+    assert bench.measured_instructions("k_fused_x.md", "fp64") is None
+    # 152 SMs x 4 a cycle x 2070 MHz = 1258.56 G warp-instructions/s peak;
+    # 1e6 instructions in a 1 ms window: 1 G/s achieved
+    r = bench.issue_roofline(1_000_000, 2.0, 2, 152)
+    assert r["bound"] == "alu" and r["peak"] == 1258.6
+    assert r["achieved"] == 1.0 and r["frac"] == round(1.0 / 1258.56, 4)
+    assert bench.issue_roofline(None, 2.0, 2, 152)["frac"] is None
