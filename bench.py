@@ -453,10 +453,12 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
 
 
 def e2e(w, precision, steps, dev):
-    """End to end through the public API with host buffers: every step copies
-    the live particles and the live counts from pinned host memory to the
-    device (qp_species_copy: one strided copy per species), runs qp_step,
-    and reads the new counts and then the new state back."""
+    """End to end through the public API with the state in host memory: every
+    step is one qp_step_host call, which copies the live particles and
+    counts from pinned host blocks to the device, runs the step, reads the
+    new counts back and copies the new state back into the host blocks
+    (and synchronises).  The bytes are the arrays of the live slots each
+    way plus the counts."""
     import torch
 
     from paper_1311_1107_gb300 import qedpic as Q
@@ -468,41 +470,30 @@ def e2e(w, precision, steps, dev):
     names = ("electron", "positron", "photon")
     host = {n: torch.empty(sim.species[n].block.shape, dtype=torch.float64, pin_memory=True)
             for n in names}
-    counts_h = torch.empty(3, dtype=torch.int64, pin_memory=True)
+    rows = {n: host[n].shape[0] for n in names}
     stream = torch.cuda.current_stream()
     st = stream_handle(stream)
-    counts_h.copy_(sim.counts)
-    live = dict(zip(names, (int(v) for v in counts_h.tolist())))
+    live = sim.live_counts()
     for n in names:
         sim.species[n].copy_state(host[n], live[n], False, st)
     torch.cuda.synchronize()
+    states = sim.host_states(host, live)
     h2d = d2h = 0
     total_slots = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        for n in names:
-            if live[n]:
-                sim.species[n].copy_state(host[n], live[n], True, st)
-                h2d += live[n] * 8 * host[n].shape[0]
-        sim.counts.copy_(counts_h, non_blocking=True)
-        h2d += 24
-        total_slots += sum(live.values())
-        sim.run(1, stream)
-        counts_h.copy_(sim.counts, non_blocking=True)
-        d2h += 24
-        stream.synchronize()
-        live = dict(zip(names, (int(v) for v in counts_h.tolist())))
-        for n in names:
-            if live[n]:
-                sim.species[n].copy_state(host[n], live[n], False, st)
-                d2h += live[n] * 8 * host[n].shape[0]
-        stream.synchronize()
+        before = [int(states[k].count) for k in range(3)]
+        total_slots += sum(before)
+        h2d += sum(c * 8 * rows[n] + 8 for c, n in zip(before, names))
+        sim.run_host(states, 1, stream)
+        d2h += sum(int(states[k].count) * 8 * rows[n] + 8 for k, n in enumerate(names))
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     Q.qp_destroy(ctx)
     return {"value": round(total_slots / wall, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
-            "steps": steps, "precision": precision}
+            "steps": steps, "precision": precision,
+            "api": "qp_step_host: host state copied in, stepped, copied back, one call a step"}
 
 
 # ----------------------------------------------------------------------------- serving

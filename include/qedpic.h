@@ -230,6 +230,35 @@ typedef struct {
  */
 int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream);
 
+/* One species' state in host memory, for qp_step_host. */
+typedef struct qp_host_state {
+    void *host;      /* block: array k of (x, y, [z if dims == 3], ux, uy, uz, tau, w)
+                        at byte k * pitch; pinned memory copies fastest            */
+    int64_t pitch;   /* bytes between arrays: >= 8 * capacity, a multiple of 8     */
+    int64_t count;   /* in: live slots to step; out: live slots after the steps    */
+} qp_host_state;
+
+/*
+ * qp_step for a caller whose state lives in host memory: for each species
+ * named in s (electron, positron, photon: st[0..2]; entries of absent
+ * species are ignored), slots [0, st[k].count) are copied from st[k].host
+ * to the device arrays and the live count set; s->n_steps steps run as
+ * qp_step runs them; the new live counts are read back into st[k].count and
+ * slots [0, count) of every array are copied back into st[k].host (the
+ * slots live before the steps as soon as they are done: a step never lowers
+ * a live count, since decayed photons keep their slots; the appended ones
+ * once the counts are read).  The call synchronises `stream` once, or twice
+ * when the steps appended particles, and returns when the host blocks hold
+ * the result.  Per-particle event
+ * counts and chi are left on the device (qp_diagnostics).  Returns what
+ * qp_step returns, or QP_ERR_INVALID_ARG (nothing enqueued) for st == NULL,
+ * a null host block, a count outside [0, capacity] or a pitch below 8 *
+ * capacity.  No counterpart in the paper: the host I/O of qp_species_copy
+ * and a step in one call, so that a step of host-resident state costs one
+ * call of the library.
+ */
+int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *stream);
+
 /*
  * Fused steps: the s->n_steps steps of qp_step, `fuse` steps per launch
  * window, every lepton held in registers from the first step of a window to

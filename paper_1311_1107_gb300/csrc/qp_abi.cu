@@ -64,6 +64,7 @@ struct qp_ctx {
     void *d_coal = nullptr;           // scratch of qp_coalesce_photons
     size_t coal_bytes = 0;
     long long *d_coal_stats = nullptr;  // [4] of the last coalescence
+    long long *h_counts = nullptr;    // [3] pinned: live counts of qp_step_host
     std::vector<SpeciesRec> species;
     int grid_cache[2][2][5];          // [batch][precision][field] blocks per SM, 0 = unknown
     // kernel timing (qp_profile_*): event pool and (kernel, start event) records
@@ -135,6 +136,7 @@ void release(qp_ctx *c)
     cudaFree(c->d_coal);
     cudaFree(c->d_coal_stats);
     cudaFree(c->d_fuse);
+    cudaFreeHost(c->h_counts);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -401,15 +403,13 @@ int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t fi
                                            d.id_append, seed, d.kind, (cudaStream_t)stream));
 }
 
-int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch, int64_t count,
-                    int32_t to_device, void *stream)
+// Slots [first, first + count) of a species' FP64 arrays between the device
+// and a host block (array k at byte k * host_pitch; slot j at byte 8 j of
+// its row); the caller has checked the range and made the device current.
+static cudaError_t copy_slots(const qp_species_desc &d, void *host, int64_t host_pitch,
+                              int64_t first, int64_t count, int32_t to_device, cudaStream_t st)
 {
-    if (!ctx) return QP_ERR_NOT_INITIALIZED;
-    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
-    const qp_species_desc &d = ctx->species[handle].d;
-    if (!host || count < 0 || count > d.capacity || host_pitch < 8 * count || host_pitch % 8)
-        return QP_ERR_INVALID_ARG;
-    if (count == 0) return QP_OK;
+    if (count == 0) return cudaSuccess;
     double *arr[8];
     int na = 0;
     arr[na++] = d.x;
@@ -420,28 +420,113 @@ int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch,
     arr[na++] = d.uz;
     arr[na++] = d.tau;
     arr[na++] = d.w;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return QP_ERR_CUDA;
-    const cudaStream_t st = (cudaStream_t)stream;
     const size_t width = (size_t)count * sizeof(double);
+    char *h0 = (char *)host + (size_t)first * sizeof(double);
     // device arrays at a constant pitch (one allocation): one strided copy
     const ptrdiff_t dpitch = (char *)arr[1] - (char *)arr[0];
     bool strided = dpitch >= (ptrdiff_t)width;
     for (int k = 2; k < na && strided; ++k) strided = (char *)arr[k] - (char *)arr[k - 1] == dpitch;
     cudaError_t e = cudaSuccess;
     if (strided) {
-        e = to_device ? cudaMemcpy2DAsync(arr[0], (size_t)dpitch, host, (size_t)host_pitch, width,
+        double *d0 = arr[0] + first;
+        e = to_device ? cudaMemcpy2DAsync(d0, (size_t)dpitch, h0, (size_t)host_pitch, width,
                                           (size_t)na, cudaMemcpyHostToDevice, st)
-                      : cudaMemcpy2DAsync(host, (size_t)host_pitch, arr[0], (size_t)dpitch, width,
+                      : cudaMemcpy2DAsync(h0, (size_t)host_pitch, d0, (size_t)dpitch, width,
                                           (size_t)na, cudaMemcpyDeviceToHost, st);
     } else {
         for (int k = 0; k < na && e == cudaSuccess; ++k) {
-            char *h = (char *)host + (size_t)k * (size_t)host_pitch;
-            e = to_device ? cudaMemcpyAsync(arr[k], h, width, cudaMemcpyHostToDevice, st)
-                          : cudaMemcpyAsync(h, arr[k], width, cudaMemcpyDeviceToHost, st);
+            char *h = h0 + (size_t)k * (size_t)host_pitch;
+            e = to_device ? cudaMemcpyAsync(arr[k] + first, h, width, cudaMemcpyHostToDevice, st)
+                          : cudaMemcpyAsync(h, arr[k] + first, width, cudaMemcpyDeviceToHost, st);
         }
     }
-    return cuda_status(e);
+    return e;
+}
+
+int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch, int64_t count,
+                    int32_t to_device, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!valid_handle(ctx, handle)) return QP_ERR_NOT_INITIALIZED;
+    const qp_species_desc &d = ctx->species[handle].d;
+    if (!host || count < 0 || count > d.capacity || host_pitch < 8 * count || host_pitch % 8)
+        return QP_ERR_INVALID_ARG;
+    if (count == 0) return QP_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    return cuda_status(copy_slots(d, host, host_pitch, 0, count, to_device, (cudaStream_t)stream));
+}
+
+int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *stream)
+{
+    if (!ctx) return QP_ERR_NOT_INITIALIZED;
+    if (!s || !st) return QP_ERR_INVALID_ARG;
+    const int32_t hs[3] = {s->electron, s->positron, s->photon};
+    for (int k = 0; k < 3; ++k) {
+        if (hs[k] == -1) continue;
+        if (!valid_handle(ctx, hs[k])) return QP_ERR_NOT_INITIALIZED;
+        const qp_species_desc &d = ctx->species[hs[k]].d;
+        if (!st[k].host || st[k].count < 0 || st[k].count > d.capacity ||
+            st[k].pitch < 8 * d.capacity || st[k].pitch % 8)
+            return QP_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return QP_ERR_CUDA;
+    if (!ctx->h_counts) {
+        cudaError_t e = cudaMallocHost((void **)&ctx->h_counts, 3 * sizeof(long long));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    const cudaStream_t cs = (cudaStream_t)stream;
+    long long *hc = ctx->h_counts;
+    // every return leaves no copy of the pinned counts pending (an error
+    // after something was enqueued synchronises first)
+    auto fail = [&](int r) {
+        (void)cudaStreamSynchronize(cs);
+        return r;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3; ++k) {
+        if (hs[k] == -1) continue;
+        const qp_species_desc &d = ctx->species[hs[k]].d;
+        hc[k] = st[k].count;
+        e = copy_slots(d, st[k].host, st[k].pitch, 0, st[k].count, 1, cs);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        e = cudaMemcpyAsync(d.n_live, hc + k, sizeof(long long), cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+    }
+    const int st_step = qp_step(ctx, s, stream);
+    if (st_step < 0) return fail(st_step);
+    // a step never lowers a live count (decayed photons keep their slots):
+    // the slots live before it go back at once, behind the step on the
+    // stream; only the appended ones wait for the new counts
+    for (int k = 0; k < 3; ++k) {
+        if (hs[k] == -1) continue;
+        const qp_species_desc &d = ctx->species[hs[k]].d;
+        e = copy_slots(d, st[k].host, st[k].pitch, 0, st[k].count, 0, cs);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        e = cudaMemcpyAsync(hc + k, d.n_live, sizeof(long long), cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+    }
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_status(e);
+    bool more = false;
+    for (int k = 0; k < 3; ++k) {
+        if (hs[k] == -1) continue;
+        const qp_species_desc &d = ctx->species[hs[k]].d;
+        const long long before = st[k].count, after = hc[k];
+        if (after < before || after > d.capacity) return QP_ERR_CUDA;  // not a step's counts
+        st[k].count = after;
+        if (after > before) {
+            e = copy_slots(d, st[k].host, st[k].pitch, before, after - before, 0, cs);
+            if (e != cudaSuccess) return fail(cuda_status(e));
+            more = true;
+        }
+    }
+    if (more) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return st_step;
 }
 
 namespace {

@@ -66,6 +66,10 @@ class qp_step_params(C.Structure):
                 ("positron", C.c_int32), ("photon", C.c_int32), ("reserved", C.c_int32)]
 
 
+class qp_host_state(C.Structure):
+    _fields_ = [("host", C.c_void_p), ("pitch", C.c_int64), ("count", C.c_int64)]
+
+
 class qp_diag(C.Structure):
     _fields_ = ([("n_live", C.c_int64), ("n_alive", C.c_int64)]
                 + [(n, C.c_double) for n in ("weight", "energy", "px", "py", "pz", "chi_mean")]
@@ -120,7 +124,7 @@ class qp_coalesce_stats(C.Structure):
 
 
 EXPORTS = ("qp_init_tables", "qp_destroy", "qp_create_species", "qp_init_optical_depth",
-           "qp_species_copy",
+           "qp_species_copy", "qp_step_host",
            "qp_step", "qp_diagnostics", "qp_export_tables", "qp_reset_counters",
            "qp_selftest_wait_timeout", "qp_profile_enable", "qp_profile_read",
            "qp_diagnostics_noalloc", "qp_status_string", "qp_destroy_species",
@@ -153,6 +157,7 @@ def lib(build_if_missing: bool = False):
         L.qp_create_species.argtypes = [vp, C.POINTER(qp_species_desc), C.POINTER(i32)]
         L.qp_init_optical_depth.argtypes = [vp, i32, C.c_uint64, i64, i64, vp]
         L.qp_species_copy.argtypes = [vp, i32, vp, i64, i64, i32, vp]
+        L.qp_step_host.argtypes = [vp, C.POINTER(qp_step_params), C.POINTER(qp_host_state), vp]
         L.qp_step.argtypes = [vp, C.POINTER(qp_step_params), vp]
         L.qp_diagnostics.argtypes = [vp, i32, C.POINTER(qp_diag), vp]
         L.qp_diagnostics_noalloc.argtypes = [C.POINTER(qp_species_desc), C.POINTER(qp_diag), vp]
@@ -230,6 +235,13 @@ def qp_species_copy(ctx, handle: int, host_ptr: int, host_pitch: int, count: int
     return _check("qp_species_copy",
                   lib().qp_species_copy(ctx, handle, host_ptr, host_pitch, count,
                                         1 if to_device else 0, stream))
+
+
+def qp_step_host(ctx, params: qp_step_params, states, stream=None) -> int:
+    """params.n_steps steps of state held in host blocks: states is a
+    qp_host_state[3] array (electron, positron, photon); their counts are
+    updated to the live counts after the steps."""
+    return _check("qp_step_host", lib().qp_step_host(ctx, C.byref(params), states, stream))
 
 
 def qp_step(ctx, params: qp_step_params, stream=None) -> int:

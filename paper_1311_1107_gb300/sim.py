@@ -246,6 +246,28 @@ class Simulation:
         self.step_index += int(n_steps)
         return st
 
+    def host_states(self, host: dict, counts: dict):
+        """qp_host_state[3] over host blocks shaped like the species' blocks
+        (pinned tensors, array k in row k) holding counts[name] live slots."""
+        arr = (Q.qp_host_state * 3)()
+        for k, name in enumerate(("electron", "positron", "photon")):
+            h = host[name]
+            arr[k].host = h.data_ptr()
+            arr[k].pitch = h.stride(0) * h.element_size()
+            arr[k].count = int(counts[name])
+        return arr
+
+    def run_host(self, states, n_steps: int = 1, stream=None) -> int:
+        """n_steps steps of state held in host blocks (qp_step_host): copied
+        in, stepped, copied back; states[k].count become the new counts."""
+        if self.pulse is not None or self.pic_pulse is not None:
+            raise ValueError("run_host steps a workload with given fields only")
+        self.params.step = self.step_index
+        self.params.n_steps = int(n_steps)
+        st = Q.qp_step_host(self.ctx, self.params, states, stream_handle(stream))
+        self.step_index += int(n_steps)
+        return st
+
     def diagnostics(self, name: str, stream=None) -> Q.qp_diag:
         return Q.qp_diagnostics(self.ctx, self.species[name].handle, stream_handle(stream))
 

@@ -56,7 +56,8 @@ def test_struct_layouts_match_header(tmp_path):
                "qp_field": Q.qp_field, "qp_step_params": Q.qp_step_params,
                "qp_diag": Q.qp_diag, "qp_tables_export": Q.qp_tables_export,
                "qp_coalesce_params": Q.qp_coalesce_params,
-               "qp_coalesce_stats": Q.qp_coalesce_stats, "qp_pulse2d": Q.qp_pulse2d}
+               "qp_coalesce_stats": Q.qp_coalesce_stats, "qp_pulse2d": Q.qp_pulse2d,
+               "qp_host_state": Q.qp_host_state}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qedpic.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
@@ -112,6 +113,8 @@ def test_arguments_rejected_before_any_device_work(lib):
     assert lib.qp_batch_progress(None, None, None, None, None) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_batch_destroy(None) == Q.QP_ERR_NOT_INITIALIZED
     assert lib.qp_species_copy(None, 0, None, 8, 1, 1, None) == Q.QP_ERR_NOT_INITIALIZED
+    hs = (Q.qp_host_state * 3)()
+    assert lib.qp_step_host(None, C.byref(s), hs, None) == Q.QP_ERR_NOT_INITIALIZED
 
 
 def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
