@@ -81,8 +81,9 @@ __device__ __forceinline__ void chunk_of(long long n, long long *beg, long long 
     if (*beg > n) *beg = n;
 }
 
+// e: the photon's energy |u| (sqrt(ux ux + uy uy + uz uz), formed by the caller)
 __device__ unsigned long long group_key(const CoParams &C, double x, double y, double z, double ux,
-                                        double uy, double uz)
+                                        double uy, double uz, double e)
 {
     const double gx = floor((x - C.x0) / C.dx);
     const double gy = floor((y - C.y0) / C.dy);
@@ -90,7 +91,6 @@ __device__ unsigned long long group_key(const CoParams &C, double x, double y, d
     if (!(gx >= 0.0 && gx < (double)C.nx && gy >= 0.0 && gy < (double)C.ny && gz >= 0.0 &&
           gz < (double)C.nz))
         return C.nomerge;
-    const double e = sqrt(ux * ux + uy * uy + uz * uz);
     const unsigned long long eb = (unsigned long long)__double_as_longlong(e);
     const unsigned long long ex = (eb >> 52) & 0x7FFull;
     if (ex == 0ull || ex == 0x7FFull) return C.nomerge;
@@ -124,7 +124,8 @@ __device__ unsigned long long group_key(const CoParams &C, double x, double y, d
 __global__ void __launch_bounds__(kCoThreads) k_co_prepare(SpeciesDev S, CoParams C,
                                                            unsigned long long *keys,
                                                            unsigned *vals, unsigned char *role,
-                                                           long long *counts, int *status)
+                                                           double *en, long long *counts,
+                                                           int *status)
 {
     const long long n = live_count(S, status);
     if (blockIdx.x == 0 && threadIdx.x == 0) counts[0] = n;
@@ -133,9 +134,14 @@ __global__ void __launch_bounds__(kCoThreads) k_co_prepare(SpeciesDev S, CoParam
         const bool alive = S.tau[i] >= 0.0;
         role[i] = alive ? 1 : 0;
         if (C.merge) {
-            keys[i] = alive ? group_key(C, S.x[i], S.y[i], S.z ? S.z[i] : 0.0, S.ux[i], S.uy[i],
-                                        S.uz[i])
-                            : C.nomerge;
+            unsigned long long key = C.nomerge;
+            if (alive) {
+                const double ux = S.ux[i], uy = S.uy[i], uz = S.uz[i];
+                const double e = sqrt(ux * ux + uy * uy + uz * uz);
+                en[i] = e;  // the merge sums these energies
+                key = group_key(C, S.x[i], S.y[i], S.z ? S.z[i] : 0.0, ux, uy, uz, e);
+            }
+            keys[i] = key;
             vals[i] = (unsigned)i;
         }
     }
@@ -284,15 +290,17 @@ struct GroupSums {
     double W, E, P[3], X[3];
 };
 
-__device__ GroupSums group_sums(const SpeciesDev &S, const unsigned *vals, long long a,
-                                long long b)
+// The sums of a run [a, b) of the sorted order, member by member in slot
+// order; en: the members' energies |u| from k_co_prepare.
+__device__ GroupSums group_sums(const SpeciesDev &S, const double *en, const unsigned *vals,
+                                long long a, long long b)
 {
     GroupSums g{0.0, 0.0, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
     for (long long k = a; k < b; ++k) {
         const unsigned i = vals[k];
         const double w = S.w[i];
         const double ux = S.ux[i], uy = S.uy[i], uz = S.uz[i];
-        const double e = sqrt(ux * ux + uy * uy + uz * uz);
+        const double e = en[i];
         g.W = g.W + w;
         g.E = g.E + w * e;
         g.P[0] = g.P[0] + w * ux;
@@ -339,10 +347,12 @@ __global__ void __launch_bounds__(kCoThreads) k_co_groups(CoParams C,
     }
 }
 
-// One thread a run: a run whose momentum vanishes is kept as it is, the
-// others become pairs (role 2 at the first member, 0 at the others).
-__global__ void __launch_bounds__(kCoThreads) k_co_runs(SpeciesDev S, const unsigned *vals,
-                                                        const uint2 *runs, unsigned char *role,
+// One thread a run: its sums, kept for k_co_pairs; a run whose momentum
+// vanishes is kept as it is, the others become pairs (role 2 at the first
+// member, 0 at the others).
+__global__ void __launch_bounds__(kCoThreads) k_co_runs(SpeciesDev S, const double *en,
+                                                        const unsigned *vals, const uint2 *runs,
+                                                        unsigned char *role, GroupSums *rsum,
                                                         const long long *counts,
                                                         long long *stats)
 {
@@ -350,13 +360,9 @@ __global__ void __launch_bounds__(kCoThreads) k_co_runs(SpeciesDev S, const unsi
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += stride) {
         const uint2 run = runs[r];
-        double P[3] = {0.0, 0.0, 0.0};
-        for (unsigned k = run.x; k < run.y; ++k) {
-            const unsigned i = vals[k];
-            P[0] = P[0] + S.w[i] * S.ux[i];
-            P[1] = P[1] + S.w[i] * S.uy[i];
-            P[2] = P[2] + S.w[i] * S.uz[i];
-        }
+        const GroupSums g = group_sums(S, en, vals, run.x, run.y);
+        rsum[r] = g;
+        const double *P = g.P;
         if (!(P[0] * P[0] + P[1] * P[1] + P[2] * P[2] > 0.0)) continue;
         for (unsigned k = run.x; k < run.y; ++k) role[vals[k]] = 0;
         role[vals[run.x]] = 2;  // the sorted run is in slot order: its first
@@ -450,6 +456,7 @@ __global__ void __launch_bounds__(kCoThreads) k_co_kept(SpeciesDev S, const unsi
 __global__ void __launch_bounds__(kCoThreads) k_co_pairs(SpeciesDev S, CoParams C,
                                                          const unsigned *vals, const uint2 *runs,
                                                          const unsigned char *role,
+                                                         const GroupSums *rsum,
                                                          const unsigned *off, Stage st,
                                                          const long long *counts)
 {
@@ -459,7 +466,7 @@ __global__ void __launch_bounds__(kCoThreads) k_co_pairs(SpeciesDev S, CoParams 
         const uint2 run = runs[q];
         const unsigned anchor = vals[run.x];
         if (role[anchor] != 2) continue;
-        const GroupSums g = group_sums(S, vals, run.x, run.y);
+        const GroupSums g = rsum[q];
         const double W = g.W;
         const double eps = g.E / W;
         const double c[3] = {g.P[0] / W, g.P[1] / W, g.P[2] / W};
@@ -582,7 +589,8 @@ size_t coalesce_scratch_bytes(int64_t cap, int grid)
 {
     const size_t c = (size_t)(cap > 0 ? cap : 1);
     return 2 * c * 8 + 2 * c * 4 + c + c * 4 + c * 9 * 8 + c * 4 +
-           ((size_t)kRadix * grid + grid + 64) * 4 + 16 * 8 + (c / 3 + 1) * 8 + 32 * 256;
+           ((size_t)kRadix * grid + grid + 64) * 4 + 16 * 8 + (c / 3 + 1) * 8 +
+           (c / 3 + 1) * sizeof(GroupSums) + 32 * 256;
 }
 
 namespace {
@@ -598,6 +606,7 @@ struct CoScratch {
     unsigned *hist, *chunk;
     long long *counts;
     uint2 *runs;
+    GroupSums *rsum;  // the sums of each run (k_co_runs, for k_co_pairs)
 };
 
 CoScratch carve(void *scratch, int64_t cap, int grid)
@@ -622,6 +631,7 @@ CoScratch carve(void *scratch, int64_t cap, int grid)
     s.chunk = (unsigned *)take((size_t)grid * 4 + 64);
     s.counts = (long long *)take(16 * 8);
     s.runs = (uint2 *)take((c / 3 + 1) * sizeof(uint2));
+    s.rsum = (GroupSums *)take((c / 3 + 1) * sizeof(GroupSums));
     return s;
 }
 
@@ -640,6 +650,9 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
     unsigned *chunk = cs.chunk;
     long long *counts = cs.counts;
     uint2 *runs = cs.runs;
+    // the photons' energies (k_co_prepare to k_co_runs) in the chi staging
+    // array, which k_co_kept and k_co_pairs write only after k_co_runs
+    double *en = stg.f[8];
 
     CoParams C{};
     int passes = 0;
@@ -675,7 +688,7 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(stats, 0, 4 * 8, st);
     if (e != cudaSuccess) return e;
-    k_co_prepare<<<grid, kCoThreads, 0, st>>>(S, C, keys[0], vals[0], role, counts, status);
+    k_co_prepare<<<grid, kCoThreads, 0, st>>>(S, C, keys[0], vals[0], role, en, counts, status);
     int cur = 0;
     for (int ps = 0; ps < passes; ++ps) {
         k_co_hist<<<grid, kCoThreads, 0, st>>>(keys[cur], 8 * ps, hist, counts);
@@ -686,14 +699,16 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
     }
     if (passes) {
         k_co_groups<<<grid, kCoThreads, 0, st>>>(C, keys[cur], counts, runs);
-        k_co_runs<<<grid, kCoThreads, 0, st>>>(S, vals[cur], runs, role, counts, stats);
+        k_co_runs<<<grid, kCoThreads, 0, st>>>(S, en, vals[cur], runs, role, cs.rsum, counts,
+                                                stats);
     }
     k_co_chunk_sums<<<grid, kCoThreads, 0, st>>>(role, chunk, counts);
     k_co_scan<<<1, 1024, 0, st>>>(chunk, grid, counts + 1);
     k_co_offsets<<<grid, kCoThreads, 0, st>>>(role, chunk, off, counts);
     k_co_kept<<<grid, kCoThreads, 0, st>>>(S, role, off, stg, counts);
     if (passes) {
-        k_co_pairs<<<grid, kCoThreads, 0, st>>>(S, C, vals[cur], runs, role, off, stg, counts);
+        k_co_pairs<<<grid, kCoThreads, 0, st>>>(S, C, vals[cur], runs, role, cs.rsum, off, stg,
+                                                 counts);
     }
     k_co_copy_back<<<grid, kCoThreads, 0, st>>>(S, stg, counts, stats);
     return cudaGetLastError();
