@@ -491,15 +491,15 @@ int qp_sort_species(qp_ctx *ctx, int32_t handle, const qp_field *grid, void *str
 
 /* Grid and bins of qp_coalesce_photons.  A live photon belongs to the group
  * of (cell, energy bin, direction bin):
- *   cell        floor((x - x0)/dx), floor((y - y0)/dy), floor((z - z0)/dz)
+ *   cell        floor((x - x0) (1/dx)), floor((y - y0) (1/dy)), floor((z - z0) (1/dz))
  *               (z cell 0 for dims 2), each in [0, n); photons outside the
  *               box are never merged;
  *   energy bin  the binary exponent of |u| and its leading log2(E) mantissa
  *               bits (E = energy_bins_per_octave bins per octave, linear in
  *               |u| within the octave);
  *   direction   the dominant axis of u with its sign (a face of a cube) and
- *               the two other components over the dominant one, each in D =
- *               direction_bins bins over [-1, 1].
+ *               the two other components times 1/|dominant component|, each
+ *               in D = direction_bins bins over [-1, 1].
  * Every decision is an exact FP64 operation or a bit extraction, so the CPU
  * oracle forms the same groups. */
 typedef struct {

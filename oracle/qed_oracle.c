@@ -1125,9 +1125,10 @@ static int or_log2i(int v)
 static uint64_t or_coalesce_key(const or_coalesce_params *C, double x, double y, double z,
                                 double ux, double uy, double uz)
 {
-    double gx = floor((x - C->x0) / C->dx);
-    double gy = floor((y - C->y0) / C->dy);
-    double gz = C->dims == 3 ? floor((z - C->z0) / C->dz) : 0.0;
+    /* cell: the offset times the reciprocal of the cell size */
+    double gx = floor((x - C->x0) * (1.0 / C->dx));
+    double gy = floor((y - C->y0) * (1.0 / C->dy));
+    double gz = C->dims == 3 ? floor((z - C->z0) * (1.0 / C->dz)) : 0.0;
     if (!(gx >= 0.0 && gx < (double)C->nx && gy >= 0.0 && gy < (double)C->ny && gz >= 0.0 &&
           gz < (double)C->nz))
         return OR_NOMERGE;
@@ -1146,8 +1147,9 @@ static uint64_t or_coalesce_key(const or_coalesce_params *C, double x, double y,
     if (fabs(u[1]) > fabs(u[f])) f = 1;
     if (fabs(u[2]) > fabs(u[f])) f = 2;
     int face = 2 * f + (u[f] < 0.0 ? 1 : 0);
-    double a = u[(f + 1) % 3] / fabs(u[f]);
-    double b = u[(f + 2) % 3] / fabs(u[f]);
+    double r = 1.0 / fabs(u[f]);
+    double a = u[(f + 1) % 3] * r;
+    double b = u[(f + 2) % 3] * r;
     int64_t D = C->dir_bins;
     int64_t ia = (int64_t)floor((a + 1.0) * (0.5 * (double)D));
     int64_t ib = (int64_t)floor((b + 1.0) * (0.5 * (double)D));

@@ -49,6 +49,7 @@ constexpr int kRngCoalesce = 5;
 
 struct CoParams {
     double x0, y0, z0, dx, dy, dz;
+    double idx, idy, idz;  // 1/dx, 1/dy, 1/dz
     long long nx, ny, nz;
     int lb;            // log2 of energy bins per octave
     int D;             // direction bins per face axis
@@ -85,9 +86,10 @@ __device__ __forceinline__ void chunk_of(long long n, long long *beg, long long 
 __device__ unsigned long long group_key(const CoParams &C, double x, double y, double z, double ux,
                                         double uy, double uz, double e)
 {
-    const double gx = floor((x - C.x0) / C.dx);
-    const double gy = floor((y - C.y0) / C.dy);
-    const double gz = C.dims == 3 ? floor((z - C.z0) / C.dz) : 0.0;
+    // cell: the offset times the reciprocal of the cell size (formed on the host)
+    const double gx = floor((x - C.x0) * C.idx);
+    const double gy = floor((y - C.y0) * C.idy);
+    const double gz = C.dims == 3 ? floor((z - C.z0) * C.idz) : 0.0;
     if (!(gx >= 0.0 && gx < (double)C.nx && gy >= 0.0 && gy < (double)C.ny && gz >= 0.0 &&
           gz < (double)C.nz))
         return C.nomerge;
@@ -100,8 +102,9 @@ __device__ unsigned long long group_key(const CoParams &C, double x, double y, d
     if (fabs(u[1]) > fabs(u[f])) f = 1;
     if (fabs(u[2]) > fabs(u[f])) f = 2;
     const int face = 2 * f + (u[f] < 0.0 ? 1 : 0);
-    const double a = u[(f + 1) % 3] / fabs(u[f]);
-    const double b = u[(f + 2) % 3] / fabs(u[f]);
+    const double r = 1.0 / fabs(u[f]);
+    const double a = u[(f + 1) % 3] * r;
+    const double b = u[(f + 2) % 3] * r;
     const long long D = C.D;
     long long ia = (long long)floor((a + 1.0) * (0.5 * (double)D));
     long long ib = (long long)floor((b + 1.0) * (0.5 * (double)D));
@@ -663,6 +666,9 @@ cudaError_t launch_coalesce(const SpeciesDev &S, const qp_coalesce_params *P, vo
         C.dx = P->dx;
         C.dy = P->dy;
         C.dz = P->dz;
+        C.idx = 1.0 / P->dx;
+        C.idy = 1.0 / P->dy;
+        C.idz = P->dz > 0.0 ? 1.0 / P->dz : 0.0;  // used with dims 3 only
         C.nx = P->nx;
         C.ny = P->ny;
         C.nz = P->nz;
