@@ -92,6 +92,26 @@ def test_fused_windows_give_the_same_bits_as_single_steps(ctx, case, precision):
           f"{da['electron'].n_emit} emissions: fused = single steps")
 
 
+@pytest.mark.parametrize("n", [0, 33])
+def test_fused_empty_and_ragged_populations(ctx, n):
+    # no leptons at all (nothing to step, nothing appended) and two tiles,
+    # the second holding one lepton: the same bits as single steps
+    w = W.plane_wave_collision(n=n, n_steps=60)
+    ref = Simulation(w, precision="mixed", ctx=ctx)
+    ref.run(60)
+    a, da = _state(ref)
+    sim = Simulation(w, precision="mixed", ctx=ctx)
+    sim.run_fused(60, 25)
+    b, db = _state(sim)
+    _same(f"n {n}", a, b, da, db)
+    assert len(b["electron"]["x"]) == n
+    if n == 0:
+        assert len(b["photon"]["x"]) == 0
+    for s_ in (ref, sim):
+        for sp in list(s_.species.values()):
+            Q.qp_destroy_species(ctx, sp.handle)
+
+
 def test_fused_overflow_drops_the_same_photons(ctx):
     w = W.plane_wave_collision(n=600, n_steps=120)
     w["capacity"] = dict(w["capacity"], photon=3000)

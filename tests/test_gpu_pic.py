@@ -66,6 +66,53 @@ def test_yee_solver_matches_the_oracle(ctx):
     assert worst <= 2e-5
 
 
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 7), (9, 1), (20_000, 3), (5, 2_000)])
+def test_yee_solver_edge_shapes(ctx, nx, ny):
+    # one node, a single row or column, more columns than one pass of the
+    # column blocks covers (64 blocks of 256), more rows than the grid's
+    # row blocks: every node updated once, as the oracle updates it
+    dx, dy = 0.2, 0.25
+    dt = 0.5 * min(dx, dy)
+    desc = _grid(nx, ny, dx, dy, 7)
+    f, keep = make_field(desc)
+    of = [c.copy() for c in desc["comps"]]
+    rng = np.random.default_rng(8)
+    J = [(rng.uniform(-1, 1, (ny, nx))).astype(np.float32) for _ in range(3)]
+    Jd = [torch.as_tensor(j).cuda() for j in J]
+    for _ in range(3):
+        Q.qp_yee_advance_b(ctx, f, 0.5 * dt)
+        O.yee_advance_b(of, dx, dy, 0.5 * dt)
+        Q.qp_yee_advance_e(ctx, f, *[j.data_ptr() for j in Jd], dt)
+        O.yee_advance_e(of, J, dx, dy, dt)
+    torch.cuda.synchronize()
+    scale = max(max(np.abs(c).max() for c in of), 1e-30)
+    worst = max(np.abs(keep[k].cpu().numpy() - of[k]).max() for k in range(6)) / scale
+    assert worst <= 2e-5, (nx, ny, worst)
+
+
+@pytest.mark.parametrize("n", [0, 1])
+def test_current_deposition_of_tiny_species(ctx, n):
+    nx, ny, dx, dy, dt = 16, 12, 0.3, 0.25, 0.1
+    arr = {"x": np.full(n, 2.05), "y": np.full(n, 1.4), "ux": np.full(n, 0.7),
+           "uy": np.full(n, -0.3), "uz": np.full(n, 0.2), "w": np.full(n, 1.5)}
+    f, keep = make_field(_grid(nx, ny, dx, dy, 4))
+    sp = DeviceSpecies(ctx, Q.QP_ELECTRON, max(n, 1), 2)
+    sp.load(arr, n)
+    Jg = torch.zeros((3, ny, nx), dtype=torch.float32, device="cuda")
+    Q.qp_deposit_current(ctx, sp.handle, f, *(Jg[k].data_ptr() for k in range(3)), dt)
+    torch.cuda.synchronize()
+    osp = O.Species.from_arrays(arr, max(n, 1), 2)
+    osp.n = n
+    Jo = [np.zeros((ny, nx)) for _ in range(3)]
+    O.deposit_current(osp, -1.0, dt, Jo, dx, dy)
+    for c in range(3):
+        g = Jg[c].cpu().numpy().astype(np.float64)
+        assert np.allclose(g, Jo[c], rtol=1e-5, atol=1e-6 * max(np.abs(Jo[c]).max(), 1.0))
+        if n == 0:
+            assert not g.any()
+    Q.qp_destroy_species(ctx, sp.handle)
+
+
 def test_current_deposition_matches_the_oracle(ctx):
     nx, ny, dx, dy, dt = 160, 96, 0.3, 0.25, 0.1
     rng = np.random.default_rng(3)

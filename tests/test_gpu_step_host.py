@@ -84,3 +84,25 @@ def test_host_step_rejects_a_pitch_below_the_capacity(ctx):
     states[0].count = sim.species["electron"].cap + 1
     with pytest.raises(Q.QPError):
         sim.run_host(states, 1)
+
+
+def test_host_step_with_empty_species_and_zero_steps(ctx):
+    w = W.plane_wave_collision(n=0, n_steps=4)
+    sim = Simulation(w, precision="fp64", ctx=ctx)
+    host = {n: torch.zeros(sim.species[n].block.shape, dtype=torch.float64, pin_memory=True)
+            for n in NAMES}
+    states = sim.host_states(host, sim.live_counts())
+    assert sim.run_host(states, 2) == Q.QP_OK
+    assert [int(states[k].count) for k in range(3)] == [0, 0, 0]
+    w = W.plane_wave_collision(n=50, n_steps=4)
+    sim = Simulation(w, precision="fp64", ctx=ctx)
+    host = {n: torch.zeros(sim.species[n].block.shape, dtype=torch.float64, pin_memory=True)
+            for n in NAMES}
+    counts = sim.live_counts()
+    sim.species["electron"].copy_state(host["electron"], counts["electron"], False)
+    torch.cuda.synchronize()
+    before = host["electron"][:, :50].clone()
+    states = sim.host_states(host, counts)
+    assert sim.run_host(states, 0) == Q.QP_OK  # no step: the state comes back unchanged
+    assert int(states[0].count) == 50
+    assert torch.equal(host["electron"][:, :50], before)
