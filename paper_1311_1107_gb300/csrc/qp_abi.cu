@@ -514,7 +514,7 @@ int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *
         if (hs[k] == -1) continue;
         const qp_species_desc &d = ctx->species[hs[k]].d;
         const long long before = st[k].count, after = hc[k];
-        if (after < before || after > d.capacity) return QP_ERR_CUDA;  // not a step's counts
+        if (after < before || after > d.capacity) return fail(QP_ERR_CUDA);  // not a step's counts
         st[k].count = after;
         if (after > before) {
             e = copy_slots(d, st[k].host, st[k].pitch, before, after - before, 0, cs);
