@@ -583,11 +583,11 @@ struct StashSink {
     }
 };
 
-template <int PREC, int FK, typename R>
+template <int PREC, int FK, typename R, class Hook>
 __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned long long *bar, bool &loaded, unsigned chain_tile, int sp,
                            int64_t first, int64_t n, unsigned epoch, int *s_warp, BlockStats &bs,
-                           double *st, unsigned short *s_map)
+                           double *st, unsigned short *s_map, Hook &&before_scan)
 {
     const int tid = threadIdx.x;
     if (!loaded && tid == 0) {
@@ -640,6 +640,7 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     // stashed and mapped; their slots are written later (write_photons)
     int tile_total;
     const int nph = o.nph;
+    before_scan();
     const int local = block_scan(nph, s_warp, &tile_total);
     if (tid == 0) publish_aggregate(P.lep_words, chain_tile, tile_total, epoch);
     for (int k = 0; k < nph; ++k) s_map[local + k] = (unsigned short)(tid | (k << 8));
@@ -650,13 +651,14 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
 // goes to slot base + j, one thread per photon (coalesced stores); those
 // beyond the capacity are counted as dropped with their energy.
 __device__ void write_photons(const Problem &P, const double *st, const unsigned short *s_map,
-                              int total, long long base, int sp, BlockStats &bs)
+                              int total, long long base, int sp, BlockStats &bs, int t0,
+                              int stride)
 {
     const SpeciesDev &Ph = P.sp[2];
     const bool photons = Ph.present != 0;
     int stored = 0, dropped = 0;
     double e_drop = 0.0;
-    for (int j = threadIdx.x; j < total; j += kTile) {
+    for (int j = t0; j < total; j += stride) {
         const unsigned m = s_map[j];
         const int e = (int)(m & 0xFFu), k = (int)(m >> 8);
         const int64_t slot = base + j;
@@ -710,11 +712,11 @@ __device__ __forceinline__ double photon_move32(double x, float f, float c)
 
 // -------------------------------------------------------------------- photon tile
 
-template <int PREC, int FK, typename R>
+template <int PREC, int FK, typename R, class Hook>
 __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            unsigned long long *bar, bool &loaded, unsigned chain_tile, int64_t n,
                            unsigned epoch, int *s_warp, BlockStats &bs, double *st,
-                           unsigned short *s_map)
+                           unsigned short *s_map, Hook &&before_scan)
 {
     const int tid = threadIdx.x;
     const SpeciesDev &Ph = P.sp[2];
@@ -873,6 +875,7 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
     if (npair && Ph.nemit) Ph.nemit[i] += 1;
     warp_count(&bs.c[2][cClamp], clamped);
     warp_count(&bs.c[2][cPair], npair != 0);
+    before_scan();
     if (!pairs) return 0;
 
     // ---- this tile's pairs: aggregate published now, records stashed
@@ -901,11 +904,11 @@ __device__ int photon_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
 // beyond it the pair is dropped and its energy counted.
 __device__ void write_pairs(const Problem &P, const double *st, const unsigned short *s_map,
                             int total, long long excl, long long be, long long bp, long long room,
-                            BlockStats &bs)
+                            BlockStats &bs, int t0, int stride)
 {
     const SpeciesDev &El = P.sp[0], &Po = P.sp[1];
     const bool leptons = El.present && Po.present;
-    for (int j = threadIdx.x; j < total; j += kTile) {
+    for (int j = t0; j < total; j += stride) {
         const int e = (int)(s_map[j] & 0xFFu);
         const double px = st[0 * kTile + e], py = st[1 * kTile + e], pz = st[2 * kTile + e];
         const double gux = st[3 * kTile + e], guy = st[4 * kTile + e], guz = st[5 * kTile + e];
@@ -1021,12 +1024,43 @@ struct Pending {
     long long base, be, bp, room;
 };
 
+// The writes of a stashed tile whose exclusive prefix excl is known:
+// threads t0, t0 + stride, ... write its photons or pairs; `leader` (one
+// thread) sets the new live count when it is the last tile of its chain.
+__device__ __forceinline__ void flush_write(const StepArgs &a, const Problem &P, const Pending &pd,
+                                           long long excl, BlockStats &bs, const double *st,
+                                           const unsigned short *s_map, int t0, int stride,
+                                           bool leader)
+{
+    if (pd.chain == 0) {
+        if (pd.last && leader) {
+            const long long tot = pd.base + excl + pd.total;
+            if (P.sp[2].present) {
+                P.pending[2] = tot < P.sp[2].cap ? tot : P.sp[2].cap;
+                if (tot > P.sp[2].cap) raise_status(a.status, QP_WARN_BUFFER_FULL);
+            } else if (tot > pd.base) {
+                raise_status(a.status, QP_WARN_BUFFER_FULL);
+            }
+        }
+        if (pd.total) write_photons(P, st, s_map, pd.total, pd.base + excl, pd.sp, bs, t0, stride);
+    } else {
+        if (pd.last && leader) {
+            const long long tot = excl + pd.total;
+            const long long add = tot < pd.room ? tot : pd.room;
+            P.pending[0] = pd.be + add;
+            P.pending[1] = pd.bp + add;
+            if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
+        }
+        if (pd.total)
+            write_pairs(P, st, s_map, pd.total, excl, pd.be, pd.bp, pd.room, bs, t0, stride);
+    }
+}
+
 // Resolve a stashed tile's prefix (its predecessors are, by now, almost
 // always published) and write its photons or pairs; the last tile of a
 // chain also sets the new live count applied at the end of the launch.
-// All threads of the block; the record was written before a barrier.  The
-// tile loop has one call site, after the physics of a tile (the registers
-// of the physics are free by then).
+// All threads of the block (when the block leaves a problem or the launch);
+// the record was written before a barrier.
 __device__ __forceinline__ void flush_pending(const StepArgs &a, const Problem &P, const Pending &pd,
                                            unsigned epoch, long long *s_excl, BlockStats &bs,
                                            const double *st, const unsigned short *s_map)
@@ -1037,30 +1071,23 @@ __device__ __forceinline__ void flush_pending(const StepArgs &a, const Problem &
         if (threadIdx.x == 0) *s_excl = e;
     }
     __syncthreads();
-    const long long excl = *s_excl;
-    if (pd.chain == 0) {
-        if (pd.last && threadIdx.x == 0) {
-            const long long tot = pd.base + excl + pd.total;
-            if (P.sp[2].present) {
-                P.pending[2] = tot < P.sp[2].cap ? tot : P.sp[2].cap;
-                if (tot > P.sp[2].cap) raise_status(a.status, QP_WARN_BUFFER_FULL);
-            } else if (tot > pd.base) {
-                raise_status(a.status, QP_WARN_BUFFER_FULL);
-            }
-        }
-        if (pd.total) write_photons(P, st, s_map, pd.total, pd.base + excl, pd.sp, bs);
-    } else {
-        if (pd.last && threadIdx.x == 0) {
-            const long long tot = excl + pd.total;
-            const long long add = tot < pd.room ? tot : pd.room;
-            P.pending[0] = pd.be + add;
-            P.pending[1] = pd.bp + add;
-            if (tot > add) raise_status(a.status, QP_WARN_BUFFER_FULL);
-        }
-        if (pd.total) write_pairs(P, st, s_map, pd.total, excl, pd.be, pd.bp, pd.room, bs);
-    }
+    flush_write(a, P, pd, *s_excl, bs, st, s_map, threadIdx.x, kTile, threadIdx.x == 0);
     // the record, map, stash buffer and s_excl are free for reuse after this
     __syncthreads();
+}
+
+// The same by one warp, without a block barrier: the warp that finishes a
+// tile's physics first flushes the block's oldest stashed tile while the
+// others are still computing (the buffers are reused only after the tile
+// loop's closing barrier).
+__device__ void flush_pending_warp(const StepArgs &a, const Problem &P, const Pending &pd,
+                                   unsigned epoch, BlockStats &bs, const double *st,
+                                   const unsigned short *s_map)
+{
+    const int lane = threadIdx.x & 31;
+    const long long excl = resolve_prefix(pd.chain ? P.pho_words : P.lep_words, pd.tile,
+                                          pd.total, epoch, a.spin_limit, a.status);
+    flush_write(a, P, pd, excl, bs, st, s_map, lane, 32, lane == 0);
 }
 
 // One launch = one step of every active problem.  Persistent blocks take
@@ -1102,6 +1129,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     __shared__ int s_warp[kWarps];
     __shared__ unsigned s_ticket[2];
     __shared__ long long s_excl;
+    __shared__ unsigned s_claim;  // warps past their tile's physics, all tiles so far
     __shared__ long long s_tmp[kWarps];
     __shared__ BlockStats bs;
     __shared__ __align__(16) Problem s_prob;        // batch: the problem of the current tile
@@ -1125,6 +1153,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
     clear_stats(bs);
+    if (tid == 0) s_claim = 0u;  // visible after the barrier below
     double *const stash_block = a.stash + (size_t)blockIdx.x * kStashBufs * kStashFields * kTile;
     // tiles of this block with stashed appends: numbers q_lo..q-1 are not
     // yet written (uniform over the block)
@@ -1168,8 +1197,9 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
             b = lo;
         }
         const bool leave = !more || (BATCH && b != cur);  // the current problem's last tile is done
-        // ---- stashed appends: the oldest tile when the ring is full, all of
-        // them when the block leaves its problem (the one flush site)
+        // ---- stashed appends: all of them when the block leaves its problem
+        // (during a problem the first warp past a tile's physics flushes the
+        // oldest one: see before_scan below; this loop then finds no full ring)
         {
             const Problem &F = BATCH ? s_prob : a.single;
             while (q_lo != q && (leave || q - q_lo == (unsigned)kStashBufs)) {
@@ -1207,12 +1237,32 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
         const int sb = (int)(q % kStashBufs);
         double *st = stash_block + (size_t)sb * kStashFields * kTile;
         bool stashed = true;
+        // Right before a tile's own scan, every warp claims once (so each
+        // tile adds kWarps to s_claim): the first warp past its physics
+        // (claim a multiple of kWarps) flushes the oldest stashed tile, two
+        // tiles back, when two are pending, while the others still compute.
+        // Its buffers are reused only after the closing barrier of this tile.
+        // Not on the 2D grid: its single-wave steps have one tile a block
+        // (nothing to overlap) and the flush code would spill there.
+        constexpr bool kEarlyFlush = FK != QP_FIELD_YEE2D;
+        const bool flush_early = kEarlyFlush && q - q_lo == (unsigned)(kStashBufs - 1);
+        const int ob = (int)(q_lo % kStashBufs);
+        auto before_scan = [&]() {
+            if constexpr (!kEarlyFlush) return;
+            unsigned c = 0u;
+            if ((tid & 31) == 0) c = atomicAdd(&s_claim, 1u);
+            c = __shfl_sync(0xFFFFFFFFu, c, 0);
+            if (flush_early && c % (unsigned)kWarps == 0u)
+                flush_pending_warp(a, P, s_pq[ob], epoch, bs,
+                                   stash_block + (size_t)ob * kStashFields * kTile, s_map[ob]);
+        };
         if (lt < pc.tiles_l) {
             const int sp = lt < pc.tiles_e ? 0 : 1;
             const int64_t first = (lt - (sp ? pc.tiles_e : 0)) * kTile;
             const int total =
                 lepton_tile<PREC, FK, R>(a, P, sm, &s_bar[0], lep_loaded, (unsigned)lt, sp,
-                                         first, pc.n[sp], epoch, s_warp, bs, st, s_map[sb]);
+                                         first, pc.n[sp], epoch, s_warp, bs, st, s_map[sb],
+                                         before_scan);
             if (tid == 0) {
                 Pending &r = s_pq[sb];
                 r.chain = 0;
@@ -1233,7 +1283,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
             }
             const int total =
                 photon_tile<PREC, FK, R>(a, P, sm, &s_bar[1], ph_loaded, pt, pc.n[2], epoch,
-                                         s_warp, bs, st, s_map[sb]);
+                                         s_warp, bs, st, s_map[sb], before_scan);
             stashed = P.pairs != 0;  // without pairs a photon tile appends nothing
             if (tid == 0 && stashed) {
                 Pending &r = s_pq[sb];
@@ -1249,6 +1299,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
         }
         if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
         __syncthreads();  // the record and the next ticket are visible
+        if (flush_early) ++q_lo;
         if (stashed) ++q;
     }
 
