@@ -457,10 +457,20 @@ int qp_species_copy(qp_ctx *ctx, int32_t handle, void *host, int64_t host_pitch,
     return cuda_status(copy_slots(d, host, host_pitch, 0, count, to_device, (cudaStream_t)stream));
 }
 
+namespace {
+int build_problem(const qp_ctx *ctx, const qp_step_params *s, qp::Problem &P);
+}
+
 int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *stream)
 {
     if (!ctx) return QP_ERR_NOT_INITIALIZED;
     if (!s || !st) return QP_ERR_INVALID_ARG;
+    {
+        // what qp_step would reject, before anything is copied
+        qp::Problem check{};
+        const int v = build_problem(ctx, s, check);
+        if (v != QP_OK) return v;
+    }
     const int32_t hs[3] = {s->electron, s->positron, s->photon};
     for (int k = 0; k < 3; ++k) {
         if (hs[k] == -1) continue;

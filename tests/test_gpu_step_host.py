@@ -84,6 +84,20 @@ def test_host_step_rejects_a_pitch_below_the_capacity(ctx):
     states[0].count = sim.species["electron"].cap + 1
     with pytest.raises(Q.QPError):
         sim.run_host(states, 1)
+    # a step description qp_step rejects: refused before the state is copied
+    sim.species["electron"].load(w["electrons"])
+    torch.cuda.synchronize()
+    before = sim.species["electron"].block.clone()
+    states[0].count = 64
+    host["electron"].zero_()
+    dt = sim.params.dt
+    sim.params.dt = -1.0
+    with pytest.raises(Q.QPError) as e:
+        sim.run_host(states, 1)
+    assert e.value.status == Q.QP_ERR_INVALID_ARG
+    sim.params.dt = dt
+    torch.cuda.synchronize()
+    assert torch.equal(sim.species["electron"].block, before)
 
 
 def test_host_step_with_empty_species_and_zero_steps(ctx):
