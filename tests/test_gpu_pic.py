@@ -185,18 +185,27 @@ def test_pic_foil_matches_the_oracle(ctx, precision):
     # the fields: the pulse on the grid plus the plasma's current.  The
     # current follows the particles, whose orbits are chaotic, and a particle
     # whose emissions differ (a discrete event decided at a rounding-level
-    # margin) deposits a different current from then on.  The GPU run is
-    # another sample of that sensitivity, which the oracle's noise-kicked
-    # twins measure: the bar is 1e-3 of the largest field or four times the
-    # twins' spread (a margin for sample-to-sample variation), whichever is
-    # larger
+    # margin; the order of the float atomics of the deposition varies from
+    # run to run) deposits a different current from then on, which shows at
+    # a few nodes.  The GPU run is another sample of that sensitivity, which
+    # the oracle's noise-kicked twins measure.  Bars: the rms difference
+    # within 1e-4 of the rms field or four times the twins' rms spread
+    # (measured 2.6e-6 - 3.1e-6, and 5.6e-5 in a run where one particle's
+    # emission count differed; twins 3e-5), and the largest difference
+    # within 1e-2 of the largest field or ten times the twins' (measured
+    # 1.4e-5 - 1.7e-5, 2.2e-3 in that run; twins 6.7e-4): a wrong stencil,
+    # staggering or sign of the current misses both by orders of magnitude
     ey_g = sim._keep[1].cpu().numpy()
     ey_o = osim.field._keep[1]
     scale = np.abs(ey_o).max()
     err = np.abs(ey_g - ey_o).max() / scale
     spread = max(np.abs(t[0].field._keep[1] - ey_o).max() / scale for t in twin_runs)
+    rms = np.sqrt(np.mean((ey_g - ey_o) ** 2)) / np.sqrt(np.mean(ey_o ** 2))
+    rms_spread = max(np.sqrt(np.mean((t[0].field._keep[1] - ey_o) ** 2))
+                     for t in twin_runs) / np.sqrt(np.mean(ey_o ** 2))
     print(f"[PIC foil {precision}] E_y largest difference {err:.3g} of the largest "
-          f"(oracle twins {spread:.3g})")
-    assert err <= max(1e-3, 4.0 * spread) and scale > 50.0
+          f"(oracle twins {spread:.3g}); rms {rms:.3g} of the rms (twins {rms_spread:.3g})")
+    assert rms <= max(1e-4, 4.0 * rms_spread) and scale > 50.0
+    assert err <= max(1e-2, 10.0 * spread)
     assert np.abs(o["uy"]).max() > 5.0 and rep["comparable"] > 0
     sim.close()
