@@ -63,6 +63,91 @@ __global__ void __launch_bounds__(kPicBlock) k_yee_e(YeeGrid g, float idx, float
         }
 }
 
+// The same updates four nodes a thread (x = 4 q .. 4 q + 3 of a row) with
+// 16-byte loads and stores, for grids whose rows are whole float4s (nx a
+// multiple of 4, arrays 16-byte aligned); the arithmetic of each node is
+// k_yee_b's and k_yee_e's.  The neighbour past the four (x + 4 for B, x - 1
+// for E) is one scalar load.
+__device__ __forceinline__ float4 ld4(const float *a, int64_t k)
+{
+    return *reinterpret_cast<const float4 *>(a + k);
+}
+
+__global__ void __launch_bounds__(kPicBlock) k_yee_b4(YeeGrid g, float idx, float idy, float dtb)
+{
+    const int64_t nq = g.nx / 4;
+    for (int64_t j = blockIdx.y; j < g.ny; j += gridDim.y)
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t k = j * g.nx + 4 * q;
+            const bool up = j + 1 < g.ny, right = 4 * q + 4 < g.nx;
+            const float4 ez = ld4(g.f[2], k), ey = ld4(g.f[1], k), ex = ld4(g.f[0], k);
+            const float4 ezu = up ? ld4(g.f[2], k + g.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 exu = up ? ld4(g.f[0], k + g.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float ezr = right ? g.f[2][k + 4] : 0.0f, eyr = right ? g.f[1][k + 4] : 0.0f;
+            float4 bx = ld4(g.f[3], k), by = ld4(g.f[4], k), bz = ld4(g.f[5], k);
+            const float vez[5] = {ez.x, ez.y, ez.z, ez.w, ezr};
+            const float vey[5] = {ey.x, ey.y, ey.z, ey.w, eyr};
+            const float vezu[4] = {ezu.x, ezu.y, ezu.z, ezu.w};
+            const float vex[4] = {ex.x, ex.y, ex.z, ex.w}, vexu[4] = {exu.x, exu.y, exu.z, exu.w};
+            float *pbx = &bx.x, *pby = &by.x, *pbz = &bz.x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float dEz_dy = (vezu[c] - vez[c]) * idy;
+                const float dEz_dx = (vez[c + 1] - vez[c]) * idx;
+                const float dEy_dx = (vey[c + 1] - vey[c]) * idx;
+                const float dEx_dy = (vexu[c] - vex[c]) * idy;
+                pbx[c] -= dtb * dEz_dy;
+                pby[c] += dtb * dEz_dx;
+                pbz[c] -= dtb * (dEy_dx - dEx_dy);
+            }
+            *reinterpret_cast<float4 *>(g.f[3] + k) = bx;
+            *reinterpret_cast<float4 *>(g.f[4] + k) = by;
+            *reinterpret_cast<float4 *>(g.f[5] + k) = bz;
+        }
+}
+
+__global__ void __launch_bounds__(kPicBlock) k_yee_e4(YeeGrid g, float idx, float idy,
+                                                      const float *jx, const float *jy,
+                                                      const float *jz, float dt)
+{
+    const int64_t nq = g.nx / 4;
+    for (int64_t j = blockIdx.y; j < g.ny; j += gridDim.y)
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t k = j * g.nx + 4 * q;
+            const bool down = j > 0, left = q > 0;
+            const float4 bz = ld4(g.f[5], k), by = ld4(g.f[4], k), bx = ld4(g.f[3], k);
+            const float4 bzd = down ? ld4(g.f[5], k - g.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 bxd = down ? ld4(g.f[3], k - g.nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float bzl = left ? g.f[5][k - 1] : 0.0f, byl = left ? g.f[4][k - 1] : 0.0f;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 cx = jx ? ld4(jx, k) : z4, cy = jy ? ld4(jy, k) : z4,
+                         cz = jz ? ld4(jz, k) : z4;
+            float4 ex = ld4(g.f[0], k), ey = ld4(g.f[1], k), ez = ld4(g.f[2], k);
+            const float vbz[5] = {bzl, bz.x, bz.y, bz.z, bz.w};
+            const float vby[5] = {byl, by.x, by.y, by.z, by.w};
+            const float vbzd[4] = {bzd.x, bzd.y, bzd.z, bzd.w};
+            const float vbx[4] = {bx.x, bx.y, bx.z, bx.w}, vbxd[4] = {bxd.x, bxd.y, bxd.z, bxd.w};
+            const float vjx[4] = {cx.x, cx.y, cx.z, cx.w}, vjy[4] = {cy.x, cy.y, cy.z, cy.w},
+                        vjz[4] = {cz.x, cz.y, cz.z, cz.w};
+            float *pex = &ex.x, *pey = &ey.x, *pez = &ez.x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float dBz_dy = (vbz[c + 1] - vbzd[c]) * idy;
+                const float dBz_dx = (vbz[c + 1] - vbz[c]) * idx;
+                const float dBy_dx = (vby[c + 1] - vby[c]) * idx;
+                const float dBx_dy = (vbx[c] - vbxd[c]) * idy;
+                pex[c] += dt * (dBz_dy - vjx[c]);
+                pey[c] += dt * (-dBz_dx - vjy[c]);
+                pez[c] += dt * (dBy_dx - dBx_dy - vjz[c]);
+            }
+            *reinterpret_cast<float4 *>(g.f[0] + k) = ex;
+            *reinterpret_cast<float4 *>(g.f[1] + k) = ey;
+            *reinterpret_cast<float4 *>(g.f[2] + k) = ez;
+        }
+}
+
 // One thread a particle: q w v / (dx dy) spread with the linear weights of
 // each component's staggering at the mid-step position x - v dt/2 (after a
 // step: x^(n+1) and v^(n+1/2)).  FP32 atomic sums (their order varies).
@@ -121,6 +206,25 @@ dim3 node_grid(const YeeGrid &g, int num_sms)
     return dim3((unsigned)bx, (unsigned)(by > 0 ? by : 1));
 }
 
+dim3 quad_grid(const YeeGrid &g, int num_sms)
+{
+    YeeGrid q = g;
+    q.nx = g.nx / 4;
+    return node_grid(q, num_sms);
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0u; }
+
+// Rows of whole float4s: nx a multiple of 4 and every array 16-byte aligned.
+bool quads(const YeeGrid &g, const float *jx = nullptr, const float *jy = nullptr,
+           const float *jz = nullptr)
+{
+    if (g.nx % 4 != 0) return false;
+    for (int c = 0; c < 6; ++c)
+        if (!aligned16(g.f[c])) return false;
+    return aligned16(jx) && aligned16(jy) && aligned16(jz);
+}
+
 int grid_blocks(int64_t n, int num_sms)
 {
     int64_t b = (n + kPicBlock - 1) / kPicBlock;
@@ -134,17 +238,24 @@ int grid_blocks(int64_t n, int num_sms)
 cudaError_t launch_yee_b(const YeeGrid &g, double dtb, int num_sms, cudaStream_t st)
 {
     // 1/dx and 1/dy once, as each node would form them (FP64 quotient to float)
-    k_yee_b<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, (float)(1.0 / g.dx),
-                                                         (float)(1.0 / g.dy), (float)dtb);
+    const float idx = (float)(1.0 / g.dx), idy = (float)(1.0 / g.dy);
+    if (quads(g))
+        k_yee_b4<<<quad_grid(g, num_sms), kPicBlock, 0, st>>>(g, idx, idy, (float)dtb);
+    else
+        k_yee_b<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, idx, idy, (float)dtb);
     return cudaGetLastError();
 }
 
 cudaError_t launch_yee_e(const YeeGrid &g, const float *jx, const float *jy, const float *jz,
                          double dt, int num_sms, cudaStream_t st)
 {
-    k_yee_e<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, (float)(1.0 / g.dx),
-                                                         (float)(1.0 / g.dy), jx, jy, jz,
-                                                         (float)dt);
+    const float idx = (float)(1.0 / g.dx), idy = (float)(1.0 / g.dy);
+    if (quads(g, jx, jy, jz))
+        k_yee_e4<<<quad_grid(g, num_sms), kPicBlock, 0, st>>>(g, idx, idy, jx, jy, jz,
+                                                              (float)dt);
+    else
+        k_yee_e<<<node_grid(g, num_sms), kPicBlock, 0, st>>>(g, idx, idy, jx, jy, jz,
+                                                             (float)dt);
     return cudaGetLastError();
 }
 

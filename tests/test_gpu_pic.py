@@ -66,11 +66,13 @@ def test_yee_solver_matches_the_oracle(ctx):
     assert worst <= 2e-5
 
 
-@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 7), (9, 1), (20_000, 3), (5, 2_000)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 7), (9, 1), (20_000, 3), (5, 2_000),
+                                   (4, 1), (8, 2_000), (65_544, 2)])
 def test_yee_solver_edge_shapes(ctx, nx, ny):
     # one node, a single row or column, more columns than one pass of the
-    # column blocks covers (64 blocks of 256), more rows than the grid's
-    # row blocks: every node updated once, as the oracle updates it
+    # column blocks covers (64 blocks of 256 threads; of 4 nodes each when
+    # rows are whole float4s, nx a multiple of 4), more rows than the
+    # grid's row blocks: every node updated once, as the oracle updates it
     dx, dy = 0.2, 0.25
     dt = 0.5 * min(dx, dy)
     desc = _grid(nx, ny, dx, dy, 7)
