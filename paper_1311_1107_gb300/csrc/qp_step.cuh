@@ -1107,15 +1107,16 @@ __device__ void flush_pending_warp(const StepArgs &a, const Problem &P, const Pe
 // device table of problems, each copied to shared memory for its tiles, with
 // time and step counters advanced on the device.
 // Resident blocks of 128 per SM.  FP64: 4 (128 registers, no spills).
-// Mixed: 8 (64 registers; the few spills cost less than the extra resident
-// warps gain), except with the Yee grid: 7 (73 registers), where the 24
-// loads of the gather are in flight together and spill at 64 (measured on
-// the 2D foil: 30.4 us per step at 7, 32.7 at 8; the analytic-field
-// collision: 366 us at 7, 356 at 8).
+// Mixed: 7 (72 registers): the Yee gather keeps its 24 loads in flight
+// (the 2D foil: 30.4 us per step at 7, 32.7 at 8), and since the first warp
+// past a tile's physics flushes the oldest stashed tile (its code in the
+// tile loop) the analytic-field steps spill less at 72 than at 64 (the
+// 2e6-electron collision: 0.371 ms per step at 7, 0.386 at 8; before that
+// change, 366 us at 7 and 356 at 8).
 template <int PREC, int FK>
 constexpr int step_min_blocks()
 {
-    return PREC == kFP64 ? 4 : (FK == QP_FIELD_YEE2D ? 7 : 8);
+    return PREC == kFP64 ? 4 : 7;
 }
 
 template <int PREC, int FK, bool BATCH>
