@@ -169,6 +169,21 @@ def test_fused_rejects_pairs_on(ctx):
         sim.run_fused(10, 5)
 
 
+@pytest.mark.parametrize("n_steps,fuse", [(10, 0), (70_000, 70_000)])
+def test_fused_rejects_bad_windows(ctx, n_steps, fuse):
+    # a window of no steps, and one of more than 65535 steps (the steps left
+    # to a photon are counted in 16 bits): refused, nothing stepped
+    w = W.plane_wave_collision(n=64, n_steps=10)
+    sim = Simulation(w, precision="mixed", ctx=ctx)
+    before = sim.species["electron"].block.clone()
+    with pytest.raises(Q.QPError) as e:
+        sim.run_fused(n_steps, fuse)
+    assert e.value.status == Q.QP_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert torch.equal(sim.species["electron"].block, before)
+    assert sim.step_index == 0
+
+
 def test_fused_refuses_a_stream_being_captured(ctx):
     # a window reads the lepton counts to the host: during a capture the
     # call returns QP_ERR_INVALID_ARG before anything is enqueued
