@@ -323,9 +323,23 @@ __device__ __forceinline__ bool group_start(const unsigned long long *keys, long
 {
     const unsigned long long k = keys[j];
     if (k == nomerge || (j > 0 && keys[j - 1] == k)) return false;
-    long long e = j + 1;
-    while (e < n && keys[e] == k) ++e;
-    *end = e;
+    // the first index past j with another key (the keys are sorted): steps
+    // doubling from j until one lands past the group, then bisection
+    long long lo = j, step = 1;  // keys[lo] == k
+    long long hi = n;            // keys[hi] != k, or hi == n
+    while (lo + step < n && keys[lo + step] == k) {
+        lo += step;
+        step <<= 1;
+    }
+    if (lo + step < n) hi = lo + step;
+    while (hi - lo > 1) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (keys[mid] == k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *end = hi;
     return true;
 }
 
