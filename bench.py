@@ -29,8 +29,9 @@ The line also carries
       every host core.
 Particle-steps count the live slots at each step start, decayed photons
 (tau < 0, kept in their slots) left out.  L2 is flushed (256 MB write)
-between timed steps; each step is timed with CUDA events on its stream;
-clocks are sampled with nvidia-smi meanwhile.
+between timed steps; each step is timed with CUDA events on its stream,
+queued by the host ahead of the device (a spin kernel before the first
+timed step); clocks are sampled with nvidia-smi meanwhile.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload foil|collision|plane|serving] [--requests R]
@@ -222,11 +223,20 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
     live = [sim.species[n].n_live for n in names]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
-    Q.qp_profile_enable(ctx, True)
+    # A step of a workload with given fields is one k_step launch: its own
+    # events time the kernel.  Where a step also refills or advances the
+    # grid, the library's per-launch events time k_step among the step's
+    # launches (they add ~4 us of event records to each such step).
+    single = sim.pulse is None and sim.pic_pulse is None
+    Q.qp_profile_enable(ctx, not single)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    # a spin of ~50 ms ahead of the first timed step: the host queues the
+    # steps before the device reaches them, so the events time the device's
+    # work and not the Python loop between launches
+    torch.cuda._sleep(int(1e8 + 2e5 * steps))
     for k in range(steps):
         flush.zero_()
         torch.cat(live, out=counts[k])       # live slots at the start of the step
@@ -238,7 +248,10 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms, launches = Q.qp_profile_read(ctx)
+    if single:
+        ms, launches = [sum(step_ms), 0.0, 0.0], [steps, 0, 0]
+    else:
+        ms, launches = Q.qp_profile_read(ctx)
     Q.qp_profile_enable(ctx, False)
     c = counts.cpu().numpy()
     diag = {n: sim.diagnostics(n) for n in names}
