@@ -239,6 +239,25 @@ __device__ __forceinline__ void wait_tables(unsigned long long *bar, const StepA
 
 // -------------------------------------------------------------------- lepton tile
 
+// Issue the copy of the rate tables H and G into shared memory (one TMA
+// bulk copy each, completing on `bar`); one thread, before a barrier that
+// makes the barrier's initialisation visible to the block.
+template <int PREC, typename R>
+__device__ __forceinline__ void stage_rate_tables(const StepArgs &a, Smem<R> &sm,
+                                                  unsigned long long *bar)
+{
+    const unsigned bytes = kNRatePad * sizeof(R);
+    mbar_init(bar, 1);
+    mbar_expect_tx(bar, 2 * bytes);
+    if constexpr (PREC == kFP64) {
+        bulk_g2s(sm.H, a.tab.H, bytes, bar);
+        bulk_g2s(sm.G, a.tab.Gs, bytes, bar);
+    } else {
+        bulk_g2s(sm.H, a.tab.Hf, bytes, bar);
+        bulk_g2s(sm.G, a.tab.Gsf, bytes, bar);
+    }
+}
+
 // State of one lepton at the start of a step (the FP64 storage of both
 // paths; component c of the new state goes to the sink's put<c> as soon as
 // it is formed, c = x y z ux uy uz tau, tau only when it changed).
@@ -590,21 +609,8 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
                            double *st, unsigned short *s_map, Hook &&before_scan)
 {
     const int tid = threadIdx.x;
-    if (!loaded && tid == 0) {
-        // stage the rate tables with one TMA bulk copy each; the copy
-        // overlaps the particle loads, gather and push below
-        const unsigned bytes = kNRatePad * sizeof(R);
-        mbar_init(bar, 1);
-        mbar_expect_tx(bar, 2 * bytes);
-        if constexpr (PREC == kFP64) {
-            bulk_g2s(sm.H, a.tab.H, bytes, bar);
-            bulk_g2s(sm.G, a.tab.Gs, bytes, bar);
-        } else {
-            bulk_g2s(sm.H, a.tab.Hf, bytes, bar);
-            bulk_g2s(sm.G, a.tab.Gsf, bytes, bar);
-        }
-    }
-    if (!loaded) __syncthreads();
+    // the rate tables' copy was issued in the kernel's prologue
+    // (stage_rate_tables); `loaded`: every thread has seen it land
     const SpeciesDev &S = P.sp[sp];
     const int64_t i = first + tid;
     const bool active = i < n;
@@ -620,9 +626,10 @@ __device__ int lepton_tile(const StepArgs &a, const Problem &P, Smem<R> &sm,
         if (o.n_emit && S.nemit) S.nemit[i] += o.n_emit;
     }
     if (!loaded) {
-        // threads without a particle also wait, so the block never leaves
-        // (or reuses the tables) with the copy in flight
-        if (!active) wait_tables(bar, a);
+        // every thread waits once (at once if its particle already did, or
+        // if the copy has landed): later tiles read the tables without a
+        // wait, and the block never leaves with the copy in flight
+        wait_tables(bar, a);
         loaded = true;
     }
 
@@ -1091,11 +1098,13 @@ __device__ void flush_pending_warp(const StepArgs &a, const Problem &P, const Pe
 }
 
 // One launch = one step of every active problem.  Persistent blocks take
-// 128-particle tiles from an atomic ticket (the next ticket is fetched while
-// the current tile runs when more tiles than blocks remain); tickets enumerate, problem after problem, its
-// electron tiles, positron tiles and photon tiles, so within each problem's
-// chains start order is tile order and the decoupled look-back only ever
-// waits on tiles that are running.  A tile's appends are written
+// 128-particle tiles by ticket (block b's first tile is b in a cooperative
+// launch, every other ticket comes from an atomic counter; the next ticket
+// is fetched while the current tile runs when more tiles than blocks
+// remain); tickets enumerate, problem after problem, its electron tiles,
+// positron tiles and photon tiles, so within each problem's chains start
+// order is tile order and the decoupled look-back only ever waits on tiles
+// that are running.  A tile's appends are written
 // kStashBufs - 1 tiles later: its aggregate is published right after its
 // physics, its records go to a stash, and its prefix is resolved after the
 // block's next two tiles, when the earlier tiles have almost always
@@ -1142,27 +1151,36 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     __shared__ unsigned short s_map[kStashBufs][kMapEntries];
 
     const int tid = threadIdx.x;
-    // the first ticket is taken at entry: its atomic overlaps the reads of
-    // the live counts below.  Every ticket comes from the counter, so a tile
-    // belongs to a block only once that block runs: a wait is always for a
-    // running block, even when kernels of other streams hold part of the
-    // GPU (a fixed first tile per block would let the running blocks wait
-    // for one that cannot start).  A block whose ticket is past the last
-    // tile leaves without work.
-    if (tid == 0) s_ticket[0] = atomicAdd(&a.ctl->ticket, 1u);
+    // Tickets.  A tile must belong to a running block (its successors' look-
+    // backs wait on it).  In a cooperative launch (a single problem) every
+    // block is resident for the whole launch, so block b takes tile b at
+    // entry and later tickets come from the counter, offset by the grid: no
+    // block queues on the contended counter before its first tile.  A batch
+    // (its launches captured in graphs, next to other streams' kernels)
+    // takes every ticket from the counter, so a tile belongs to a block only
+    // once that block runs; its first atomic overlaps the reads of the live
+    // counts below.  A block whose ticket is past the last tile leaves
+    // without work.
+    const unsigned tbase = a.fixed_first ? gridDim.x : 0u;
+    if (tid == 0) s_ticket[0] = a.fixed_first ? blockIdx.x : atomicAdd(&a.ctl->ticket, 1u);
     const int np = BATCH ? a.n_problems : 1;
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
     clear_stats(bs);
     if (tid == 0) s_claim = 0u;  // visible after the barrier below
+    // the lepton tiles' rate tables, staged from the start by a thread of
+    // another warp than the ticket's and the counts' (their copy overlaps
+    // the live counts' reads and the first tile's loads, gather and push)
+    if (tid == 32) stage_rate_tables<PREC>(a, sm, &s_bar[0]);
     double *const stash_block = a.stash + (size_t)blockIdx.x * kStashBufs * kStashFields * kTile;
     // tiles of this block with stashed appends: numbers q_lo..q-1 are not
     // yet written (uniform over the block)
     unsigned q = 0, q_lo = 0;
 
-    // tiles of every problem, and the ticket offset of each
+    // tiles of every problem, and the ticket offset of each (threads 64 on:
+    // not the ticket's or the tables' warp)
     bool bad = false;
-    for (int b = tid; b < np; b += kTile) {
+    for (int b = (tid + kTile - 64) % kTile; b < np; b += kTile) {
         const ProbCounts c = problem_counts(table[b]);
         s_off[b] = c.tiles_l + c.tiles_g;
         s_tl[b] = (int)c.tiles_l;
@@ -1183,7 +1201,7 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
         // fetch the next ticket while this tile runs, when another tile is
         // likely left for this block (else the atomic only adds contention)
         const bool early = t + (long long)gridDim.x < n_tickets;
-        if (early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        if (early && tid == 0) s_ticket[buf ^ 1] = tbase + atomicAdd(&a.ctl->ticket, 1u);
         int b = 0;
         if (BATCH && more) {
             // the problem of ticket t: the first b with s_off[b] > t
@@ -1298,11 +1316,15 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
                 r.room = room;
             }
         }
-        if (!early && tid == 0) s_ticket[buf ^ 1] = atomicAdd(&a.ctl->ticket, 1u);
+        if (!early && tid == 0) s_ticket[buf ^ 1] = tbase + atomicAdd(&a.ctl->ticket, 1u);
         __syncthreads();  // the record and the next ticket are visible
         if (flush_early) ++q_lo;
         if (stashed) ++q;
     }
+
+    // a block that ran no lepton tile lets the tables' copy land before it
+    // leaves
+    if (!lep_loaded) wait_tables(&s_bar[0], a);
 
     // ---- the last block to finish publishes the step of every problem:
     // the last block of each group counts in `done`, the last of those is it
