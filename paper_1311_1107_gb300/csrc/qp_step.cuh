@@ -51,6 +51,17 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *((const volatile unsigned long long *)p);
 }
 
+// *p += v at GPU scope with acquire-release semantics; returns the old value
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // Decoupled look-back over a chain of tiles.  A tile first publishes its
 // aggregate (the number of particles it appends); the exclusive prefix is
 // then computed by one full warp with a 32-tile window: lane l inspects tile
@@ -1328,21 +1339,25 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
 
     // ---- the last block to finish publishes the step of every problem:
     // the last block of each group counts in `done`, the last of those is it
+    // The counts are acquire-release atomics: a count releases the block's
+    // writes (every thread's: the barrier that closed its last flush orders
+    // them before thread 0's count) and the group's last count acquires the
+    // group's, so the last block sees every block's pending counts.
     if (tid == 0) {
-        __threadfence();
         const unsigned g = blockIdx.x % kDoneGroups;
         const unsigned in_group = (gridDim.x - 1 - g) / kDoneGroups + 1;
         const unsigned groups = gridDim.x < kDoneGroups ? gridDim.x : kDoneGroups;
         s_last = 0;
-        if (atomicAdd(&a.ctl->grp[g][0], 1u) == in_group - 1) {
+        if (atom_add_acq_rel(&a.ctl->grp[g][0], 1u) == in_group - 1) {
             a.ctl->grp[g][0] = 0u;  // every block of the group has counted
-            __threadfence();
-            s_last = atomicAdd(&a.ctl->done, 1u) == groups - 1;
+            s_last = atom_add_acq_rel(&a.ctl->done, 1u) == groups - 1;
         }
     }
     __syncthreads();
     if (s_last) {
-        __threadfence();
+        // thread 0 acquired with its count; the other threads' reads (a
+        // batch's problems) follow this fence
+        if (BATCH) __threadfence();
         for (int b = tid; b < np; b += kTile) {
             const Problem &Q = table[b];
             if (Q.device_step && *((volatile long long *)Q.left_ctr) <= 0) continue;
@@ -1351,11 +1366,13 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
                 const ProbCounts c = problem_counts(Q);
                 *Q.work_ctr += c.n[0] + c.n[1] + c.n[2];
             }
+            // the three counts read together, then written
             volatile long long *pend = Q.pending;
-            if (s_tl[b] > 0 && Q.sp[2].present) *Q.sp[2].n_live = pend[2];
+            const long long p0 = pend[0], p1 = pend[1], p2 = pend[2];
+            if (s_tl[b] > 0 && Q.sp[2].present) *Q.sp[2].n_live = p2;
             if (s_tg[b] > 0 && Q.pairs && Q.sp[0].present && Q.sp[1].present) {
-                *Q.sp[0].n_live = pend[0];
-                *Q.sp[1].n_live = pend[1];
+                *Q.sp[0].n_live = p0;
+                *Q.sp[1].n_live = p1;
             }
             if (Q.device_step) {
                 *Q.step_ctr += 1;
@@ -1363,11 +1380,11 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
             }
         }
         __syncthreads();
+        // the next launch reads these after this one has ended: no fence
         if (tid == 0) {
             *((volatile unsigned *)&a.ctl->ticket) = 0u;
             *((volatile unsigned *)&a.ctl->done) = 0u;
             *((volatile unsigned *)&a.ctl->epoch) = epoch + 1u;
-            __threadfence();
         }
     }
 }
