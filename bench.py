@@ -341,8 +341,10 @@ def fused_leg(dev, flush, warmup: int):
     return out
 
 
+# the step kernel's sources, and the unit that picks its launch (grid shape,
+# cooperative or not)
 STEP_SOURCES = ("qp_step.cuh", "qp_device.cuh", "qp_mixed.cuh", "qp_df.h", "qp_internal.h",
-                "qp_kernels.h", "qp_step_fp64.cu", "qp_step_mixed.cu")
+                "qp_kernels.h", "qp_step_fp64.cu", "qp_step_mixed.cu", "qp_kernels.cu")
 
 
 def kernel_source_id() -> str:
