@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "qp_df.h"
 #include "qp_kernels.h"
 
 namespace qp {
@@ -151,7 +152,40 @@ __global__ void __launch_bounds__(kPicBlock) k_yee_e4(YeeGrid g, float idx, floa
 // One thread a particle: q w v / (dx dy) spread with the linear weights of
 // each component's staggering at the mid-step position x - v dt/2 (after a
 // step: x^(n+1) and v^(n+1/2)).  FP32 atomic sums (their order varies).
-__global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, float q, double dt, YeeGrid g,
+// Constants of the deposition: FP32, with the grid's 1/dx, 1/dy and
+// x0/dx, y0/dy as float pairs (hi + lo) so that the cell coordinate of a
+// position keeps double-float precision without an FP64 instruction.
+struct DepositConsts {
+    float q_area;                    // q / (dx dy)
+    float idx_hi, idx_lo, idy_hi, idy_lo;
+    float x0s_hi, x0s_lo, y0s_hi, y0s_lo;
+    float hdt_x, hdt_y;              // dt / (2 dx), dt / (2 dy)
+};
+
+// Cell and in-cell fraction of a double-float cell coordinate (the fraction
+// in [0, 1) from the pair's two parts).
+__device__ __forceinline__ float cell_of(df2 a, float &frac)
+{
+    float f = floorf(a.hi);
+    float r = (a.hi - f) + a.lo;
+    if (r < 0.0f) {
+        r += 1.0f;
+        f -= 1.0f;
+    }
+    if (r >= 1.0f) {
+        r -= 1.0f;
+        f += 1.0f;
+    }
+    frac = r;
+    return f;
+}
+
+// J += q w v at the mid-step position x - v dt/2, linear weights on each
+// component's staggered nodes (Jx at i+1/2, Jy at j+1/2, Jz at the node).
+// The FP64 state is read as double-float positions and nearest-float
+// momenta and weights by integer instructions (qp_df.h): no instruction
+// runs on the FP64 pipe.
+__global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, DepositConsts c, YeeGrid g,
                                                        float *jx, float *jy, float *jz,
                                                        int *status)
 {
@@ -162,23 +196,31 @@ __global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, float q, do
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     float *J[3] = {jx, jy, jz};
-    const float ox[3] = {0.5f, 0.0f, 0.0f}, oy[3] = {0.0f, 0.5f, 0.0f};
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const float ux = (float)S.ux[p], uy = (float)S.uy[p], uz = (float)S.uz[p];
+        const double xd = S.x[p], yd = S.y[p], uxd = S.ux[p], uyd = S.uy[p], uzd = S.uz[p],
+                     wd = S.w[p];
+        const float ux = hi_d(uxd), uy = hi_d(uyd), uz = hi_d(uzd);
         const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
         const float v[3] = {ux * ig, uy * ig, uz * ig};
-        // mid-step position in cells (the subtraction in FP64: positions are large)
-        const float gx0 = (float)((S.x[p] - 0.5 * dt * (double)v[0] - g.x0) / g.dx);
-        const float gy0 = (float)((S.y[p] - 0.5 * dt * (double)v[1] - g.y0) / g.dy);
-        const float a = q * (float)S.w[p] / (float)(g.dx * g.dy);
+        // mid-step position in cells
+        const df2 gx = df_add_f(df_sub(df_mul(split_d(xd), {c.idx_hi, c.idx_lo}),
+                                       {c.x0s_hi, c.x0s_lo}),
+                                -c.hdt_x * v[0]);
+        const df2 gy = df_add_f(df_sub(df_mul(split_d(yd), {c.idy_hi, c.idy_lo}),
+                                       {c.y0s_hi, c.y0s_lo}),
+                                -c.hdt_y * v[1]);
+        const float a = c.q_area * hi_d(wd);
+        float fx0, fy0, fxh, fyh;
+        const float fi0 = cell_of(gx, fx0), fj0 = cell_of(gy, fy0);
+        const float fih = cell_of(df_add_f(gx, -0.5f), fxh), fjh = cell_of(df_add_f(gy, -0.5f), fyh);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float gx = gx0 - ox[c], gy = gy0 - oy[c];
-            const float fi = floorf(gx), fj = floorf(gy);
-            const float fx = gx - fi, fy = gy - fj;
+        for (int k = 0; k < 3; ++k) {
+            // Jx: x - 1/2 in cells; Jy: y - 1/2; Jz: the node itself
+            const float fi = k == 0 ? fih : fi0, fj = k == 1 ? fjh : fj0;
+            const float fx = k == 0 ? fxh : fx0, fy = k == 1 ? fyh : fy0;
             if (!(fi >= -1.0f && fj >= -1.0f && fi < (float)g.nx && fj < (float)g.ny)) continue;
             const int64_t i = (int64_t)fi, j = (int64_t)fj;
-            const float av = a * v[c];
+            const float av = a * v[k];
             if (av == 0.0f) continue;
 #pragma unroll
             for (int b = 0; b < 2; ++b)
@@ -187,7 +229,7 @@ __global__ void __launch_bounds__(kPicBlock) k_deposit(SpeciesDev S, float q, do
                     const int64_t ii = i + e, jj = j + b;
                     if (ii < 0 || jj < 0 || ii >= g.nx || jj >= g.ny) continue;
                     const float wgt = (e ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy);
-                    atomicAdd(&J[c][jj * g.nx + ii], av * wgt);
+                    atomicAdd(&J[k][jj * g.nx + ii], av * wgt);
                 }
         }
     }
@@ -262,8 +304,20 @@ cudaError_t launch_yee_e(const YeeGrid &g, const float *jx, const float *jy, con
 cudaError_t launch_deposit(const SpeciesDev &S, double q, double dt, const YeeGrid &g, float *jx,
                            float *jy, float *jz, int *status, int num_sms, cudaStream_t st)
 {
-    k_deposit<<<grid_blocks(S.cap, num_sms), kPicBlock, 0, st>>>(S, (float)q, dt, g, jx, jy, jz,
-                                                                 status);
+    DepositConsts c;
+    const double idx = 1.0 / g.dx, idy = 1.0 / g.dy, x0s = g.x0 * idx, y0s = g.y0 * idy;
+    auto split = [](double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    c.q_area = (float)(q / (g.dx * g.dy));
+    split(idx, c.idx_hi, c.idx_lo);
+    split(idy, c.idy_hi, c.idy_lo);
+    split(x0s, c.x0s_hi, c.x0s_lo);
+    split(y0s, c.y0s_hi, c.y0s_lo);
+    c.hdt_x = (float)(0.5 * dt * idx);
+    c.hdt_y = (float)(0.5 * dt * idy);
+    k_deposit<<<grid_blocks(S.cap, num_sms), kPicBlock, 0, st>>>(S, c, g, jx, jy, jz, status);
     return cudaGetLastError();
 }
 
