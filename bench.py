@@ -30,7 +30,7 @@ The line also carries
 Particle-steps count the live slots at each step start, decayed photons
 (tau < 0, kept in their slots) left out.  L2 is flushed (256 MB write)
 between timed steps; each step is timed with CUDA events on its stream,
-queued by the host ahead of the device (a spin kernel before the first
+queued by the host ahead of the device (~1 ms of flushes before the first
 timed step); clocks are sampled with nvidia-smi meanwhile.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -211,16 +211,22 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
     ctx = Q.qp_init_tables(LAMBDA_M, dev)
     sim = Simulation(w, precision=precision, ctx=ctx, device=dev, track_chi=False, ids=ids)
     stream = torch.cuda.current_stream()
-    # warm-up steps on the initial state, then back to the initial state
-    for _ in range(warmup):
-        flush.zero_()
-        sim.run(1)
-    torch.cuda.synchronize()
-    sim.load_initial()
-    torch.cuda.synchronize()
     names = ("electron", "positron", "photon")
     counts = torch.zeros((steps, 3), dtype=torch.int64, device=f"cuda:{dev}")
     live = [sim.species[n].n_live for n in names]
+    # warm-up steps on the initial state (the timed loop's own launches, so
+    # that every kernel and event the loop uses has run once), then back to
+    # the initial state
+    for _ in range(warmup):
+        flush.zero_()
+        torch.cat(live, out=counts[0])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.run(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sim.load_initial()
+    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     # A step of a workload with given fields is one k_step launch: its own
@@ -233,10 +239,13 @@ def run_path(w, precision, steps, warmup, dev, dist, flush, ids=None):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    # a spin of ~50 ms ahead of the first timed step: the host queues the
-    # steps before the device reaches them, so the events time the device's
-    # work and not the Python loop between launches
-    torch.cuda._sleep(int(1e8 + 2e5 * steps))
+    # ~1 ms of L2 flushes ahead of the first timed step: the host queues the
+    # steps before the device reaches them (and stays ahead: a step's flush
+    # alone outlasts the host's loop), so the events time the device's work
+    # and not the Python loop between launches; real work, not an idle
+    # spin, so the clocks stay up
+    for _ in range(25):
+        flush.zero_()
     for k in range(steps):
         flush.zero_()
         torch.cat(live, out=counts[k])       # live slots at the start of the step
