@@ -718,7 +718,6 @@ int qp_step(qp_ctx *ctx, const qp_step_params *s, void *stream)
     a.ctl = ctx->d_ctl;
     a.n_problems = 0;
     a.problems = nullptr;
-    a.fixed_first = 1;  // a cooperative launch (launch_step)
     qp::Problem &P = a.single;
     P.lep_words = ctx->d_chain;
     P.pho_words = ctx->d_chain + ctx->chain_words;

@@ -128,7 +128,6 @@ struct StepArgs {
     double a_S, C_rate, tau0w;
     unsigned int spin_limit;          // bound of every device-side wait
     int32_t n_problems;               // 0: the single problem below
-    int32_t fixed_first;              // 1: a cooperative launch; block b's first tile is b
     const Problem *problems;          // device table of n_problems entries
     double *stash;                    // append records: [block][2][fields][kTile]
     Problem single;

@@ -149,9 +149,10 @@ cudaError_t launch_step(const StepArgs &a, int precision, int field_kind, bool b
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = step_smem_bytes(precision);
     void *args[] = {(void *)&a};
-    // fixed first tiles need every block resident at once: a cooperative
-    // launch guarantees it (or fails to launch)
-    if (a.fixed_first)
+    // the single-problem mixed-path kernel takes fixed first tiles, which
+    // need every block resident at once: a cooperative launch guarantees it
+    // (or fails to launch)
+    if (!batch && precision == QP_MIXED)
         return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTile), args, smem, st);
     return cudaLaunchKernel(fn, dim3(grid), dim3(kTile), args, smem, st);
 }

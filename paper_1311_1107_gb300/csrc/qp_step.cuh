@@ -1174,8 +1174,12 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
     // once that block runs; its first atomic overlaps the reads of the live
     // counts below.  A block whose ticket is past the last tile leaves
     // without work.
-    const unsigned tbase = a.fixed_first ? gridDim.x : 0u;
-    if (tid == 0) s_ticket[0] = a.fixed_first ? blockIdx.x : atomicAdd(&a.ctl->ticket, 1u);
+    // launched cooperatively (launch_step); not on the FP64 path, whose
+    // one-launch-a-step runs of small problems (4096 e-, 32 tiles on 608
+    // blocks) took 75 -> 108 us a step when launched cooperatively
+    constexpr bool kFixedFirst = !BATCH && PREC != kFP64;
+    const unsigned tbase = kFixedFirst ? gridDim.x : 0u;
+    if (tid == 0) s_ticket[0] = kFixedFirst ? blockIdx.x : atomicAdd(&a.ctl->ticket, 1u);
     const int np = BATCH ? a.n_problems : 1;
     const Problem *table = BATCH ? a.problems : &a.single;
     const unsigned epoch = __ldcg(&a.ctl->epoch);
