@@ -222,7 +222,11 @@ typedef struct {
  * energy recorded; the step still completes.  The first step with species
  * larger than any stepped before grows the context's look-back scratch (one
  * allocation, synchronous); otherwise no allocation, no host synchronisation,
- * no host reads: the call can then be captured in a CUDA graph.
+ * no host reads: the call can then be captured in a CUDA graph.  Each step
+ * is one launch of the step kernel over every resident block of the GPU; on
+ * the mixed path it is a cooperative launch, which starts only once all its
+ * blocks fit on the GPU (kernels of other streams that hold SMs finish
+ * first).
  * Returns QP_ERR_INVALID_ARG (nothing enqueued) for bad parameters, a
  * missing photon species while species emit, or a YEE2D grid with a NULL
  * component; QP_ERR_CUDA if a launch fails.  Overflow, table clamping and
