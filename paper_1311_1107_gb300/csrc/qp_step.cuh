@@ -1165,18 +1165,18 @@ __global__ void __launch_bounds__(kTile, step_min_blocks<PREC, FK>())
 
     const int tid = threadIdx.x;
     // Tickets.  A tile must belong to a running block (its successors' look-
-    // backs wait on it).  In a cooperative launch (a single problem) every
-    // block is resident for the whole launch, so block b takes tile b at
-    // entry and later tickets come from the counter, offset by the grid: no
-    // block queues on the contended counter before its first tile.  A batch
-    // (its launches captured in graphs, next to other streams' kernels)
-    // takes every ticket from the counter, so a tile belongs to a block only
-    // once that block runs; its first atomic overlaps the reads of the live
-    // counts below.  A block whose ticket is past the last tile leaves
+    // backs wait on it).  A single problem on the mixed path is launched
+    // cooperatively (launch_step): every block is resident for the whole
+    // launch, so block b takes tile b at entry and later tickets come from
+    // the counter, offset by the grid; no block queues on the contended
+    // counter before its first tile.  The FP64 path and batches take every
+    // ticket from the counter, so a tile belongs to a block only once that
+    // block runs (a batch's launches are captured in graphs next to other
+    // streams' kernels; the FP64 path's one-launch-a-step runs of small
+    // problems, 4096 e- on 608 blocks, took 75 -> 108 us a step when
+    // launched cooperatively); the first atomic overlaps the reads of the
+    // live counts below.  A block whose ticket is past the last tile leaves
     // without work.
-    // launched cooperatively (launch_step); not on the FP64 path, whose
-    // one-launch-a-step runs of small problems (4096 e-, 32 tiles on 608
-    // blocks) took 75 -> 108 us a step when launched cooperatively
     constexpr bool kFixedFirst = !BATCH && PREC != kFP64;
     const unsigned tbase = kFixedFirst ? gridDim.x : 0u;
     if (tid == 0) s_ticket[0] = kFixedFirst ? blockIdx.x : atomicAdd(&a.ctl->ticket, 1u);
