@@ -482,7 +482,8 @@ def e2e(w, precision, steps, dev):
     counts from pinned host blocks to the device, runs the step, reads the
     new counts back and copies the new state back into the host blocks
     (and synchronises).  The bytes are the arrays of the live slots each
-    way plus the counts."""
+    way (back: without the weights of the slots live before the step, which
+    a step does not change) plus the counts."""
     import torch
 
     from paper_1311_1107_gb300 import qedpic as Q
@@ -510,7 +511,11 @@ def e2e(w, precision, steps, dev):
         total_slots += sum(before)
         h2d += sum(c * 8 * rows[n] + 8 for c, n in zip(before, names))
         sim.run_host(states, 1, stream)
-        d2h += sum(int(states[k].count) * 8 * rows[n] + 8 for k, n in enumerate(names))
+        # slots live before the step come back without their weight row (the
+        # step writes the weights of appended particles only); appended
+        # slots with every row
+        d2h += sum(b * 8 * (rows[n] - 1) + (int(states[k].count) - b) * 8 * rows[n] + 8
+                   for k, (b, n) in enumerate(zip(before, names)))
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     Q.qp_destroy(ctx)

@@ -407,7 +407,8 @@ int qp_init_optical_depth(qp_ctx *ctx, int32_t handle, uint64_t seed, int64_t fi
 // and a host block (array k at byte k * host_pitch; slot j at byte 8 j of
 // its row); the caller has checked the range and made the device current.
 static cudaError_t copy_slots(const qp_species_desc &d, void *host, int64_t host_pitch,
-                              int64_t first, int64_t count, int32_t to_device, cudaStream_t st)
+                              int64_t first, int64_t count, int32_t to_device, cudaStream_t st,
+                              bool skip_weight = false)
 {
     if (count == 0) return cudaSuccess;
     double *arr[8];
@@ -420,6 +421,7 @@ static cudaError_t copy_slots(const qp_species_desc &d, void *host, int64_t host
     arr[na++] = d.uz;
     arr[na++] = d.tau;
     arr[na++] = d.w;
+    if (skip_weight) --na;  // the weight is the last row
     const size_t width = (size_t)count * sizeof(double);
     char *h0 = (char *)host + (size_t)first * sizeof(double);
     // device arrays at a constant pitch (one allocation): one strided copy
@@ -494,6 +496,11 @@ int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *
         (void)cudaStreamSynchronize(cs);
         return r;
     };
+    // the three live counters side by side in device memory (as a
+    // Simulation keeps them): one copy each way instead of three
+    bool adjacent = hs[0] != -1 && hs[1] != -1 && hs[2] != -1;
+    for (int k = 1; k < 3 && adjacent; ++k)
+        adjacent = ctx->species[hs[k]].d.n_live == ctx->species[hs[0]].d.n_live + k;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 3; ++k) {
         if (hs[k] == -1) continue;
@@ -501,22 +508,34 @@ int qp_step_host(qp_ctx *ctx, const qp_step_params *s, qp_host_state *st, void *
         hc[k] = st[k].count;
         e = copy_slots(d, st[k].host, st[k].pitch, 0, st[k].count, 1, cs);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        e = cudaMemcpyAsync(d.n_live, hc + k, sizeof(long long), cudaMemcpyHostToDevice, cs);
+        if (!adjacent)
+            e = cudaMemcpyAsync(d.n_live, hc + k, sizeof(long long), cudaMemcpyHostToDevice, cs);
         if (e != cudaSuccess) return fail(cuda_status(e));
     }
+    if (adjacent)
+        e = cudaMemcpyAsync(ctx->species[hs[0]].d.n_live, hc, 3 * sizeof(long long),
+                            cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return fail(cuda_status(e));
     const int st_step = qp_step(ctx, s, stream);
     if (st_step < 0) return fail(st_step);
     // a step never lowers a live count (decayed photons keep their slots):
     // the slots live before it go back at once, behind the step on the
-    // stream; only the appended ones wait for the new counts
+    // stream, without their weights (a step writes the weights of appended
+    // particles only, so the host's are current); the appended slots, all
+    // rows, wait for the new counts
     for (int k = 0; k < 3; ++k) {
         if (hs[k] == -1) continue;
         const qp_species_desc &d = ctx->species[hs[k]].d;
-        e = copy_slots(d, st[k].host, st[k].pitch, 0, st[k].count, 0, cs);
+        e = copy_slots(d, st[k].host, st[k].pitch, 0, st[k].count, 0, cs, true);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        e = cudaMemcpyAsync(hc + k, d.n_live, sizeof(long long), cudaMemcpyDeviceToHost, cs);
+        if (!adjacent)
+            e = cudaMemcpyAsync(hc + k, d.n_live, sizeof(long long), cudaMemcpyDeviceToHost, cs);
         if (e != cudaSuccess) return fail(cuda_status(e));
     }
+    if (adjacent)
+        e = cudaMemcpyAsync(hc, ctx->species[hs[0]].d.n_live, 3 * sizeof(long long),
+                            cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) return fail(cuda_status(e));
     e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return cuda_status(e);
     bool more = false;
