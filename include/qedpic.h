@@ -248,10 +248,11 @@ typedef struct qp_host_state {
  * species are ignored), slots [0, st[k].count) are copied from st[k].host
  * to the device arrays and the live count set; s->n_steps steps run as
  * qp_step runs them; the new live counts are read back into st[k].count and
- * slots [0, count) of every array are copied back into st[k].host (the
- * slots live before the steps as soon as they are done: a step never lowers
- * a live count, since decayed photons keep their slots; the appended ones
- * once the counts are read).  The call synchronises `stream` once, or twice
+ * slots [0, count) are copied back into st[k].host (the slots live before
+ * the steps as soon as they are done, every array but the weights, which a
+ * step writes for appended particles only: a step never lowers a live
+ * count, since decayed photons keep their slots; the appended ones, every
+ * array, once the counts are read).  The call synchronises `stream` once, or twice
  * when the steps appended particles, and returns when the host blocks hold
  * the result.  Per-particle event
  * counts and chi are left on the device (qp_diagnostics).  Returns what
