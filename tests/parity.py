@@ -46,12 +46,16 @@ def oracle_pic_start(sim, workload):
     O.fill_pulse2d(p, sim.field, sim.P.step * sim.P.dt)
 
 
-def oracle_pic_steps(sim, n_steps):
+def oracle_pic_steps(sim, n_steps, field_noise=0.0, noise_key=0):
     """PIC cycles of the oracle: B half step, the QED step, the leptons'
-    current (FP64, rounded to the grid's float), B half step, E full step."""
+    current (FP64, rounded to the grid's float), B half step, E full step.
+    field_noise: relative +-kick of every grid value after every cycle (a
+    twin run's model of the device's FP32 solver arithmetic and unordered
+    current sums, which the oracle's FP64 solver does not have)."""
     f = sim.field
     comps = f._keep
     dt = sim.P.dt
+    rng = np.random.default_rng(1000 + noise_key) if field_noise else None
     for _ in range(n_steps):
         O.yee_advance_b(comps, f.dx, f.dy, 0.5 * dt)
         sim.run(1)
@@ -61,14 +65,18 @@ def oracle_pic_steps(sim, n_steps):
                 O.deposit_current(sp, q, dt, J, f.dx, f.dy, f.x0, f.y0)
         O.yee_advance_b(comps, f.dx, f.dy, 0.5 * dt)
         O.yee_advance_e(comps, [j.astype(np.float32) for j in J], f.dx, f.dy, dt)
+        if field_noise:
+            for c in comps:
+                c *= (1.0 + field_noise * rng.choice((-1.0, 1.0), size=c.shape)).astype(c.dtype)
 
 
-def oracle_steps(sim, workload, n_steps):
+def oracle_steps(sim, workload, n_steps, field_noise=0.0, noise_key=0):
     """n_steps of an oracle run; a workload with a refilled grid gets the
     oracle's own refill (from the pulse, FP64 rounded to float) before each
-    step, a PIC workload the oracle's own solver and deposition."""
+    step, a PIC workload the oracle's own solver and deposition (with
+    field_noise, kicked after every cycle: see oracle_pic_steps)."""
     if workload["field"].get("pic"):
-        oracle_pic_steps(sim, n_steps)
+        oracle_pic_steps(sim, n_steps, field_noise, noise_key)
         return
     pulse = oracle_pulse(workload["field"])
     if pulse is None:
@@ -79,14 +87,17 @@ def oracle_steps(sim, workload, n_steps):
         sim.run(1)
 
 
-def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, noise_key=0):
+def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, noise_key=0,
+               field_noise=0.0):
     """Run the oracle on a workload.  sample: optional slot indices of the
     electrons to keep (each keeps its random stream).  extra: optional dict
     species -> arrays of initial positrons/photons (with their own tau).
     kick: relative perturbation of the initial electron momenta (sign
     alternating with the slot); noise: relative +-kick of every lepton
-    momentum after every step.  Both serve the twin run that measures how
-    strongly each trajectory amplifies rounding-level differences."""
+    momentum after every step; field_noise (PIC workloads): relative +-kick
+    of every grid value after every cycle.  All serve the twin run that
+    measures how strongly each trajectory amplifies rounding-level
+    differences."""
     dims = workload["dims"]
     cap = dict(workload["capacity"])
     el_arr = workload["electrons"]
@@ -132,7 +143,7 @@ def run_oracle(workload, n_steps, sample=None, extra=None, kick=0.0, noise=0.0, 
                 photons=ph)
     if workload["field"].get("pic"):
         oracle_pic_start(sim, workload)
-    oracle_steps(sim, workload, n_steps)
+    oracle_steps(sim, workload, n_steps, field_noise, noise_key)
     return sim, {"electron": el, "positron": po, "photon": ph}
 
 
