@@ -476,6 +476,16 @@ def roofline(res, dims, pairs, hbm_peak, peak_kind, traffic=None):
     return out
 
 
+def e2e_bytes(before, after, rows):
+    """Bytes moved by one qp_step_host call: in, every array (`rows` per
+    species) of the slots live before the step and the count; back, those
+    slots without their weight row (a step writes the weights of appended
+    particles only), the appended slots with every row, and the count."""
+    h2d = sum(b * 8 * r + 8 for b, r in zip(before, rows))
+    d2h = sum(b * 8 * (r - 1) + (a - b) * 8 * r + 8 for b, a, r in zip(before, after, rows))
+    return h2d, d2h
+
+
 def e2e(w, precision, steps, dev):
     """End to end through the public API with the state in host memory: every
     step is one qp_step_host call, which copies the live particles and
@@ -503,21 +513,20 @@ def e2e(w, precision, steps, dev):
         sim.species[n].copy_state(host[n], live[n], False, st)
     torch.cuda.synchronize()
     states = sim.host_states(host, live)
-    h2d = d2h = 0
-    total_slots = 0
+    counts = [[int(states[k].count) for k in range(3)]]
     t0 = time.perf_counter()
     for _ in range(steps):
-        before = [int(states[k].count) for k in range(3)]
-        total_slots += sum(before)
-        h2d += sum(c * 8 * rows[n] + 8 for c, n in zip(before, names))
         sim.run_host(states, 1, stream)
-        # slots live before the step come back without their weight row (the
-        # step writes the weights of appended particles only); appended
-        # slots with every row
-        d2h += sum(b * 8 * (rows[n] - 1) + (int(states[k].count) - b) * 8 * rows[n] + 8
-                   for k, (b, n) in enumerate(zip(before, names)))
+        counts.append([int(states[k].count) for k in range(3)])
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
+    r = [rows[n] for n in names]
+    total_slots = sum(sum(c) for c in counts[:-1])
+    h2d = d2h = 0
+    for before, after in zip(counts[:-1], counts[1:]):
+        i, o = e2e_bytes(before, after, r)
+        h2d += i
+        d2h += o
     Q.qp_destroy(ctx)
     return {"value": round(total_slots / wall, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),

@@ -90,3 +90,13 @@ def test_fused_window_issue_roofline(tmp_path, monkeypatch):
     assert r["bound"] == "alu" and r["peak"] == 1258.6
     assert r["achieved"] == 1.0 and r["frac"] == round(1.0 / 1258.56, 4)
     assert bench.issue_roofline(None, 2.0, 2, 152)["frac"] is None
+
+
+def test_end_to_end_bytes_count_the_copies_made():
+    # in: all seven rows of the live slots and a count per species; back:
+    # six rows (no weights) of the slots live before the step, seven of the
+    # appended ones, and the counts
+    h2d, d2h = bench.e2e_bytes([10, 0, 5], [12, 1, 7], [7, 7, 7])
+    assert h2d == (10 * 56 + 8) + 8 + (5 * 56 + 8)
+    assert d2h == (10 * 48 + 2 * 56 + 8) + (1 * 56 + 8) + (5 * 48 + 2 * 56 + 8)
+    assert bench.e2e_bytes([0, 0, 0], [0, 0, 0], [8, 8, 8]) == (24, 24)
