@@ -138,3 +138,27 @@ def test_sort_by_cell_is_a_stable_permutation():
     assert sorted(orig) == list(range(n))
     np.testing.assert_array_equal(sp.x[:n], xs[orig])
     np.testing.assert_array_equal(sp.ux[:n] ** 2 >= 0, True)
+
+
+def test_pic_twin_field_kicks_are_rounding_level():
+    # the twin runs of the PIC parity test kick every grid value by a
+    # relative +-eps after every cycle: without the kick a run repeats bit
+    # for bit, with it the grid moves by about eps per cycle and no more
+    from paper_1311_1107_gb300 import workloads as W
+    from tests.parity import run_oracle
+
+    w = W.laser_on_foil(nx=64, ny=32, ppc=2, foil_cells=2, n_steps=8,
+                        photon_capacity=1 << 12, pair_capacity=1 << 8, pic=True)
+    a, _ = run_oracle(w, 4)
+    b, _ = run_oracle(w, 4)
+    c, _ = run_oracle(w, 4, field_noise=2e-7, noise_key=0)
+    d, _ = run_oracle(w, 4, field_noise=2e-7, noise_key=1)
+    for k in range(6):
+        fa, fb = a.field._keep[k], b.field._keep[k]
+        assert np.array_equal(fa, fb)
+    ey_a, ey_c, ey_d = a.field._keep[1], c.field._keep[1], d.field._keep[1]
+    scale = np.abs(ey_a).max()
+    assert scale > 0
+    dc = np.abs(ey_c - ey_a).max() / scale
+    assert 0 < dc < 1e-5
+    assert not np.array_equal(ey_c, ey_d)  # the key picks the kick pattern
